@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Grouped F + F^H pairs per second on one GB300 (d = 20, |u| <= 2, M = 1e6).
+
+Workload (synthetic, seeded): 211 ANOVA terms (empty set, 20 one-dimensional
+terms with N = 64, 190 two-dimensional terms with N = 32), 183,851 complex
+coefficients N(0,1)/(1+|k|^2), M = 1,000,000 i.i.d. uniform nodes on
+[-1/2, 1/2)^20, y complex N(0,1).  One step = one grouped_trafo + one
+grouped_adjoint through the C ABI.  Inputs are resident in HBM for ``value``;
+``e2e`` repeats the step with host buffers (pinned H2D of fhat and y, D2H of
+both results) inside the timed region.  L2 is flushed (256 MB write) before
+every timed step, outside the step's events.
+
+``--impl reference`` times the FP64 oracle (direct summation on the host
+cores) on a bounded node sample of the same workload and scales to M = 1e6.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, every rank runs an independent replica (the transform
+pair needs no exchange between problems), ``value`` sums over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grouped F+F^H pairs/s (M=1e6,d=20)"
+UNIT = "pairs/s"
+WORKLOAD = "d=20, |u|<=2 (211 terms), N=64 (1D) / 32x32 (2D), 183851 coeffs, M=1e6 uniform nodes"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--M", type=int, default=1_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=20000, help="nodes in the oracle's timed sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [v.strip() for v in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- reference ---
+
+def oracle_pair_seconds(w, m: int):
+    """Time one oracle F and one oracle F^H on the first m nodes (FP64, host cores)."""
+    import numpy as np
+
+    from oracle import ndft
+    x = w["x"][:, :m].astype(np.float32).astype(np.float64)
+    y = w["y"][:m]
+    ndft.load()
+    t0 = time.perf_counter()
+    ndft.trafo(x, w["terms"], w["bandwidths"], w["fhat"])
+    ndft.adjoint(x, w["terms"], w["bandwidths"], y)
+    return time.perf_counter() - t0, ndft.default_threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2010_10199_gb300 import inputs
+    m = args.cpu_sample
+    w = inputs.c2_scale(M=max(m, 1))
+    times = []
+    cores = 1
+    for i in range(args.warmup + args.steps):
+        t, cores = oracle_pair_seconds(w, m)
+        if i >= args.warmup:
+            times.append(t)
+    per_pair_full = sum(times) / len(times) * (args.M / m)
+    value = 1.0 / per_pair_full
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_pair_full * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": WORKLOAD, "M": args.M, "sample_nodes": m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{m} of {args.M} nodes per step, all 211 terms; scaled linearly in M"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- mine ----
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in sorted(files):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_mine(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2010_10199_gb300 import build as cuda_build
+    from paper_2010_10199_gb300 import gft, inputs
+
+    cuda_build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    w = inputs.c2_scale(M=args.M)
+    x32 = torch.from_numpy(w["x"].astype(np.float32)).to(dev)
+    P = gft.Plan(x32, w["terms"], w["bandwidths"])
+    n = P.n_coeffs
+    fhat_h = torch.from_numpy(w["fhat"].astype(np.complex64)).pin_memory()
+    y_h = torch.from_numpy(w["y"].astype(np.complex64)).pin_memory()
+    fhat = fhat_h.to(dev)
+    y = y_h.to(dev)
+    f = torch.empty(args.M, dtype=torch.complex64, device=dev)
+    g = torch.empty(n, dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def pair():
+        P.trafo(fhat, out=f)
+        P.adjoint(y, out=g)
+
+    for _ in range(args.warmup):
+        pair()
+    torch.cuda.synchronize()
+    P.profile(True)
+    P.profile_read(reset=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        pair()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    prof = P.profile_read(reset=True)
+    P.profile(False)
+    total_s = sum(step_ms) / 1e3
+    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_max = float(t.item())
+    value = args.steps * world / total_max
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        f_h = torch.empty(args.M, dtype=torch.complex64).pin_memory()
+        g_h = torch.empty(n, dtype=torch.complex64).pin_memory()
+        ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps + 1):
+            if k > 0:
+                flush.zero_()
+                ee[k - 1][0].record(stream)
+            fhat.copy_(fhat_h, non_blocking=True)
+            y.copy_(y_h, non_blocking=True)
+            pair()
+            f_h.copy_(f, non_blocking=True)
+            g_h.copy_(g, non_blocking=True)
+            if k > 0:
+                ee[k - 1][1].record(stream)
+        torch.cuda.synchronize()
+        e_s = sum(a.elapsed_time(b) for a, b in ee) / 1e3
+        te = torch.tensor([e_s], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": args.steps * world / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * (n + args.M), "d2h_bytes_per_step": 8 * (n + args.M)}
+
+    # roofline of the dominant kernel (algorithmic bytes per launch / live event time)
+    peaks, peak_kind = measured_peaks()
+    gms, gl = prof.get("gather", (0.0, 0))
+    sms, sl = prof.get("spread", (0.0, 0))
+    M, d = args.M, 20
+    n_terms2, n_terms1 = 190, 20
+    grid_bytes = 8 * (n_terms2 * 69 * 72 + n_terms1 * 136)
+    if gms / max(gl, 1) >= sms / max(sl, 1):
+        kname, kms, klaunch = "gather_f32", gms / max(gl, 1), gl
+        # nodes read (4 B per coordinate), f written, grids and coefficients read once
+        alg_bytes = 4 * d * M + 8 * M + grid_bytes + 8 * n
+    else:
+        kname, kms, klaunch = "spread_f32", sms / max(sl, 1), sl
+        # nodes and y read, one grid written
+        alg_bytes = 4 * d * M + 8 * M + grid_bytes
+    achieved = alg_bytes / (kms / 1e3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        tj = json.load(open(tf))
+        src = [os.path.join(ROOT, "paper_2010_10199_gb300", "csrc", s) for s in tj.get("sources", [])]
+        if tj.get("kernel") == kname and all(os.path.exists(s) for s in src) and source_hash(src) == tj.get("hash"):
+            traffic = tj.get("dram_bytes_per_launch")
+    # on-chip (shared-memory) roofline: window taps x 8 bytes read (gather) or updated (spread)
+    taps = n_terms2 * 6 * 8 + n_terms1 * 8
+    smem_bytes = taps * 8 * M
+    clk_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    smem_peak = 152 * 128 * clk_mhz * 1e6 / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
+            "kernel_ms": kms, "alg_bytes_per_launch": alg_bytes, "peak_source": peak_kind,
+            "onchip": {"bound": "smem", "achieved": smem_bytes / (kms / 1e3) / 1e9, "peak": smem_peak,
+                       "unit": "GB/s", "frac": smem_bytes / (kms / 1e3) / 1e9 / smem_peak,
+                       "peak_basis": "152 SMs x 128 B/clk x median SM clock in the timed region"}}
+
+    launches = 0
+    per_stage_kernels = {"trafo_pre": 1, "gather": 1, "spread": 1, "reduce_partials": 1, "adjoint_post": 1,
+                         "empty_sum": 2, "solver_vec": 1}
+    for name, (_, cnt) in prof.items():
+        launches += cnt * per_stage_kernels.get(name, 1)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        m = args.cpu_sample
+        ts, cores = oracle_pair_seconds(w, m)
+        cpu = {"value": 1.0 / (ts * args.M / m), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one pair on the first {m} of {args.M} nodes, all 211 terms, FP64 direct sums; "
+                         f"{ts:.1f} s, scaled linearly in M"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64)",
+                "config": {"workload": WORKLOAD, "M": args.M, "precision": "fp32 grids and accumulation",
+                           "window": "Kaiser-Bessel, sigma=2, 6 row x 8 column taps",
+                           "l2": "flushed (256 MB write) before every timed step",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+                "wall_s": wall}
+        print(json.dumps(line), flush=True)
+    P.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        if args.impl == "mine":
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        else:
+            torch.distributed.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_mine(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * anova_gft.h -- C ABI of the GB300 grouped Fourier transform library.
+ *
+ * Grouped Fourier transform (Bartel, Potts, Schmischke, "Grouped
+ * Transformations and Regularization in High-Dimensional Explainable ANOVA
+ * Approximation"):
+ *
+ *   f_j = sum_{u in U} sum_{k in I_{N_u}^{u,d}} fhat_k exp(+2 pi i <k, x_j>)
+ *                                  (Definition "grouped Fourier transform", Sec. 3)
+ *   (F^H y)_k = sum_j y_j exp(-2 pi i <k, x_j>)    (stacked adjoint, Sec. 3)
+ *
+ * computed per ANOVA term u through the low-dimensional identity of eq.
+ * (somafm): zero-extend the block fhat(u) to ghat(u), deconvolve by the
+ * window's Fourier coefficients, oversampled FFT, and window gather/spread
+ * with a Kaiser--Bessel window (the NFFT the paper cites after eq. (somafm)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All pointers named *_dev are DEVICE pointers on the device that was
+ *   current when the plan was created; all other pointers are host pointers.
+ *   The caller owns every pointer it passes; the library never frees them and
+ *   keeps no reference to them after the call returns (the plan copies the
+ *   nodes it is given).
+ * - Complex vectors are interleaved (re, im).  Their element type follows the
+ *   plan's precision: float pairs (anova_cfloat) for ANOVA_PREC_F32,
+ *   ANOVA_PREC_BF16 and ANOVA_PREC_F16 (the 16-bit modes only change how the
+ *   oversampled grids are stored), double pairs for ANOVA_PREC_F64.
+ * - Nodes x are SoA [d][M] (coordinate t of node j at x[t*M + j]) in the
+ *   plan's real type, on the torus T = R/Z; values outside [-1/2, 1/2) are
+ *   wrapped (a node at exactly 1/2 is the node -1/2).
+ * - Terms: term_dims is a host array [n_terms][3] of coordinate ids, each
+ *   row ascending and padded with -1 (a row of three -1 is the empty set);
+ *   bandwidth[i] is N_u (even, >= 2; ignored for the empty set).  The term
+ *   order given here is the coefficient block order.  Inside a block the
+ *   multi-index over the term's coordinates is row-major (last coordinate
+ *   fastest), each coordinate running -N/2, ..., -1, 1, ..., N/2-1
+ *   (I_N minus {0}, Remark "cardinality"); the empty set is the single k = 0
+ *   coefficient.  The number of coefficients is sum_u (N_u - 1)^{|u|}.
+ * - Work is enqueued on the plan's stream; calls return once the work is
+ *   enqueued unless stated otherwise.  Calls on one plan must not overlap.
+ * - Every call returns an int status: ANOVA_OK (0) or a negative code below;
+ *   anova_status_string() names it.  No exception or longjmp crosses the ABI.
+ */
+#ifndef ANOVA_GFT_H
+#define ANOVA_GFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct anova_plan_s *anova_plan_t;
+typedef struct { float re, im; } anova_cfloat;
+typedef struct { double re, im; } anova_cdouble;
+
+enum anova_precision {
+    ANOVA_PREC_F32 = 0,   /* grids, vectors and accumulation in FP32 */
+    ANOVA_PREC_BF16 = 1,  /* grids stored in BF16, FP32 accumulation */
+    ANOVA_PREC_F16 = 2,   /* grids stored in FP16, FP32 accumulation */
+    ANOVA_PREC_F64 = 3    /* everything in FP64 */
+};
+
+enum anova_status {
+    ANOVA_OK = 0,
+    ANOVA_ERR_INVALID = -1,      /* bad argument (null pointer, size, term, bandwidth) */
+    ANOVA_ERR_UNSUPPORTED = -2,  /* valid but outside what this build handles (|u| > 3, huge grid) */
+    ANOVA_ERR_NOMEM = -3,        /* device or host allocation failed */
+    ANOVA_ERR_CUDA = -4,         /* a CUDA call failed; the plan may be unusable */
+    ANOVA_ERR_BREAKDOWN = -5,    /* solver breakdown (reported in info, x still valid) */
+    ANOVA_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
+    ANOVA_ERR_NOT_FINITE = -7    /* a solver scalar became NaN or Inf */
+};
+
+/* Options of anova_plan_create; zero-initialise and set what you need. */
+typedef struct {
+    int precision;      /* enum anova_precision */
+    double eps;         /* target relative l2 error of F and F^H (0: default for the precision) */
+    int window_m_col;   /* window half-width along the fastest grid axis (0: auto) */
+    int window_m_row;   /* window half-width along the other axes (0: auto) */
+    double sigma;       /* minimal oversampling factor n_u / N_u (0: 2.0) */
+    int n_ctas;         /* persistent CTAs of the spreading/gathering kernels (0: auto) */
+} anova_plan_options;
+
+/*
+ * anova_plan_create -- build the term table, grids and window tables for a
+ * fixed node set (Sec. 3: the grouped index set of eq. (groupedset) and the
+ * block order of eq. (bananarama)).
+ *   out        : receives the plan handle (host pointer, required)
+ *   d          : spatial dimension, 1 <= d
+ *   M          : number of nodes, 0 <= M < 2^31
+ *   x_dev      : nodes [d][M] (device, plan's real type); copied into the plan
+ *   n_terms    : number of terms, >= 1
+ *   term_dims  : host [n_terms][3], see conventions
+ *   bandwidth  : host [n_terms], even N_u >= 2 for non-empty terms
+ *   opts       : host, may be NULL for defaults (FP32, eps 1e-5)
+ *   stream     : cudaStream_t used by every later call on this plan (NULL = legacy default)
+ * Errors: ANOVA_ERR_INVALID for bad sizes/terms, ANOVA_ERR_UNSUPPORTED for
+ * |u| > 3 or a grid that does not fit the kernels, ANOVA_ERR_NOMEM.
+ * Synchronises the stream before returning.
+ */
+int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, int n_terms,
+                      const int32_t *term_dims, const int32_t *bandwidth,
+                      const anova_plan_options *opts, void *stream);
+
+/* Release the plan and all device memory it owns.  NULL is a no-op. */
+void anova_plan_destroy(anova_plan_t plan);
+
+/* Number of coefficients |I_N(U)| = sum_u (N_u - 1)^{|u|} (Remark "cardinality"); -1 for NULL. */
+int64_t anova_num_coeffs(anova_plan_t plan);
+
+/* Offset and length of block u in the coefficient vector. */
+int anova_term_offset(anova_plan_t plan, int u, int64_t *off, int64_t *len);
+
+/* Oversampled grid size n_u and window half-widths (col, row) chosen for term u. */
+int anova_term_grid(anova_plan_t plan, int u, int *n, int *m_col, int *m_row);
+
+/*
+ * grouped_trafo -- f = F(X, I_N(U)) fhat  (Definition "grouped Fourier
+ * transform" and eq. (somafm), Sec. 3).
+ *   fhat_dev : [num_coeffs] complex (plan's vector type), read only
+ *   f_dev    : [M] complex, overwritten
+ * The two buffers must not overlap.
+ */
+int grouped_trafo(anova_plan_t plan, const void *fhat_dev, void *f_dev);
+
+/*
+ * grouped_adjoint -- fhat = F(X, I_N(U))^H y  (stacked adjoint after the
+ * error remark, Sec. 3).
+ *   y_dev    : [M] complex, read only
+ *   fhat_dev : [num_coeffs] complex, overwritten
+ */
+int grouped_adjoint(anova_plan_t plan, const void *y_dev, void *fhat_dev);
+
+/* Summary of a solve; fields a solver does not use are zero. */
+typedef struct {
+    int iterations;        /* iterations run (last lambda for paths) */
+    int status;            /* 0 ok, or an anova_status code (breakdown, not finite, ...) */
+    int stop_reason;       /* LSQR: 0 max_it, 1 breakdown, 2 residual test, 3 normal-eq test;
+                              FISTA: 0 max_it, 1 step tolerance */
+    int n_trafo;           /* grouped_trafo applications */
+    int n_adjoint;         /* grouped_adjoint applications */
+    int active_groups;     /* FISTA: groups with f_u != 0 at the end */
+    double rnorm;          /* LSQR: estimate of sqrt(||y - F f||^2 + 2 lam ||f||_W^2); FISTA: ||y - F f|| */
+    double arnorm;         /* LSQR: estimate of the normal-equation residual */
+    double objective;      /* FISTA: 1/2 ||y - F f||^2 + lam sum_u ||f_u||_W */
+    double L;              /* FISTA: final step constant */
+    double seconds;        /* device time of the solve (CUDA events) */
+} anova_solve_info;
+
+/*
+ * lsqr_solve -- minimiser of 1/2 ||y - F f||^2 + lambda f^H W f
+ * (eq. (new_min_prob), Sec. 4.1) by LSQR (Paige and Saunders 1982) on
+ * A = F W^{-1/2} with damping sqrt(2 lambda), started from f = 0.
+ * The regulariser of eq. (new_min_prob) has no factor 1/2, hence sqrt(2 lambda).
+ *   y_dev      : [M] complex
+ *   w_dev      : [num_coeffs] double weights omega_k >= 1 (W = diag(omega)), or NULL for W = I
+ *   lambda     : >= 0
+ *   max_it     : iteration cap (>= 1)
+ *   atol, btol : Paige--Saunders stopping tolerances (0 disables the tests)
+ *   fhat_dev   : [num_coeffs] complex, overwritten with the solution
+ *   info       : host, may be NULL
+ * Vector updates run in the plan's precision; the bidiagonalisation scalars
+ * (alpha, beta, rho, phi, c, s, norms) are FP64 on the device.  The iteration
+ * is driven on the device (no host round trip per iteration); the call
+ * returns after the solve has finished.
+ */
+int lsqr_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, double lambda,
+               int max_it, double atol, double btol, void *fhat_dev, anova_solve_info *info);
+
+/*
+ * fista_solve -- group lasso min 1/2 ||y - F f||^2 + lambda sum_u ||f_u||_{W_u}
+ * (eq. (alligatoah), Sec. 4.2) by Algorithm "FISTA for group lasso" along a
+ * warm-started lambda path (largest first, f_0 = 0 or fhat_path_dev[0] on entry
+ * when warm_start is set).
+ *   y_dev        : [M] complex
+ *   w_dev        : [num_coeffs] double weights, or NULL for W = I
+ *   lambdas      : host [n_lambda], any order (solved largest first)
+ *   max_it, tol  : per lambda; stop when ||f_k - f_{k-1}|| <= tol ||f_k||
+ *   step_mode    : 0 constant step L (Remark after the Algorithm), 1 backtracking
+ *   L0, eta      : step constant (constant mode: L; backtracking: L_0) and eta > 1;
+ *                  L0 <= 0 asks for 1.01 times a power-iteration estimate of ||F||^2
+ *   group_mask   : host [n_terms] uint8, 1 = group may be nonzero; NULL = all groups
+ *   fhat_path_dev: [n_lambda][num_coeffs] complex, solution per lambda in the
+ *                  order lambdas are given
+ *   info         : host [n_lambda] (may be NULL)
+ */
+int fista_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, const double *lambdas,
+                int n_lambda, int max_it, double tol, int step_mode, double L0, double eta,
+                const uint8_t *group_mask, int warm_start, void *fhat_path_dev,
+                anova_solve_info *info);
+
+/*
+ * Per-kernel timing (no counterpart in the paper; measurement support).
+ * anova_profile_enable(plan, 1) makes every later call record CUDA events on
+ * the plan's stream around each kernel it launches; anova_profile_read
+ * synchronises the stream and returns, for each stage s < *n_stages, the
+ * summed device milliseconds ms[s] and launch count launches[s] since the last
+ * reset (reset = 1 clears them after reading).  Stages:
+ *   0 trafo_pre (deconvolve + FFT), 1 gather, 2 spread, 3 reduce_partials,
+ *   4 adjoint_post (fold + FFT + deconvolve), 5 empty-set sum, 6 solver vector ops
+ * name_out (may be NULL) receives a static name per stage.
+ */
+int anova_profile_enable(anova_plan_t plan, int on);
+int anova_profile_read(anova_plan_t plan, double *ms, int64_t *launches, const char **names, int max_stages,
+                       int *n_stages, int reset);
+
+/* Human-readable name of a status code (static string). */
+const char *anova_status_string(int status);
+
+/* Library version string. */
+const char *anova_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANOVA_GFT_H */

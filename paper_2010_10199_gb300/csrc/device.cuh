@@ -1,0 +1,227 @@
+// Device helpers: window evaluation, bulk async copies with bounded mbarrier
+// waits, and the shared-memory mixed-radix FFT used for the oversampled grids.
+#pragma once
+
+#include "internal.cuh"
+
+namespace agft {
+
+// ---------------------------------------------------------------- windows --
+
+// Horner evaluation of a degree-7 polynomial held in registers.
+__device__ __forceinline__ float horner8(const float c[NCOEF], float v) {
+    float s = c[NCOEF - 1];
+#pragma unroll
+    for (int i = NCOEF - 2; i >= 0; --i) s = fmaf(s, v, c[i]);
+    return s;
+}
+
+// Direct evaluation of the normalised Kaiser--Bessel window at distance d
+// (grid units); used where no per-tap polynomial is kept in registers.
+__device__ __forceinline__ float kb_direct(float d, int m, float b, float inv_psi0) {
+    float s2 = fmaf(-d, d, (float)(m * m));
+    if (s2 <= 0.0f) return s2 == 0.0f ? b * (1.0f / 3.14159265358979f) * inv_psi0 : 0.0f;
+    float s = sqrtf(s2);
+    float bs = b * s;
+    float v;
+    if (bs < 1e-2f) {
+        v = b * (1.0f + bs * bs * (1.0f / 6.0f));
+    } else {
+        float e = expf(bs);
+        v = 0.5f * (e - 1.0f / e) / s;
+    }
+    return v * (1.0f / 3.14159265358979f) * inv_psi0;
+}
+
+__device__ __forceinline__ double kb_direct_d(double d, int m, double b, double inv_psi0) {
+    double s2 = fma(-d, d, (double)(m * m));
+    if (s2 <= 0.0) return s2 == 0.0 ? b / 3.141592653589793238 * inv_psi0 : 0.0;
+    double s = sqrt(s2);
+    return sinh(b * s) / (3.141592653589793238 * s) * inv_psi0;
+}
+
+// Grid position of a coordinate x in [-1/2, 1/2): t = (x + 1/2) n wrapped to
+// [0, n).  Returns floor(t) and writes tau = t - floor(t).
+__device__ __forceinline__ int grid_pos(float x, int n, float &tau) {
+    float t = (x + 0.5f) * (float)n;
+    float fl = floorf(t);
+    tau = t - fl;
+    int i = (int)fl;
+    if (i >= n) i -= n;   // x rounded up to 1/2
+    if (i < 0) i += n;
+    return i;
+}
+
+__device__ __forceinline__ int grid_pos_d(double x, int n, double &tau) {
+    double t = (x + 0.5) * (double)n;
+    double fl = floor(t);
+    tau = t - fl;
+    int i = (int)fl;
+    if (i >= n) i -= n;
+    if (i < 0) i += n;
+    return i;
+}
+
+__device__ __forceinline__ int wrap(int i, int n) {
+    i = i < 0 ? i + n : i;
+    return i >= n ? i - n : i;
+}
+
+// ------------------------------------------------------- async bulk copies --
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy (16-byte aligned, size multiple of 16), completion
+// counted on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait for the mbarrier phase with parity `parity`.  Gives up after
+// `limit` polls, records `code` in *err and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code,
+                                          long long limit = (1LL << 22)) {
+    uint32_t a = smem_addr(bar);
+    for (long long it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    if (err) atomicCAS(err, 0, code);
+    return false;
+}
+
+// ----------------------------------------------------------- shared FFT ---
+
+// Mixed-radix Stockham FFT over a batch of lines held in shared memory.
+// Line l, element i lives at base[l * lstride + i * estride] in both ping-pong
+// buffers.  Computes X[q] = sum_i x[i] exp(sign 2 pi i i q / n) (unnormalised).
+// Radices 4, 2, 3, 5.  All threads of the block must call it; returns the
+// buffer (0 = a, 1 = b) that holds the result.
+template <typename C, typename R>
+struct CplxOps;
+
+template <>
+struct CplxOps<float2, float> {
+    static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
+};
+template <>
+struct CplxOps<double2, double> {
+    static __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
+};
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+__host__ __device__ inline int fft_radices(int n, int *rad) {
+    int k = 0;
+    while (n % 4 == 0) { rad[k++] = 4; n /= 4; }
+    while (n % 2 == 0) { rad[k++] = 2; n /= 2; }
+    while (n % 3 == 0) { rad[k++] = 3; n /= 3; }
+    while (n % 5 == 0) { rad[k++] = 5; n /= 5; }
+    return n == 1 ? k : -1;
+}
+
+template <typename C, typename R>
+__device__ int smem_fft(C *a, C *b, int n, int nlines, int lstride, int estride, int sign) {
+    using O = CplxOps<C, R>;
+    int rad[24];
+    int ns = fft_radices(n, rad);
+    C *src = a, *dst = b;
+    int which = 0;
+    int Ns = 1;
+    for (int s = 0; s < ns; ++s) {
+        const int Rr = rad[s];
+        const int nb = n / Rr;
+        for (int w = threadIdx.x; w < nlines * nb; w += blockDim.x) {
+            const int l = w / nb, j = w - l * nb;
+            const C *in = src + (size_t)l * lstride;
+            C *out = dst + (size_t)l * lstride;
+            C v[5];
+            const int jm = j % Ns;
+            // twiddles exp(sign 2 pi i r jm / (Ns Rr))
+            for (int r = 0; r < Rr; ++r) {
+                C x = in[(size_t)(j + r * nb) * estride];
+                if (r && jm) {
+                    R sn, cs;
+                    O::sincospi_((R)(2 * sign * r * jm) / (R)(Ns * Rr), &sn, &cs);
+                    x = cmul(x, O::mk(cs, sn));
+                }
+                v[r] = x;
+            }
+            C V[5];
+            if (Rr == 2) {
+                V[0] = O::mk(v[0].x + v[1].x, v[0].y + v[1].y);
+                V[1] = O::mk(v[0].x - v[1].x, v[0].y - v[1].y);
+            } else if (Rr == 4) {
+                C s0 = O::mk(v[0].x + v[2].x, v[0].y + v[2].y);
+                C d0 = O::mk(v[0].x - v[2].x, v[0].y - v[2].y);
+                C s1 = O::mk(v[1].x + v[3].x, v[1].y + v[3].y);
+                C d1 = O::mk(v[1].x - v[3].x, v[1].y - v[3].y);
+                // multiply d1 by (sign) i
+                C jd1 = sign > 0 ? O::mk(-d1.y, d1.x) : O::mk(d1.y, -d1.x);
+                V[0] = O::mk(s0.x + s1.x, s0.y + s1.y);
+                V[2] = O::mk(s0.x - s1.x, s0.y - s1.y);
+                V[1] = O::mk(d0.x + jd1.x, d0.y + jd1.y);
+                V[3] = O::mk(d0.x - jd1.x, d0.y - jd1.y);
+            } else {
+                for (int q = 0; q < Rr; ++q) {
+                    C acc = v[0];
+                    for (int r = 1; r < Rr; ++r) {
+                        R sn, cs;
+                        O::sincospi_((R)(2 * sign * ((r * q) % Rr)) / (R)Rr, &sn, &cs);
+                        C t = cmul(v[r], O::mk(cs, sn));
+                        acc.x += t.x;
+                        acc.y += t.y;
+                    }
+                    V[q] = acc;
+                }
+            }
+            const int idxD = (j / Ns) * Ns * Rr + jm;
+            for (int r = 0; r < Rr; ++r) out[(size_t)(idxD + r * Ns) * estride] = V[r];
+        }
+        __syncthreads();
+        C *t = src;
+        src = dst;
+        dst = t;
+        which ^= 1;
+        Ns *= Rr;
+    }
+    return which;
+}
+
+}  // namespace agft

@@ -1,0 +1,152 @@
+// Internal definitions shared by the CUDA translation units of the library.
+//
+// Method: grouped Fourier transform of Sec. 3 (Definition "grouped Fourier
+// transform", identity eq. (somafm), stacked adjoint), evaluated per ANOVA term
+// with an NFFT: deconvolution by the window's Fourier coefficients, an
+// oversampled FFT, and a Kaiser--Bessel window gather (forward) or spread
+// (adjoint).  The window is
+//     psi(d) = sinh(b sqrt(m^2 - d^2)) / (pi sqrt(m^2 - d^2)),  |d| <= m,
+// in grid units d = n x - q, with b = pi (2 - 1/sigma), sigma = n/N, and
+// Fourier transform (1/n) I_0(m sqrt(b^2 - (2 pi k / n)^2)) of psi(n x).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "anova_gft.h"
+
+namespace agft {
+
+constexpr int MAX_ORDER = 3;
+constexpr int MAXM = 8;          // largest window half-width
+constexpr int NCOEF = 8;         // coefficients of the per-tap polynomial (degree 7)
+constexpr int GATHER_THREADS = 256;
+constexpr int PTS_PER_HALF = 16; // points per half-warp in the gather tile
+constexpr int GATHER_TILE = (GATHER_THREADS / 16) * PTS_PER_HALF;  // 256 points
+constexpr int SPREAD_THREADS = 256;
+constexpr int MAX_SMEM = 227 * 1024;
+
+// One window shape (half-width m, oversampling sigma).  Tap j of a node with
+// grid position t = n x sits at grid index floor(t) - m + 1 + j and has weight
+// psi(tau + m - 1 - j) / psi(0), tau = t - floor(t); the weight is stored as a
+// degree-7 polynomial in v = 2 tau - 1 (Chebyshev interpolation, monomial form).
+struct Window {
+    float c[2 * MAXM][NCOEF];
+    int m;
+    float b;          // shape parameter pi (2 - 1/sigma)
+    float inv_psi0;   // 1 / psi(0)
+    double bd, inv_psi0d;
+};
+
+// A term in kernel schedule order.  Grid layout: erows x stride (complex
+// elements), the last coordinate of the term along a row.  Orders 1 and 2
+// store halos so that a window never wraps: periodic column q sits at stored
+// column q + hc (hc = m_col - 1) and the stored columns q + hc +- n repeat it;
+// order-2 rows likewise with hr = m_row - 1.  Order-3 grids have no halo: the
+// row index is i_first * n + i_second and all indices wrap modulo n.  The row
+// stride is = 8 (mod 16) complex elements, so two consecutive rows of eight
+// columns fall in complementary shared-memory bank halves.
+struct Term {
+    int order;          // 1..3 (the empty set is handled separately)
+    int col;            // coordinate along the row
+    int row0, row1;     // other coordinates (-1 if absent)
+    int N, n, stride;
+    int rows;           // n^(order-1)
+    int wc, wr;         // window ids: column axis, row axes
+    int mc, mr;         // their half-widths
+    int new_rowgroup;   // 1 if the row weights cached by the gather must be recomputed
+    int hr, hc;         // halo widths (rows, columns): stored index = periodic index + halo
+    int erows;          // stored rows (order 2: n + 2 hr + 1; order 1: 1; order 3: n^2, no halo)
+    int pad_;
+    long long grid_off;   // element offset in the grid buffer
+    long long grid_bytes; // bytes (multiple of 16)
+    long long coef_off;   // offset in the coefficient vector
+    long long coef_len;
+    int dc_off, dr_off;   // offsets of the column / row deconvolution factors
+    int user_index;
+    int pad2_;
+};
+
+// Device-visible view of a plan (passed by value to kernels).
+struct DevPlan {
+    int d;
+    long long M;
+    int n_terms;              // scheduled (non-empty) terms
+    int n_empty;              // empty-set terms
+    const float *x;           // [d][M] FP32 nodes (or null)
+    const double *xd;         // [d][M] FP64 nodes (or null)
+    const Term *terms;
+    const Window *windows;
+    const float *deconv;      // deconvolution factors
+    const double *deconvd;
+    const long long *empty_off;  // coefficient offsets of the empty terms
+    long long grid_elems;     // total grid elements (complex)
+    long long max_grid_bytes;
+    int *err;                 // device error word (bounded waits)
+};
+
+constexpr int N_STAGES = 7;
+struct Profiler;   // per-stage CUDA-event timing (profile.cu)
+
+struct Plan {
+    Profiler *prof;
+    int device;
+    cudaStream_t stream;
+    int precision;
+    int d;
+    long long M;
+    int n_user_terms;
+    long long n_coeffs;
+    // host copies
+    Term *h_terms;
+    int n_terms;
+    int n_empty;
+    long long *h_user_off;  // per user term: coefficient offset
+    long long *h_user_len;
+    int *h_user_n, *h_user_mc, *h_user_mr;
+    // device buffers
+    void *x;                // FP32 or FP64 nodes [d][M]
+    Term *terms;
+    Window *windows;
+    int n_windows;
+    float *deconv;
+    double *deconvd;
+    long long *empty_off;
+    void *grids;            // complex grid buffer (precision dependent)
+    long long grid_elems;
+    long long max_grid_bytes;
+    int max_fft_elems;      // largest n^order
+    void *partials;         // adjoint partial grids [spread_ctas][grid_elems]
+    int spread_ctas;
+    int gather_ctas;
+    int *err;
+    void *scratch;          // reduction scratch
+    size_t scratch_bytes;
+    int sm_count;
+};
+
+DevPlan dev_view(const Plan &p);
+
+// stage timing: call stage_begin before and stage_end after a kernel launch
+void stage_begin(Plan &p, int stage);
+void stage_end(Plan &p, int stage);
+void profiler_free(Plan &p);
+enum { ST_PRE = 0, ST_GATHER = 1, ST_SPREAD = 2, ST_REDUCE = 3, ST_POST = 4, ST_SUMY = 5, ST_SOLVER = 6 };
+
+// kernels launched by the entry points (trafo.cu / adjoint.cu)
+int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f);
+int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
+
+// status from a CUDA error
+inline int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return ANOVA_OK;
+    if (e == cudaErrorMemoryAllocation) return ANOVA_ERR_NOMEM;
+    return ANOVA_ERR_CUDA;
+}
+
+}  // namespace agft
+
+struct anova_plan_s {
+    agft::Plan p;
+};

@@ -1,0 +1,502 @@
+// Plan construction: term schedule, grid layout, window tables and
+// deconvolution factors; the C-ABI bookkeeping entry points.
+//
+// Grouped index set and block order: eq. (groupedset) and (bananarama), Sec. 3;
+// cardinality (N_u - 1)^{|u|}: Remark "cardinality", Sec. 2.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace agft {
+
+// ------------------------------------------------------------ host maths --
+
+// Modified Bessel function I_0 by its power series sum (z/2)^{2j} / (j!)^2.
+static double bessel_i0(double z) {
+    double q = 0.25 * z * z, term = 1.0, sum = 1.0;
+    for (int j = 1; j < 500; ++j) {
+        term *= q / ((double)j * (double)j);
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+// psi(d) = sinh(b sqrt(m^2 - d^2)) / (pi sqrt(m^2 - d^2)), continuous at |d| = m.
+static double kb_window(double d, int m, double b) {
+    double s2 = (double)m * m - d * d;
+    if (s2 < 0) return 0.0;
+    double s = std::sqrt(s2);
+    if (b * s < 1e-8) return b / M_PI;
+    return std::sinh(b * s) / (M_PI * s);
+}
+
+// Deconvolution factor psi(0) / I_0(m sqrt(b^2 - (2 pi k / n)^2)): the inverse of
+// n times the Fourier coefficient of the normalised window psi(n x) / psi(0).
+static double deconv_factor(int k, int n, int m, double b) {
+    double a = 2.0 * M_PI * k / n;
+    double r = b * b - a * a;
+    double psi0 = std::sinh(b * m) / (M_PI * m);
+    return psi0 / bessel_i0(m * std::sqrt(r > 0 ? r : 0.0));
+}
+
+// Degree-7 Chebyshev interpolant of each tap weight as a function of v = 2 tau - 1.
+static void window_polys(Window &w, int m, double b) {
+    const int P = NCOEF;
+    double psi0 = kb_window(0.0, m, b);
+    for (int j = 0; j < 2 * MAXM; ++j)
+        for (int i = 0; i < P; ++i) w.c[j][i] = 0.0f;
+    for (int j = 0; j < 2 * m; ++j) {
+        double fv[NCOEF], a[NCOEF];
+        for (int i = 0; i < P; ++i) {
+            double v = std::cos(M_PI * (i + 0.5) / P);
+            double tau = 0.5 * (v + 1.0);
+            fv[i] = kb_window(tau + m - 1 - j, m, b) / psi0;
+        }
+        for (int k = 0; k < P; ++k) {
+            double s = 0;
+            for (int i = 0; i < P; ++i) s += fv[i] * std::cos(M_PI * k * (i + 0.5) / P);
+            a[k] = (k == 0 ? 1.0 : 2.0) * s / P;
+        }
+        // sum a_k T_k(v) -> monomials, T_{k+1} = 2 v T_k - T_{k-1}
+        double Tm1[NCOEF] = {0}, T0[NCOEF] = {0}, mono[NCOEF] = {0};
+        T0[0] = 1.0;
+        double T1[NCOEF] = {0};
+        T1[1] = 1.0;
+        for (int i = 0; i < P; ++i) mono[i] += a[0] * T0[i];
+        if (P > 1)
+            for (int i = 0; i < P; ++i) mono[i] += a[1] * T1[i];
+        for (int i = 0; i < P; ++i) Tm1[i] = T0[i];
+        for (int i = 0; i < P; ++i) T0[i] = T1[i];
+        for (int k = 2; k < P; ++k) {
+            double Tn[NCOEF] = {0};
+            for (int i = 0; i < P; ++i) {
+                if (i > 0) Tn[i] += 2.0 * T0[i - 1];
+                Tn[i] -= Tm1[i];
+            }
+            for (int i = 0; i < P; ++i) mono[i] += a[k] * Tn[i];
+            for (int i = 0; i < P; ++i) {
+                Tm1[i] = T0[i];
+                T0[i] = Tn[i];
+            }
+        }
+        for (int i = 0; i < P; ++i) w.c[j][i] = (float)mono[i];
+    }
+    w.m = m;
+    w.b = (float)b;
+    w.bd = b;
+    w.inv_psi0 = (float)(1.0 / psi0);
+    w.inv_psi0d = 1.0 / psi0;
+}
+
+static bool smooth235(int n) {
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+static int fft_size(int N, double sigma) {
+    int n = (int)std::ceil(sigma * N - 1e-9);
+    if (n < N + 2) n = N + 2;
+    if (n % 2) ++n;
+    while (!smooth235(n)) n += 2;
+    return n;
+}
+
+static int row_stride(int n) {
+    int s = n;
+    while (s % 16 != 8) ++s;
+    return s;
+}
+
+__global__ void wrap_nodes_f32(const float *in, float *out, long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        float v = in[i];
+        v = v - floorf(v + 0.5f);   // into [-1/2, 1/2)
+        if (v >= 0.5f) v -= 1.0f;
+        out[i] = v;
+    }
+}
+
+__global__ void wrap_nodes_f64(const double *in, double *out, long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        double v = in[i];
+        v = v - floor(v + 0.5);
+        if (v >= 0.5) v -= 1.0;
+        out[i] = v;
+    }
+}
+
+DevPlan dev_view(const Plan &p) {
+    DevPlan v;
+    v.d = p.d;
+    v.M = p.M;
+    v.n_terms = p.n_terms;
+    v.n_empty = p.n_empty;
+    v.x = p.precision == ANOVA_PREC_F64 ? nullptr : (const float *)p.x;
+    v.xd = p.precision == ANOVA_PREC_F64 ? (const double *)p.x : nullptr;
+    v.terms = p.terms;
+    v.windows = p.windows;
+    v.deconv = p.deconv;
+    v.deconvd = p.deconvd;
+    v.empty_off = p.empty_off;
+    v.grid_elems = p.grid_elems;
+    v.max_grid_bytes = p.max_grid_bytes;
+    v.err = p.err;
+    return v;
+}
+
+static void free_plan(Plan &p) {
+    profiler_free(p);
+    void *bufs[] = {p.x, p.terms, p.windows, p.deconv, p.deconvd, p.empty_off, p.grids, p.partials,
+                    p.err, p.scratch};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete[] p.h_terms;
+    delete[] p.h_user_off;
+    delete[] p.h_user_len;
+    delete[] p.h_user_n;
+    delete[] p.h_user_mc;
+    delete[] p.h_user_mr;
+}
+
+}  // namespace agft
+
+using namespace agft;
+
+extern "C" {
+
+const char *anova_status_string(int s) {
+    switch (s) {
+        case ANOVA_OK: return "ok";
+        case ANOVA_ERR_INVALID: return "invalid argument";
+        case ANOVA_ERR_UNSUPPORTED: return "unsupported configuration";
+        case ANOVA_ERR_NOMEM: return "out of memory";
+        case ANOVA_ERR_CUDA: return "CUDA error";
+        case ANOVA_ERR_BREAKDOWN: return "solver breakdown";
+        case ANOVA_ERR_TIMEOUT: return "device wait timed out";
+        case ANOVA_ERR_NOT_FINITE: return "non-finite solver scalar";
+        default: return "unknown status";
+    }
+}
+
+const char *anova_version(void) { return "anova-gft 0.1 (sm_103a)"; }
+
+int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, int n_terms,
+                      const int32_t *term_dims, const int32_t *bandwidth, const anova_plan_options *opts,
+                      void *stream) {
+    if (!out) return ANOVA_ERR_INVALID;
+    *out = nullptr;
+    if (d < 1 || M < 0 || M >= (1LL << 31) || n_terms < 1 || !term_dims || !bandwidth) return ANOVA_ERR_INVALID;
+    if (M > 0 && !x_dev) return ANOVA_ERR_INVALID;
+    anova_plan_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.precision < ANOVA_PREC_F32 || o.precision > ANOVA_PREC_F64) return ANOVA_ERR_INVALID;
+    if (o.precision != ANOVA_PREC_F32) return ANOVA_ERR_UNSUPPORTED;   // 16-bit and FP64 grids: later
+    if (o.eps <= 0) o.eps = 1e-5;
+    if (o.sigma <= 0) o.sigma = 2.0;
+    if (o.sigma < 1.5 || o.sigma > 8) return ANOVA_ERR_INVALID;
+
+    // validate terms
+    for (int i = 0; i < n_terms; ++i) {
+        const int32_t *t = term_dims + 3 * i;
+        int ord = 0;
+        for (int j = 0; j < 3; ++j) {
+            if (t[j] < 0) {
+                for (int l = j; l < 3; ++l)
+                    if (t[l] >= 0) return ANOVA_ERR_INVALID;
+                break;
+            }
+            if (t[j] >= d) return ANOVA_ERR_INVALID;
+            if (j > 0 && t[j] <= t[j - 1]) return ANOVA_ERR_INVALID;
+            ++ord;
+        }
+        if (ord > 0 && (bandwidth[i] < 2 || bandwidth[i] % 2)) return ANOVA_ERR_INVALID;
+        if (ord > 0 && bandwidth[i] > 4096) return ANOVA_ERR_UNSUPPORTED;
+    }
+
+    anova_plan_s *h = new (std::nothrow) anova_plan_s;
+    if (!h) return ANOVA_ERR_NOMEM;
+    std::memset(&h->p, 0, sizeof(Plan));
+    Plan &p = h->p;
+    p.stream = (cudaStream_t)stream;
+    p.precision = o.precision;
+    p.d = d;
+    p.M = M;
+    p.n_user_terms = n_terms;
+    cudaGetDevice(&p.device);
+    cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, p.device);
+    if (p.sm_count <= 0) p.sm_count = 152;
+
+    int mc = o.window_m_col > 0 ? o.window_m_col : 4;
+    int mr = o.window_m_row > 0 ? o.window_m_row : (o.eps >= 5e-6 ? 3 : 4);
+    if (mc != 4) {   // eight column lanes per row segment
+        free_plan(p);
+        delete h;
+        return ANOVA_ERR_UNSUPPORTED;
+    }
+    if (mr < 2 || mr > 4) {
+        free_plan(p);
+        delete h;
+        return ANOVA_ERR_UNSUPPORTED;
+    }
+
+    // user layout
+    p.h_user_off = new long long[n_terms];
+    p.h_user_len = new long long[n_terms];
+    p.h_user_n = new int[n_terms];
+    p.h_user_mc = new int[n_terms];
+    p.h_user_mr = new int[n_terms];
+    long long off = 0;
+    std::vector<int> order(n_terms);
+    std::vector<long long> empties;
+    for (int i = 0; i < n_terms; ++i) {
+        const int32_t *t = term_dims + 3 * i;
+        int ord = (t[0] >= 0) + (t[1] >= 0) + (t[2] >= 0);
+        order[i] = ord;
+        long long len = 1;
+        for (int j = 0; j < ord; ++j) len *= (bandwidth[i] - 1);
+        p.h_user_off[i] = off;
+        p.h_user_len[i] = len;
+        p.h_user_n[i] = ord ? fft_size(bandwidth[i], o.sigma) : 0;
+        p.h_user_mc[i] = ord ? mc : 0;
+        p.h_user_mr[i] = ord > 1 ? mr : 0;
+        if (ord == 0) empties.push_back(off);
+        off += len;
+    }
+    p.n_coeffs = off;
+    p.n_empty = (int)empties.size();
+
+    // schedule: by first coordinate, then order, then the remaining coordinates
+    std::vector<int> sched;
+    for (int i = 0; i < n_terms; ++i)
+        if (order[i] > 0) sched.push_back(i);
+    std::stable_sort(sched.begin(), sched.end(), [&](int a, int b) {
+        const int32_t *ta = term_dims + 3 * a, *tb = term_dims + 3 * b;
+        if (ta[0] != tb[0]) return ta[0] < tb[0];
+        if (order[a] != order[b]) return order[a] < order[b];
+        if (ta[1] != tb[1]) return ta[1] < tb[1];
+        return ta[2] < tb[2];
+    });
+    p.n_terms = (int)sched.size();
+    p.h_terms = new Term[p.n_terms > 0 ? p.n_terms : 1];
+
+    // windows (dedupe on m, n, N) and deconvolution tables
+    std::vector<Window> wins;
+    std::vector<int> wkey_m, wkey_n, wkey_N;
+    auto get_window = [&](int m, int n, int N) {
+        for (size_t i = 0; i < wins.size(); ++i)
+            if (wkey_m[i] == m && wkey_n[i] == n && wkey_N[i] == N) return (int)i;
+        Window w;
+        std::memset(&w, 0, sizeof(w));
+        window_polys(w, m, M_PI * (2.0 - (double)N / n));
+        wins.push_back(w);
+        wkey_m.push_back(m);
+        wkey_n.push_back(n);
+        wkey_N.push_back(N);
+        return (int)wins.size() - 1;
+    };
+    std::vector<float> dec;
+    std::vector<double> decd;
+    long long goff = 0, maxbytes = 16;
+    int max_fft = 1;
+    int status = ANOVA_OK;
+    for (int s = 0; s < p.n_terms; ++s) {
+        int i = sched[s];
+        const int32_t *t = term_dims + 3 * i;
+        Term T;
+        std::memset(&T, 0, sizeof(T));
+        T.order = order[i];
+        T.col = t[T.order - 1];
+        T.row0 = T.order >= 2 ? t[0] : -1;
+        T.row1 = T.order >= 3 ? t[1] : -1;
+        T.N = bandwidth[i];
+        T.n = p.h_user_n[i];
+        T.rows = 1;
+        for (int j = 1; j < T.order; ++j) T.rows *= T.n;
+        T.mc = mc;
+        T.mr = T.order > 1 ? mr : 0;
+        if (T.order <= 2) {
+            T.hc = T.mc - 1;
+            T.hr = T.order == 2 ? T.mr - 1 : 0;
+            T.erows = T.order == 2 ? T.n + 2 * T.hr + 1 : 1;
+            T.stride = row_stride(T.n + 2 * T.hc + 1);
+        } else {
+            T.hc = T.hr = 0;
+            T.erows = T.rows;
+            T.stride = row_stride(T.n);
+        }
+        T.wc = get_window(T.mc, T.n, T.N);
+        T.wr = T.order > 1 ? get_window(T.mr, T.n, T.N) : T.wc;
+        T.grid_off = goff;
+        long long elems = (long long)T.erows * T.stride;
+        elems = (elems + 1) & ~1LL;   // 16-byte multiple
+        T.grid_bytes = elems * 8;
+        goff += elems;
+        maxbytes = std::max(maxbytes, T.grid_bytes);
+        long long fe = 1;
+        for (int j = 0; j < T.order; ++j) fe *= T.n;
+        if (fe * 16 > 200 * 1024 || T.grid_bytes > 100 * 1024) status = ANOVA_ERR_UNSUPPORTED;
+        max_fft = (int)std::max<long long>(max_fft, fe);
+        T.coef_off = p.h_user_off[i];
+        T.coef_len = p.h_user_len[i];
+        T.user_index = i;
+        // deconvolution factors for k in I_N \ {0} (column window, then row window)
+        double bc = M_PI * (2.0 - (double)T.N / T.n);
+        T.dc_off = (int)dec.size();
+        for (int q = 0; q < T.N - 1; ++q) {
+            int k = q < T.N / 2 ? q - T.N / 2 : q - T.N / 2 + 1;
+            double v = deconv_factor(k, T.n, T.mc, bc);
+            dec.push_back((float)v);
+            decd.push_back(v);
+        }
+        T.dr_off = T.dc_off;
+        if (T.order > 1) {
+            T.dr_off = (int)dec.size();
+            for (int q = 0; q < T.N - 1; ++q) {
+                int k = q < T.N / 2 ? q - T.N / 2 : q - T.N / 2 + 1;
+                double v = deconv_factor(k, T.n, T.mr, bc);
+                dec.push_back((float)v);
+                decd.push_back(v);
+            }
+        }
+        p.h_terms[s] = T;
+    }
+    // row groups: order-2 terms sharing the first coordinate and row window
+    for (int s = 0; s < p.n_terms; ++s) {
+        Term &T = p.h_terms[s];
+        T.new_rowgroup = 1;
+        if (T.order == 2 && s > 0) {
+            const Term &P = p.h_terms[s - 1];
+            if (P.order == 2 && P.row0 == T.row0 && P.wr == T.wr && P.n == T.n) T.new_rowgroup = 0;
+        }
+    }
+    if (status != ANOVA_OK) {
+        free_plan(p);
+        delete h;
+        return status;
+    }
+    p.grid_elems = goff;
+    p.max_grid_bytes = maxbytes;
+    p.max_fft_elems = max_fft;
+    p.n_windows = (int)wins.size();
+    for (int i = 0; i < n_terms; ++i) {
+        (void)i;
+    }
+
+    // device allocations
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) {
+        if (r != cudaSuccess && e == cudaSuccess) e = r;
+    };
+    size_t xbytes = (size_t)d * M * (p.precision == ANOVA_PREC_F64 ? 8 : 4);
+    if (xbytes) chk(cudaMalloc(&p.x, xbytes));
+    chk(cudaMalloc(&p.terms, sizeof(Term) * std::max(1, p.n_terms)));
+    chk(cudaMalloc(&p.windows, sizeof(Window) * std::max<size_t>(1, wins.size())));
+    chk(cudaMalloc(&p.deconv, sizeof(float) * std::max<size_t>(1, dec.size())));
+    chk(cudaMalloc(&p.deconvd, sizeof(double) * std::max<size_t>(1, decd.size())));
+    chk(cudaMalloc(&p.empty_off, sizeof(long long) * std::max<size_t>(1, empties.size())));
+    chk(cudaMalloc(&p.grids, (size_t)std::max<long long>(1, p.grid_elems) * 8));
+    chk(cudaMalloc(&p.err, sizeof(int) * 4));
+    // adjoint partial grids
+    long long per_cta = 2048;
+    int sc = (int)std::min<long long>((long long)p.sm_count, std::max<long long>(1, (M + per_cta - 1) / per_cta));
+    if (o.n_ctas > 0) sc = o.n_ctas;
+    p.spread_ctas = sc;
+    p.gather_ctas = (int)std::min<long long>((long long)p.sm_count,
+                                             std::max<long long>(1, (M + GATHER_TILE - 1) / GATHER_TILE));
+    if (e == cudaSuccess && p.n_terms > 0)
+        chk(cudaMalloc(&p.partials, (size_t)sc * (size_t)p.grid_elems * 8));
+    p.scratch_bytes = 1 << 20;
+    chk(cudaMalloc(&p.scratch, p.scratch_bytes));
+    if (e != cudaSuccess) {
+        free_plan(p);
+        delete h;
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    chk(cudaMemcpyAsync(p.terms, p.h_terms, sizeof(Term) * p.n_terms, cudaMemcpyHostToDevice, p.stream));
+    if (!wins.empty())
+        chk(cudaMemcpyAsync(p.windows, wins.data(), sizeof(Window) * wins.size(), cudaMemcpyHostToDevice,
+                            p.stream));
+    if (!dec.empty()) {
+        chk(cudaMemcpyAsync(p.deconv, dec.data(), sizeof(float) * dec.size(), cudaMemcpyHostToDevice, p.stream));
+        chk(cudaMemcpyAsync(p.deconvd, decd.data(), sizeof(double) * decd.size(), cudaMemcpyHostToDevice,
+                            p.stream));
+    }
+    if (!empties.empty())
+        chk(cudaMemcpyAsync(p.empty_off, empties.data(), sizeof(long long) * empties.size(),
+                            cudaMemcpyHostToDevice, p.stream));
+    chk(cudaMemsetAsync(p.err, 0, sizeof(int) * 4, p.stream));
+    if (xbytes) {
+        long long total = (long long)d * M;
+        int blocks = (int)std::min<long long>(4096, (total + 255) / 256);
+        if (p.precision == ANOVA_PREC_F64)
+            wrap_nodes_f64<<<blocks, 256, 0, p.stream>>>((const double *)x_dev, (double *)p.x, total);
+        else
+            wrap_nodes_f32<<<blocks, 256, 0, p.stream>>>((const float *)x_dev, (float *)p.x, total);
+        chk(cudaGetLastError());
+    }
+    chk(cudaStreamSynchronize(p.stream));
+    // wins vector is copied; keep host term table
+    if (e != cudaSuccess) {
+        free_plan(p);
+        delete h;
+        return cuda_status(e);
+    }
+    *out = h;
+    return ANOVA_OK;
+}
+
+void anova_plan_destroy(anova_plan_t plan) {
+    if (!plan) return;
+    cudaStreamSynchronize(plan->p.stream);
+    free_plan(plan->p);
+    delete plan;
+}
+
+int64_t anova_num_coeffs(anova_plan_t plan) { return plan ? plan->p.n_coeffs : -1; }
+
+int anova_term_offset(anova_plan_t plan, int u, int64_t *off, int64_t *len) {
+    if (!plan || u < 0 || u >= plan->p.n_user_terms) return ANOVA_ERR_INVALID;
+    if (off) *off = plan->p.h_user_off[u];
+    if (len) *len = plan->p.h_user_len[u];
+    return ANOVA_OK;
+}
+
+int anova_term_grid(anova_plan_t plan, int u, int *n, int *m_col, int *m_row) {
+    if (!plan || u < 0 || u >= plan->p.n_user_terms) return ANOVA_ERR_INVALID;
+    if (n) *n = plan->p.h_user_n[u];
+    if (m_col) *m_col = plan->p.h_user_mc[u];
+    if (m_row) *m_row = plan->p.h_user_mr[u];
+    return ANOVA_OK;
+}
+
+int grouped_trafo(anova_plan_t plan, const void *fhat_dev, void *f_dev) {
+    if (!plan) return ANOVA_ERR_INVALID;
+    Plan &p = plan->p;
+    if (p.M > 0 && !f_dev) return ANOVA_ERR_INVALID;
+    if (p.n_coeffs > 0 && !fhat_dev) return ANOVA_ERR_INVALID;
+    if (p.M == 0) return ANOVA_OK;
+    return launch_trafo_f32(p, (const float2 *)fhat_dev, (float2 *)f_dev);
+}
+
+int grouped_adjoint(anova_plan_t plan, const void *y_dev, void *fhat_dev) {
+    if (!plan) return ANOVA_ERR_INVALID;
+    Plan &p = plan->p;
+    if (!fhat_dev) return ANOVA_ERR_INVALID;
+    if (p.M > 0 && !y_dev) return ANOVA_ERR_INVALID;
+    return launch_adjoint_f32(p, (const float2 *)y_dev, (float2 *)fhat_dev);
+}
+
+}  // extern "C"

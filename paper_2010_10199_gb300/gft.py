@@ -1,0 +1,272 @@
+"""ctypes binding of the C ABI in ``include/anova_gft.h`` (argument marshalling only).
+
+Every computation runs in ``libanova_gft.so``; this module converts Python
+arguments to the C types and checks status codes.  There is no fallback: if
+the shared library is missing or cannot be loaded, every call raises.
+
+The raw entry points keep the C names (``anova_plan_create``, ``grouped_trafo``,
+``grouped_adjoint``, ``lsqr_solve``, ``fista_solve``, ...).  ``Plan`` is a small
+convenience wrapper that takes torch CUDA tensors and passes their device
+pointers and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libanova_gft.so")
+
+PREC_F32, PREC_BF16, PREC_F16, PREC_F64 = 0, 1, 2, 3
+
+_lib = None
+
+
+class AnovaError(RuntimeError):
+    def __init__(self, fn: str, status: int, text: str):
+        super().__init__(f"{fn} failed: {text} ({status})")
+        self.status = status
+
+
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("eps", ctypes.c_double), ("window_m_col", ctypes.c_int),
+                ("window_m_row", ctypes.c_int), ("sigma", ctypes.c_double), ("n_ctas", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("stop_reason", ctypes.c_int),
+                ("n_trafo", ctypes.c_int), ("n_adjoint", ctypes.c_int), ("active_groups", ctypes.c_int),
+                ("rnorm", ctypes.c_double), ("arnorm", ctypes.c_double), ("objective", ctypes.c_double),
+                ("L", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load libanova_gft.so (raises if it is missing: there is no CPU path)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(p)
+    vp, i32p, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+    lib.anova_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int64, vp, ctypes.c_int,
+                                      i32p, i32p, ctypes.POINTER(PlanOptions), vp]
+    lib.anova_plan_create.restype = ctypes.c_int
+    lib.anova_plan_destroy.argtypes = [vp]
+    lib.anova_plan_destroy.restype = None
+    lib.anova_num_coeffs.argtypes = [vp]
+    lib.anova_num_coeffs.restype = ctypes.c_int64
+    lib.anova_term_offset.argtypes = [vp, ctypes.c_int, i64p, i64p]
+    lib.anova_term_offset.restype = ctypes.c_int
+    lib.anova_term_grid.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]
+    lib.anova_term_grid.restype = ctypes.c_int
+    lib.grouped_trafo.argtypes = [vp, vp, vp]
+    lib.grouped_trafo.restype = ctypes.c_int
+    lib.grouped_adjoint.argtypes = [vp, vp, vp]
+    lib.grouped_adjoint.restype = ctypes.c_int
+    lib.lsqr_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp,
+                               ctypes.POINTER(SolveInfo)]
+    lib.lsqr_solve.restype = ctypes.c_int
+    lib.fista_solve.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, vp, ctypes.POINTER(SolveInfo)]
+    lib.fista_solve.restype = ctypes.c_int
+    lib.anova_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.anova_profile_enable.restype = ctypes.c_int
+    lib.anova_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_char_p), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.c_int]
+    lib.anova_profile_read.restype = ctypes.c_int
+    lib.anova_status_string.argtypes = [ctypes.c_int]
+    lib.anova_status_string.restype = ctypes.c_char_p
+    lib.anova_version.argtypes = []
+    lib.anova_version.restype = ctypes.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(fn: str, rc: int):
+    if rc != 0:
+        raise AnovaError(fn, rc, load().anova_status_string(rc).decode())
+    return rc
+
+
+# ------------------------------------------------------------ raw C names --
+
+def anova_plan_create(d, M, x_ptr, term_dims, bandwidth, opts: PlanOptions | None = None, stream=0):
+    """term_dims: list of tuples (|u| <= 3); bandwidth: list of ints.  Returns the handle."""
+    lib = load()
+    n = len(term_dims)
+    td = (ctypes.c_int32 * (3 * n))()
+    bw = (ctypes.c_int32 * n)()
+    for i, u in enumerate(term_dims):
+        u = tuple(int(c) for c in u)
+        if len(u) > 3:
+            raise AnovaError("anova_plan_create", -2, "term order above 3")
+        for j in range(3):
+            td[3 * i + j] = u[j] if j < len(u) else -1
+        bw[i] = int(bandwidth[i]) if len(u) else 0
+    h = ctypes.c_void_p()
+    rc = lib.anova_plan_create(ctypes.byref(h), int(d), int(M), ctypes.c_void_p(int(x_ptr) or None), n, td, bw,
+                               ctypes.byref(opts) if opts is not None else None, ctypes.c_void_p(int(stream) or None))
+    _check("anova_plan_create", rc)
+    return h
+
+
+def anova_plan_destroy(h):
+    load().anova_plan_destroy(h)
+
+
+def anova_num_coeffs(h) -> int:
+    return int(load().anova_num_coeffs(h))
+
+
+def anova_term_offset(h, u):
+    off, ln = ctypes.c_int64(), ctypes.c_int64()
+    _check("anova_term_offset", load().anova_term_offset(h, int(u), ctypes.byref(off), ctypes.byref(ln)))
+    return off.value, ln.value
+
+
+def anova_term_grid(h, u):
+    n, mc, mr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check("anova_term_grid", load().anova_term_grid(h, int(u), ctypes.byref(n), ctypes.byref(mc), ctypes.byref(mr)))
+    return n.value, mc.value, mr.value
+
+
+def grouped_trafo(h, fhat_ptr, f_ptr):
+    return _check("grouped_trafo", load().grouped_trafo(h, ctypes.c_void_p(int(fhat_ptr) or None),
+                                                        ctypes.c_void_p(int(f_ptr) or None)))
+
+
+def grouped_adjoint(h, y_ptr, fhat_ptr):
+    return _check("grouped_adjoint", load().grouped_adjoint(h, ctypes.c_void_p(int(y_ptr) or None),
+                                                            ctypes.c_void_p(int(fhat_ptr) or None)))
+
+
+def lsqr_solve(h, y_ptr, w_ptr, lam, max_it, atol, btol, fhat_ptr):
+    info = SolveInfo()
+    rc = load().lsqr_solve(h, ctypes.c_void_p(int(y_ptr) or None), ctypes.c_void_p(int(w_ptr) or None), float(lam),
+                           int(max_it), float(atol), float(btol), ctypes.c_void_p(int(fhat_ptr) or None),
+                           ctypes.byref(info))
+    if rc not in (0, -5):
+        _check("lsqr_solve", rc)
+    return rc, info
+
+
+def fista_solve(h, y_ptr, w_ptr, lambdas, max_it, tol, step_mode, L0, eta, group_mask, warm_start, path_ptr):
+    n = len(lambdas)
+    lam = (ctypes.c_double * n)(*[float(v) for v in lambdas])
+    infos = (SolveInfo * n)()
+    mask = None
+    if group_mask is not None:
+        mask = (ctypes.c_uint8 * len(group_mask))(*[1 if v else 0 for v in group_mask])
+    rc = load().fista_solve(h, ctypes.c_void_p(int(y_ptr) or None), ctypes.c_void_p(int(w_ptr) or None), lam, n,
+                            int(max_it), float(tol), int(step_mode), float(L0), float(eta), mask, int(warm_start),
+                            ctypes.c_void_p(int(path_ptr) or None), infos)
+    if rc not in (0, -5):
+        _check("fista_solve", rc)
+    return rc, [infos[i] for i in range(n)]
+
+
+def anova_profile_enable(h, on: bool = True):
+    return _check("anova_profile_enable", load().anova_profile_enable(h, 1 if on else 0))
+
+
+def anova_profile_read(h, reset: bool = False) -> dict:
+    """{stage name: (milliseconds, launches)} since the last reset."""
+    n = 16
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    names = (ctypes.c_char_p * n)()
+    ns = ctypes.c_int()
+    _check("anova_profile_read", load().anova_profile_read(h, ms, cnt, names, n, ctypes.byref(ns), 1 if reset else 0))
+    return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(min(ns.value, n))}
+
+
+def anova_status_string(status: int) -> str:
+    return load().anova_status_string(int(status)).decode()
+
+
+def anova_version() -> str:
+    return load().anova_version().decode()
+
+
+# ---------------------------------------------------------- torch helper --
+
+class Plan:
+    """Owns an anova plan for torch CUDA node tensor ``x`` of shape [d, M]."""
+
+    def __init__(self, x, terms, bandwidths, precision: int = PREC_F32, eps: float = 0.0, sigma: float = 0.0,
+                 window_m_row: int = 0, n_ctas: int = 0, stream=None):
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda):
+            raise TypeError("x must be a CUDA tensor [d, M]")
+        self.real = torch.float64 if precision == PREC_F64 else torch.float32
+        self.cplx = torch.complex128 if precision == PREC_F64 else torch.complex64
+        x = x.to(self.real).contiguous()
+        self.d, self.M = int(x.shape[0]), int(x.shape[1])
+        self.terms = [tuple(u) for u in terms]
+        self.bandwidths = [int(b) for b in bandwidths]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        opts = PlanOptions(precision=precision, eps=eps, window_m_col=0, window_m_row=window_m_row, sigma=sigma,
+                           n_ctas=n_ctas)
+        self.handle = anova_plan_create(self.d, self.M, x.data_ptr() if self.M else 0, self.terms,
+                                        self.bandwidths, opts, self.stream.cuda_stream)
+        self.n_coeffs = anova_num_coeffs(self.handle)
+        self.device = x.device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            anova_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _vec(self, v, n, name):
+        import torch
+        if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == self.cplx and v.numel() == n
+                and v.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous CUDA {self.cplx} tensor with {n} entries")
+        return v
+
+    def trafo(self, fhat, out=None):
+        import torch
+        self._vec(fhat, self.n_coeffs, "fhat")
+        out = torch.empty(self.M, dtype=self.cplx, device=self.device) if out is None else out
+        self._vec(out, self.M, "out")
+        grouped_trafo(self.handle, fhat.data_ptr() if self.n_coeffs else 0, out.data_ptr() if self.M else 0)
+        return out
+
+    def adjoint(self, y, out=None):
+        import torch
+        self._vec(y, self.M, "y")
+        out = torch.empty(self.n_coeffs, dtype=self.cplx, device=self.device) if out is None else out
+        self._vec(out, self.n_coeffs, "out")
+        grouped_adjoint(self.handle, y.data_ptr() if self.M else 0, out.data_ptr())
+        return out
+
+    def profile(self, on: bool = True):
+        anova_profile_enable(self.handle, on)
+
+    def profile_read(self, reset: bool = False) -> dict:
+        return anova_profile_read(self.handle, reset)
+
+    def term_offset(self, u):
+        return anova_term_offset(self.handle, u)
+
+    def term_grid(self, u):
+        return anova_term_grid(self.handle, u)

@@ -1,0 +1,154 @@
+"""Parity of the CUDA grouped transform F and F^H with the FP64 oracle.
+
+Bar: FP32 transforms within 1e-5 relative l2 of the oracle on the same
+(FP32-rounded) nodes, as the benchmark spec fixes for FP32.  Cases span
+several gather tiles (256 nodes) with a ragged tail, the benchmark sizes on
+sampled outputs, and the degenerate cases of the method (empty set only,
+N = 2, one node, no nodes, nodes on the wrap boundary, third-order terms).
+"""
+import numpy as np
+import pytest
+
+from oracle import anova, ndft
+from paper_2010_10199_gb300 import inputs
+
+from gpu_util import cplx_dev, f32_nodes, host, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gft():
+    import torch
+    from paper_2010_10199_gb300 import build, gft as g
+    assert torch.cuda.is_available()
+    build.build()
+    g.load()
+    return g
+
+
+def _plan(gft, x, terms, bw, **kw):
+    import torch
+    return gft.Plan(to_dev(x, torch.float32), terms, bw, **kw)
+
+
+def _pair_check(gft, x, terms, bw, fhat=None, y=None, tol=TOL, seed=1):
+    xo = f32_nodes(x)
+    n = anova.n_coeffs(terms, bw)
+    M = x.shape[1]
+    fhat = inputs.decaying_coefficients(seed, terms, bw) if fhat is None else fhat
+    y = inputs.complex_normal(seed, 4, M) if y is None else y
+    P = _plan(gft, x, terms, bw)
+    assert P.n_coeffs == n
+    f = host(P.trafo(cplx_dev(fhat)))
+    g = host(P.adjoint(cplx_dev(y)))
+    f_ref = ndft.trafo(xo, terms, bw, fhat)
+    g_ref = ndft.adjoint(xo, terms, bw, y)
+    ef, eg = rel_l2(f, f_ref), rel_l2(g, g_ref)
+    assert ef <= tol, f"forward rel l2 {ef:.3e}"
+    assert eg <= tol, f"adjoint rel l2 {eg:.3e}"
+    return ef, eg
+
+
+def test_c1_small_full(gft):
+    w = inputs.c1_small()
+    _pair_check(gft, w["x"], w["terms"], w["bandwidths"], y=w["y"])
+
+
+@pytest.mark.parametrize("M", [1, 255, 256, 257, 1000, 4099])
+def test_ragged_sizes(gft, M):
+    x = inputs.uniform_points(7, 5, M)
+    terms = anova.term_set(5, 2)
+    bw = [0] + [16] * 5 + [8] * 10
+    _pair_check(gft, x, terms, bw)
+
+
+def test_c2_subsample_all_terms(gft):
+    w = inputs.c2_scale(M=10000)
+    _pair_check(gft, w["x"], w["terms"], w["bandwidths"], fhat=w["fhat"], y=w["y"])
+
+
+def test_third_order_terms(gft):
+    d = 4
+    x = inputs.beta22_points(3, d, 3000)
+    terms = anova.term_set(d, 3)
+    bw = [0] + [20] * 4 + [12] * 6 + [10] * 4
+    _pair_check(gft, x, terms, bw)
+
+
+def test_mixed_bandwidths_and_orders(gft):
+    x = inputs.uniform_points(9, 6, 2000)
+    terms = [(), (2,), (0, 5), (1, 3, 4), (3,), (0, 1), (2, 4, 5)]
+    bw = [0, 2, 6, 4, 34, 10, 6]
+    _pair_check(gft, x, terms, bw)
+
+
+def test_bandwidth_two(gft):
+    x = inputs.uniform_points(11, 3, 700)
+    terms = [(0,), (1, 2), (0, 1, 2)]
+    bw = [2, 2, 2]
+    _pair_check(gft, x, terms, bw)
+
+
+def test_empty_set_only(gft):
+    x = inputs.uniform_points(12, 2, 513)
+    _pair_check(gft, x, [()], [0], fhat=np.array([1.5 - 0.5j]))
+
+
+def test_wrap_boundary_nodes(gft):
+    # nodes at -1/2, just below 1/2 (rounds to 1/2 in FP32 and wraps), and duplicates
+    x = inputs.uniform_points(13, 3, 600)
+    x[:, :50] = -0.5
+    x[:, 50:100] = 0.5 - 1e-9
+    x[:, 100:150] = x[:, 150:200]
+    x[0, 200:260] = 0.49999997
+    terms = anova.term_set(3, 2)
+    bw = [0, 16, 16, 16, 8, 8, 8]
+    _pair_check(gft, x, terms, bw)
+
+
+def test_no_nodes(gft):
+    import torch
+    terms = anova.term_set(3, 2)
+    bw = [0, 8, 8, 8, 4, 4, 4]
+    P = gft.Plan(torch.zeros((3, 0), device="cuda"), terms, bw)
+    g = host(P.adjoint(torch.zeros(0, dtype=torch.complex64, device="cuda")))
+    assert np.all(g == 0)
+    f = P.trafo(cplx_dev(np.ones(P.n_coeffs)))
+    assert f.numel() == 0
+
+
+def test_forward_is_deterministic(gft):
+    w = inputs.c1_small()
+    P = _plan(gft, w["x"], w["terms"], w["bandwidths"])
+    fh = cplx_dev(inputs.decaying_coefficients(3, w["terms"], w["bandwidths"]))
+    a = host(P.trafo(fh))
+    b = host(P.trafo(fh))
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.slow
+def test_c2_full_size_sampled(gft):
+    """The benchmark workload (M = 1e6, d = 20, 211 terms): forward on 2000
+    sampled nodes and adjoint on three sampled blocks against the oracle, plus
+    adjointness of the GPU pair over the whole vector."""
+    import torch
+    w = inputs.c2_scale()
+    x, terms, bw = w["x"], w["terms"], w["bandwidths"]
+    xo = f32_nodes(x)
+    P = _plan(gft, x, terms, bw)
+    fh_d = cplx_dev(w["fhat"])
+    y_d = cplx_dev(w["y"])
+    f = host(P.trafo(fh_d))
+    g = host(P.adjoint(y_d))
+    idx = inputs.subsample(w, 2000)
+    f_ref = ndft.trafo(xo[:, idx], terms, bw, w["fhat"])
+    assert rel_l2(f[idx], f_ref) <= TOL
+    offs, lens = anova.layout(terms, bw)
+    for u in (1, 20, 150):
+        ref = ndft.adjoint(xo, [terms[u]], [bw[u]], w["y"])
+        assert rel_l2(g[offs[u]:offs[u] + lens[u]], ref) <= TOL, f"term {terms[u]}"
+    lhs = np.vdot(w["y"], f)
+    rhs = np.vdot(g, w["fhat"])
+    assert abs(lhs - rhs) / abs(lhs) <= 1e-5
