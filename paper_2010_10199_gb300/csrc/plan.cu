@@ -40,11 +40,17 @@ static double kb_window(double d, int m, double b) {
 
 // Deconvolution factor psi(0) / I_0(m sqrt(b^2 - (2 pi k / n)^2)): the inverse of
 // n times the Fourier coefficient of the normalised window psi(n x) / psi(0).
+//
+// The kernels place node x at grid position t = (x + 1/2) n, i.e. stored grid
+// index q' = q + n/2 for the periodic index q of position q/n.  The shift by
+// n/2 multiplies frequency k by exp(i pi k) = (-1)^k, which is folded in here
+// (n is always even), for the forward and the adjoint alike.
 static double deconv_factor(int k, int n, int m, double b) {
     double a = 2.0 * M_PI * k / n;
     double r = b * b - a * a;
     double psi0 = std::sinh(b * m) / (M_PI * m);
-    return psi0 / bessel_i0(m * std::sqrt(r > 0 ? r : 0.0));
+    double sgn = (k & 1) ? -1.0 : 1.0;
+    return sgn * psi0 / bessel_i0(m * std::sqrt(r > 0 ? r : 0.0));
 }
 
 // Degree-7 Chebyshev interpolant of each tap weight as a function of v = 2 tau - 1.
