@@ -19,6 +19,11 @@
 
 namespace agft {
 
+// shared-memory float reduction without a returned value
+__device__ __forceinline__ void red_add(float *addr, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_addr(addr)), "f"(v) : "memory");
+}
+
 __device__ __forceinline__ int freq_index_a(int q, int N) { return q < N / 2 ? q - N / 2 : q - N / 2 + 1; }
 
 template <int MR>
@@ -69,8 +74,8 @@ spread_f32(DevPlan P, const float2 *__restrict__ y, float2 *__restrict__ partial
 #pragma unroll
                 for (int j = 0; j < MR; ++j) {
                     float w = horner8(rc[j], va);
-                    atomicAdd(base + 4 * j * stride, yx * w);
-                    atomicAdd(base + 4 * j * stride + 1, yy * w);
+                    red_add(base + 4 * j * stride, yx * w);
+                    red_add(base + 4 * j * stride + 1, yy * w);
                 }
             }
         } else if (order == 1) {
@@ -81,8 +86,8 @@ spread_f32(DevPlan P, const float2 *__restrict__ y, float2 *__restrict__ partial
                     int fb = grid_pos(__ldg(xc + p), n, tb);
                     float cw = horner8(cc, 2.f * tb - 1.f);
                     float *base = (float *)(S + fb + k);
-                    atomicAdd(base, yv.x * cw);
-                    atomicAdd(base + 1, yv.y * cw);
+                    red_add(base, yv.x * cw);
+                    red_add(base + 1, yv.y * cw);
                 }
             }
         } else {
@@ -107,8 +112,8 @@ spread_f32(DevPlan P, const float2 *__restrict__ y, float2 *__restrict__ partial
                         int rb = wrap(fb - mr + 1 + jb, n);
                         float *c = (float *)(S + (ra * n + rb) * stride + cidx);
                         float w = wa * wb;
-                        atomicAdd(c, yx * w);
-                        atomicAdd(c + 1, yy * w);
+                        red_add(c, yx * w);
+                        red_add(c + 1, yy * w);
                     }
                 }
             }

@@ -1,0 +1,256 @@
+// Forward gather over all terms, f_j = c_empty + sum_u sum_taps g_u[tap] psi(...)
+// (the window interpolation step of the NFFT behind eq. (somafm), Sec. 3), FP32.
+//
+// Point-major and persistent: a CTA owns a tile of 128 nodes whose coordinates
+// it stages in shared memory, and walks the term schedule; each term's stored
+// grid arrives in shared memory by a bulk async copy (double-buffered,
+// mbarrier-tracked).  A half-warp owns 8 nodes and evaluates one node at a
+// time with 16 lanes = 2 grid rows x 8 grid columns, so a warp instruction
+// reads 2 nodes x 2 rows x 8 columns; the row pitch = 8 (mod 16) complex
+// elements puts the two rows of a node in complementary bank halves.
+// Order-2 terms reuse the row weights of their first coordinate across the
+// row group (all terms sharing that coordinate), so per node and term a lane
+// evaluates one window polynomial.  Lanes accumulate over all terms in
+// registers; a transposed reduce-scatter per tile finishes each node.
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace agft {
+
+constexpr int G2_THREADS = 256;
+constexpr int G2_PTS = 8;                              // nodes per half-warp
+constexpr int G2_TILE = (G2_THREADS / 16) * G2_PTS;    // 128 nodes per CTA tile
+
+template <int MR, int PITCH>
+__global__ void __launch_bounds__(G2_THREADS, 2)
+gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restrict__ fhat, float2 *__restrict__ f,
+            int n_tiles, int pitch_rt) {
+    extern __shared__ __align__(128) float2 sm2[];
+    const int gb_el = (int)(P.max_grid_bytes / 8);
+    float *xs = (float *)(sm2 + 2 * gb_el);                     // [d][G2_TILE]
+    uint64_t *bars = (uint64_t *)(xs + P.d * G2_TILE);
+    const int pitch = PITCH ? PITCH : pitch_rt;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int sub = lane & 15;
+    const int r = sub >> 3, k = sub & 7;
+    const int hw = (tid >> 5) * 2 + (lane >> 4);
+    const int pbase = hw * G2_PTS;
+    const long long M = P.M;
+    const int nt = P.n_terms, d = P.d;
+    const float *__restrict__ X = P.x;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    float2 c0 = make_float2(0.f, 0.f);
+    for (int e = 0; e < P.n_empty; ++e) {
+        float2 c = fhat[P.empty_off[e]];
+        c0.x += c.x;
+        c0.y += c.y;
+    }
+
+    const int my_tiles = (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const long long total_it = (long long)my_tiles * nt;
+    if (total_it > 0 && tid == 0) {
+        const Term &T0 = P.terms[0];
+        mbar_expect_tx(&bars[0], (uint32_t)T0.grid_bytes);
+        bulk_g2s(sm2, grids + T0.grid_off, (uint32_t)T0.grid_bytes, &bars[0]);
+    }
+
+    long long it = 0;
+    for (int ti = 0; ti < my_tiles; ++ti) {
+        const long long p0 = ((long long)blockIdx.x + (long long)ti * gridDim.x) * G2_TILE;
+        // stage the tile's coordinates (the previous tile ended with a barrier)
+        for (int e = tid; e < d * G2_TILE; e += G2_THREADS) {
+            const int c = e / G2_TILE, i = e - c * G2_TILE;
+            const long long p = p0 + i;
+            xs[e] = p < M ? __ldg(X + (long long)c * M + p) : 0.f;
+        }
+        __syncthreads();
+
+        float ax[G2_PTS], ay[G2_PTS];
+        float rw[G2_PTS][MR];
+        int rbase[G2_PTS];
+        float cc[NCOEF];
+#pragma unroll
+        for (int i = 0; i < G2_PTS; ++i) {
+            ax[i] = ay[i] = 0.f;
+            rbase[i] = 0;
+#pragma unroll
+            for (int j = 0; j < MR; ++j) rw[i][j] = 0.f;
+        }
+        int cur_wc = -1;
+        for (int s = 0; s < nt; ++s, ++it) {
+            const int b = (int)(it & 1);
+            const uint32_t parity = (uint32_t)((it >> 1) & 1);
+            if (tid == 0 && it + 1 < total_it) {
+                const Term &Tn = P.terms[(s + 1) % nt];
+                fence_proxy_async();
+                mbar_expect_tx(&bars[b ^ 1], (uint32_t)Tn.grid_bytes);
+                bulk_g2s(sm2 + (b ? 0 : gb_el), grids + Tn.grid_off, (uint32_t)Tn.grid_bytes, &bars[b ^ 1]);
+            }
+            const Term &T = P.terms[s];
+            const int order = T.order, n = T.n;
+            const float nf = (float)n, hn = 0.5f * (float)n, nm1 = (float)(n - 1);
+            if (T.wc != cur_wc) {
+                const float *wsrc = P.windows[T.wc].c[k];
+#pragma unroll
+                for (int i = 0; i < NCOEF; ++i) cc[i] = __ldg(wsrc + i);
+                cur_wc = T.wc;
+            }
+            if (order == 2 && T.new_rowgroup) {
+                float rc[MR][NCOEF];
+#pragma unroll
+                for (int j = 0; j < MR; ++j)
+#pragma unroll
+                    for (int i = 0; i < NCOEF; ++i) rc[j][i] = __ldg(&P.windows[T.wr].c[r + 2 * j][i]);
+                const float *xr = xs + T.row0 * G2_TILE + pbase;
+#pragma unroll
+                for (int i = 0; i < G2_PTS; ++i) {
+                    const float t = fmaf(xr[i], nf, hn);
+                    const float fl = fminf(floorf(t), nm1);
+                    const float v = fmaf(2.f, t - fl, -1.f);
+#pragma unroll
+                    for (int j = 0; j < MR; ++j) rw[i][j] = horner8(rc[j], v);
+                    rbase[i] = ((int)fl + r) * pitch + k;   // stored row fl + r (row halo MR - 1)
+                }
+            }
+            mbar_wait(&bars[b], parity, P.err, 1);
+            const int boff = b ? gb_el : 0;
+            const float *xc = xs + T.col * G2_TILE + pbase;
+            if (order == 2) {
+#pragma unroll
+                for (int i = 0; i < G2_PTS; ++i) {
+                    const float t = fmaf(xc[i], nf, hn);
+                    const float fl = fminf(floorf(t), nm1);
+                    const float cw = horner8(cc, fmaf(2.f, t - fl, -1.f));
+                    const int idx = boff + rbase[i] + (int)fl;
+                    float sx = 0.f, sy = 0.f;
+#pragma unroll
+                    for (int j = 0; j < MR; ++j) {
+                        const float2 g = sm2[idx + 2 * j * pitch];
+                        sx = fmaf(rw[i][j], g.x, sx);
+                        sy = fmaf(rw[i][j], g.y, sy);
+                    }
+                    ax[i] = fmaf(cw, sx, ax[i]);
+                    ay[i] = fmaf(cw, sy, ay[i]);
+                }
+            } else if (order == 1) {
+                if (r == 0) {
+#pragma unroll
+                    for (int i = 0; i < G2_PTS; ++i) {
+                        const float t = fmaf(xc[i], nf, hn);
+                        const float fl = fminf(floorf(t), nm1);
+                        const float cw = horner8(cc, fmaf(2.f, t - fl, -1.f));
+                        const float2 g = sm2[boff + (int)fl + k];
+                        ax[i] = fmaf(cw, g.x, ax[i]);
+                        ay[i] = fmaf(cw, g.y, ay[i]);
+                    }
+                }
+            } else {
+                // order 3: rows (first, second) wrap modulo n; row weights evaluated directly
+                const Window &W = P.windows[T.wr];
+                const int mr = T.mr, mc = T.mc, stride = T.stride;
+                const float *xa_p = xs + T.row0 * G2_TILE + pbase;
+                const float *xb_p = xs + T.row1 * G2_TILE + pbase;
+                const float2 *G = sm2 + boff;
+#pragma unroll
+                for (int i = 0; i < G2_PTS; ++i) {
+                    float ta, tb, tc;
+                    const int fa = grid_pos(xa_p[i], n, ta);
+                    const int fb = grid_pos(xb_p[i], n, tb);
+                    const int fc = grid_pos(xc[i], n, tc);
+                    const float cw = horner8(cc, 2.f * tc - 1.f);
+                    const int cidx = wrap(fc - mc + 1 + k, n);
+                    float sx = 0.f, sy = 0.f;
+                    for (int ia = 0; ia < 2 * mr; ++ia) {
+                        const float wa = kb_direct(ta + (float)(mr - 1 - ia), mr, W.b, W.inv_psi0);
+                        const int ra = wrap(fa - mr + 1 + ia, n);
+                        for (int jb = r; jb < 2 * mr; jb += 2) {
+                            const float wb = kb_direct(tb + (float)(mr - 1 - jb), mr, W.b, W.inv_psi0);
+                            const int rb = wrap(fb - mr + 1 + jb, n);
+                            const float2 v = G[(ra * n + rb) * stride + cidx];
+                            const float w = wa * wb;
+                            sx = fmaf(w, v.x, sx);
+                            sy = fmaf(w, v.y, sy);
+                        }
+                    }
+                    ax[i] = fmaf(cw, sx, ax[i]);
+                    ay[i] = fmaf(cw, sy, ay[i]);
+                }
+            }
+            __syncthreads();
+        }
+        // reduce over the 16 lanes of each half-warp: first the two row halves
+        // (lane ^ 8), then a transposed reduce-scatter over the 8 nodes
+#pragma unroll
+        for (int i = 0; i < G2_PTS; ++i) {
+            ax[i] += __shfl_xor_sync(0xffffffffu, ax[i], 8);
+            ay[i] += __shfl_xor_sync(0xffffffffu, ay[i], 8);
+        }
+#pragma unroll
+        for (int o = 4; o >= 1; o >>= 1) {
+            const bool up = (sub & o) != 0;
+#pragma unroll
+            for (int i = 0; i < o; ++i) {
+                const float sx = up ? ax[i] : ax[i + o];
+                const float sy = up ? ay[i] : ay[i + o];
+                const float kx = up ? ax[i + o] : ax[i];
+                const float ky = up ? ay[i + o] : ay[i];
+                ax[i] = kx + __shfl_xor_sync(0xffffffffu, sx, o);
+                ay[i] = ky + __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+        }
+        const long long p = p0 + pbase + (sub & 7);
+        if (sub < 8 && p < M) f[p] = make_float2(ax[0] + c0.x, ay[0] + c0.y);
+    }
+}
+
+template <int MR, int PITCH>
+static void launch_one(Plan &p, const DevPlan &v, const float2 *fhat, float2 *f, int n_tiles, size_t smem,
+                       int ctas) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(gather2_f32<MR, PITCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        attr = true;
+    }
+    gather2_f32<MR, PITCH><<<ctas, G2_THREADS, smem, p.stream>>>(v, (const float2 *)p.grids, fhat, f, n_tiles,
+                                                                 p.pitch2);
+}
+
+template <int MR>
+static void launch_mr(Plan &p, const DevPlan &v, const float2 *fhat, float2 *f, int n_tiles, size_t smem,
+                      int ctas) {
+    switch (p.pitch2) {
+        case 40: launch_one<MR, 40>(p, v, fhat, f, n_tiles, smem, ctas); break;
+        case 72: launch_one<MR, 72>(p, v, fhat, f, n_tiles, smem, ctas); break;
+        default: launch_one<MR, 0>(p, v, fhat, f, n_tiles, smem, ctas); break;
+    }
+}
+
+int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f) {
+    DevPlan v = dev_view(p);
+    const int n_tiles = (int)((p.M + G2_TILE - 1) / G2_TILE);
+    const size_t smem = (size_t)p.max_grid_bytes * 2 + (size_t)p.d * G2_TILE * 4 + 64;
+    if (smem > (size_t)MAX_SMEM) return ANOVA_ERR_UNSUPPORTED;
+    const int per_sm = smem * 2 <= (size_t)MAX_SMEM ? 2 : 1;
+    const int ctas = std::max(1, std::min(n_tiles, per_sm * p.sm_count));
+    int mr = 3;
+    for (int s = 0; s < p.n_terms; ++s)
+        if (p.h_terms[s].mr > 0) mr = p.h_terms[s].mr;
+    if (mr <= 3)
+        launch_mr<3>(p, v, fhat, f, n_tiles, smem, ctas);
+    else
+        launch_mr<4>(p, v, fhat, f, n_tiles, smem, ctas);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace agft

@@ -117,6 +117,7 @@ struct Plan {
     long long grid_elems;
     long long max_grid_bytes;
     int max_fft_elems;      // largest n^order
+    int pitch2;             // row pitch shared by all order-2 grids
     void *partials;         // adjoint partial grids [spread_ctas][grid_elems]
     int spread_ctas;
     int gather_ctas;
@@ -136,6 +137,7 @@ enum { ST_PRE = 0, ST_GATHER = 1, ST_SPREAD = 2, ST_REDUCE = 3, ST_POST = 4, ST_
 
 // kernels launched by the entry points (trafo.cu / adjoint.cu)
 int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f);
+int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
 
 // status from a CUDA error

@@ -251,7 +251,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         delete h;
         return ANOVA_ERR_UNSUPPORTED;
     }
-    if (mr < 2 || mr > 4) {
+    if (mr < 3 || mr > 4) {
         free_plan(p);
         delete h;
         return ANOVA_ERR_UNSUPPORTED;
@@ -317,6 +317,11 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     long long goff = 0, maxbytes = 16;
     int max_fft = 1;
     int status = ANOVA_OK;
+    // all order-2 grids share one row pitch (the gather specialises on it)
+    p.pitch2 = 8;
+    for (int s = 0; s < p.n_terms; ++s)
+        if (order[sched[s]] == 2)
+            p.pitch2 = std::max(p.pitch2, row_stride(p.h_user_n[sched[s]] + 2 * (mc - 1) + 1));
     for (int s = 0; s < p.n_terms; ++s) {
         int i = sched[s];
         const int32_t *t = term_dims + 3 * i;
@@ -336,7 +341,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
             T.hc = T.mc - 1;
             T.hr = T.order == 2 ? T.mr - 1 : 0;
             T.erows = T.order == 2 ? T.n + 2 * T.hr + 1 : 1;
-            T.stride = row_stride(T.n + 2 * T.hc + 1);
+            T.stride = T.order == 2 ? p.pitch2 : row_stride(T.n + 2 * T.hc + 1);
         } else {
             T.hc = T.hr = 0;
             T.erows = T.rows;
@@ -415,8 +420,12 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     chk(cudaMalloc(&p.grids, (size_t)std::max<long long>(1, p.grid_elems) * 8));
     chk(cudaMalloc(&p.err, sizeof(int) * 4));
     // adjoint partial grids
-    long long per_cta = 2048;
-    int sc = (int)std::min<long long>((long long)p.sm_count, std::max<long long>(1, (M + per_cta - 1) / per_cta));
+    // spread: several CTAs per SM hide the shared-memory atomic latency; the
+    // partial grids they produce are bounded to 8 GB
+    long long per_cta = 1024;
+    long long sc_cap = std::max<long long>(1, (8LL << 30) / std::max<long long>(1, p.grid_elems * 8));
+    int sc = (int)std::min<long long>(std::min<long long>(4LL * p.sm_count, sc_cap),
+                                      std::max<long long>(1, (M + per_cta - 1) / per_cta));
     if (o.n_ctas > 0) sc = o.n_ctas;
     p.spread_ctas = sc;
     p.gather_ctas = (int)std::min<long long>((long long)p.sm_count,
