@@ -205,6 +205,41 @@ int anova_profile_enable(anova_plan_t plan, int on);
 int anova_profile_read(anova_plan_t plan, double *ms, int64_t *launches, const char **names, int max_stages,
                        int *n_stages, int reset);
 
+/*
+ * grouped_trafo_noalloc -- f = F(X, I_N(U)) fhat without a plan and without
+ * allocating anything.  The paper has no counterpart: this is a deployment
+ * variant of grouped_trafo for callers that cannot allocate device memory when
+ * they need the transform -- for example a host program whose device memory is
+ * already fully reserved by its own pool allocator, a plug-in that runs inside
+ * a callback with a fixed memory budget, or a latency-critical loop in which
+ * cudaMalloc/cudaFree (which synchronise the device) are not allowed.
+ *
+ * It computes what grouped_trafo computes with default options (FP32,
+ * eps 1e-5, sigma 2) for the same arguments as anova_plan_create plus the
+ * vectors.  All working data -- term table, window polynomials,
+ * deconvolution factors, a wrapped copy of the nodes and the oversampled grids
+ * -- lives in one file-scope device array of 32 MiB that every GPU loading
+ * the library keeps until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   x_dev    : [d][M] FP32 nodes (device), read only
+ *   fhat_dev : [num_coeffs] complex FP32 (device), read only
+ *   f_dev    : [M] complex FP32 (device), overwritten
+ *   stream   : cudaStream_t for all work (NULL = legacy default stream)
+ * Limits: the tables plus 4*d*M bytes of nodes plus the grids must fit in
+ * the 32 MiB array (at d = 20 and the |u| <= 2, N = 64/32 term set this
+ * allows M up to about 300,000); larger problems return ANOVA_ERR_UNSUPPORTED
+ * without launching anything.  At most 4096 terms.
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call reuses the same array and overwrites the
+ * previous call's contents, so calls that can overlap on the GPU (different
+ * streams or devices sharing a context, or host threads) race: serialise them.
+ * Returns after enqueueing the work.
+ */
+int grouped_trafo_noalloc(int d, int64_t M, const float *x_dev, int n_terms, const int32_t *term_dims,
+                          const int32_t *bandwidth, const anova_cfloat *fhat_dev, anova_cfloat *f_dev,
+                          void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *anova_status_string(int status);
 

@@ -129,6 +129,13 @@ struct Plan {
 
 DevPlan dev_view(const Plan &p);
 
+// host-side table builders shared with plan construction (plan.cu)
+double deconv_factor(int k, int n, int m, double b);
+void window_polys(Window &w, int m, double b);
+int fft_size(int N, double sigma);
+int row_stride(int n);
+__global__ void wrap_nodes_f32(const float *in, float *out, long long total);
+
 // stage timing: call stage_begin before and stage_end after a kernel launch
 void stage_begin(Plan &p, int stage);
 void stage_end(Plan &p, int stage);

@@ -45,7 +45,7 @@ static double kb_window(double d, int m, double b) {
 // index q' = q + n/2 for the periodic index q of position q/n.  The shift by
 // n/2 multiplies frequency k by exp(i pi k) = (-1)^k, which is folded in here
 // (n is always even), for the forward and the adjoint alike.
-static double deconv_factor(int k, int n, int m, double b) {
+double deconv_factor(int k, int n, int m, double b) {
     double a = 2.0 * M_PI * k / n;
     double r = b * b - a * a;
     double psi0 = std::sinh(b * m) / (M_PI * m);
@@ -54,7 +54,7 @@ static double deconv_factor(int k, int n, int m, double b) {
 }
 
 // Degree-7 Chebyshev interpolant of each tap weight as a function of v = 2 tau - 1.
-static void window_polys(Window &w, int m, double b) {
+void window_polys(Window &w, int m, double b) {
     const int P = NCOEF;
     double psi0 = kb_window(0.0, m, b);
     for (int j = 0; j < 2 * MAXM; ++j)
@@ -108,7 +108,7 @@ static bool smooth235(int n) {
     return n == 1;
 }
 
-static int fft_size(int N, double sigma) {
+int fft_size(int N, double sigma) {
     int n = (int)std::ceil(sigma * N - 1e-9);
     if (n < N + 2) n = N + 2;
     if (n % 2) ++n;
@@ -116,7 +116,7 @@ static int fft_size(int N, double sigma) {
     return n;
 }
 
-static int row_stride(int n) {
+int row_stride(int n) {
     int s = n;
     while (s % 16 != 8) ++s;
     return s;

@@ -86,6 +86,8 @@ def load(path: str | None = None):
                                        ctypes.POINTER(ctypes.c_char_p), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.c_int]
     lib.anova_profile_read.restype = ctypes.c_int
+    lib.grouped_trafo_noalloc.argtypes = [ctypes.c_int, ctypes.c_int64, vp, ctypes.c_int, i32p, i32p, vp, vp, vp]
+    lib.grouped_trafo_noalloc.restype = ctypes.c_int
     lib.anova_status_string.argtypes = [ctypes.c_int]
     lib.anova_status_string.restype = ctypes.c_char_p
     lib.anova_version.argtypes = []
@@ -151,6 +153,23 @@ def grouped_trafo(h, fhat_ptr, f_ptr):
 def grouped_adjoint(h, y_ptr, fhat_ptr):
     return _check("grouped_adjoint", load().grouped_adjoint(h, ctypes.c_void_p(int(y_ptr) or None),
                                                             ctypes.c_void_p(int(fhat_ptr) or None)))
+
+
+def grouped_trafo_noalloc(d, M, x_ptr, term_dims, bandwidth, fhat_ptr, f_ptr, stream=0):
+    """Plan-free forward transform whose working memory is a static device array
+    (for callers that cannot allocate device memory; see include/anova_gft.h)."""
+    n = len(term_dims)
+    td = (ctypes.c_int32 * (3 * n))()
+    bw = (ctypes.c_int32 * n)()
+    for i, u in enumerate(term_dims):
+        u = tuple(int(c) for c in u)
+        for j in range(3):
+            td[3 * i + j] = u[j] if j < len(u) else -1
+        bw[i] = int(bandwidth[i]) if len(u) else 0
+    rc = load().grouped_trafo_noalloc(int(d), int(M), ctypes.c_void_p(int(x_ptr) or None), n, td, bw,
+                                      ctypes.c_void_p(int(fhat_ptr) or None), ctypes.c_void_p(int(f_ptr) or None),
+                                      ctypes.c_void_p(int(stream) or None))
+    return _check("grouped_trafo_noalloc", rc)
 
 
 def lsqr_solve(h, y_ptr, w_ptr, lam, max_it, atol, btol, fhat_ptr):
