@@ -191,6 +191,20 @@ int fista_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, const
                 anova_solve_info *info);
 
 /*
+ * anova_kkt_check -- optimality of a group-lasso solution of eq. (alligatoah).
+ * With r = y - F f: an inactive group (f_u = 0) must satisfy
+ * ||W^{-1/2} (F^H r)_u|| <= lambda (Lemma (iii)); an active group must satisfy
+ * (F^H r)_u = lambda W f_u / ||f_u||_W (stationarity in the proof of Lemma (ii)).
+ *   fhat_dev : [num_coeffs] complex, the candidate solution
+ *   viol_out : host [n_terms] (may be NULL): (||W^{-1/2} q_u|| - lambda)/lambda for
+ *              inactive groups, ||(F^H r)_u - lambda W f_u/||f_u||_W|| / lambda for active ones
+ *   n_viol   : host, number of groups with viol > rtol
+ * One grouped_trafo and one grouped_adjoint over all terms; synchronises.
+ */
+int anova_kkt_check(anova_plan_t plan, const void *y_dev, const double *w_dev, const void *fhat_dev,
+                    double lambda, double rtol, double *viol_out, int *n_viol);
+
+/*
  * Per-kernel timing (no counterpart in the paper; measurement support).
  * anova_profile_enable(plan, 1) makes every later call record CUDA events on
  * the plan's stream around each kernel it launches; anova_profile_read

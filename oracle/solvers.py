@@ -79,6 +79,7 @@ def lsqr(A, AH, b, n: int, damp: float = 0.0, iters: int = 50,
         res.istop = 0
         return res
     xnorm = 0.0
+    res2 = 0.0   # sum of psi_k^2: the damping part of the residual estimate
     for it in range(1, iters + 1):
         # bidiagonalisation
         u = A(v) - alpha * u
@@ -109,7 +110,8 @@ def lsqr(A, AH, b, n: int, damp: float = 0.0, iters: int = 50,
         w = v_new - (theta / rho) * w
         v, alpha = v_new, alpha_new
         xnorm = _norm(x)
-        rnorm = math.hypot(phibar, psi)
+        res2 += psi * psi
+        rnorm = math.sqrt(res2 + phibar * phibar)
         arnorm = alpha * abs(s * phi)
         res = LsqrResult(x, it, 0, rnorm, arnorm, math.sqrt(anorm2))
         res.history.append((rnorm, arnorm))

@@ -43,8 +43,9 @@ spread_f32(DevPlan P, const float2 *__restrict__ y, float2 *__restrict__ partial
     const float *__restrict__ X = P.x;
     float2 *mypart = partials + (long long)blockIdx.x * P.grid_elems;
 
-    for (int s = 0; s < P.n_terms; ++s) {
-        const Term &T = P.terms[s];
+    if (P.skip && *P.skip) return;
+    for (int s = 0; s < P.n_act; ++s) {
+        const Term &T = P.terms[P.act[s]];
         const int order = T.order, n = T.n, stride = T.stride;
         const long long elems = T.grid_bytes / 8;
         float4 *S4 = (float4 *)S;
@@ -126,7 +127,8 @@ spread_f32(DevPlan P, const float2 *__restrict__ y, float2 *__restrict__ partial
 }
 
 __global__ void reduce_partials_f32(const float4 *__restrict__ partials, float4 *__restrict__ out, long long n4,
-                                    int nparts, long long pstride4) {
+                                    int nparts, long long pstride4, const int *skip) {
+    if (skip && *skip) return;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int c = 0; c < nparts; ++c) {
@@ -142,7 +144,8 @@ __global__ void reduce_partials_f32(const float4 *__restrict__ partials, float4 
 
 __global__ void adjoint_post_f32(DevPlan P, const float2 *__restrict__ grids, float2 *__restrict__ fhat) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const Term T = P.terms[blockIdx.x];
+    if (P.skip && *P.skip) return;
+    const Term T = P.terms[P.act[blockIdx.x]];
     const int n = T.n, s = T.order, N = T.N;
     int fe = n;
     for (int j = 1; j < s; ++j) fe *= n;
@@ -266,7 +269,8 @@ __global__ void adjoint_post_f32(DevPlan P, const float2 *__restrict__ grids, fl
 }
 
 // two-stage sum of y for the empty-set coefficients
-__global__ void sum_y_stage1(const float2 *__restrict__ y, long long M, double2 *part) {
+__global__ void sum_y_stage1(const float2 *__restrict__ y, long long M, double2 *part, const int *skip) {
+    if (skip && *skip) return;
     __shared__ double2 red[256];
     double sx = 0, sy = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
@@ -286,8 +290,9 @@ __global__ void sum_y_stage1(const float2 *__restrict__ y, long long M, double2 
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-__global__ void sum_y_stage2(const double2 *part, int nparts, float2 *fhat, const long long *eoff, int n_empty) {
-    if (threadIdx.x != 0) return;
+__global__ void sum_y_stage2(const double2 *part, int nparts, float2 *fhat, const long long *eoff, int n_empty,
+                             const int *skip) {
+    if (threadIdx.x != 0 || (skip && *skip)) return;
     double sx = 0, sy = 0;
     for (int i = 0; i < nparts; ++i) {
         sx += part[i].x;
@@ -310,16 +315,16 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
         int nb = 256;
         double2 *part = (double2 *)p.scratch;
         stage_begin(p, ST_SUMY);
-        sum_y_stage1<<<nb, 256, 0, p.stream>>>(y, p.M, part);
-        sum_y_stage2<<<1, 32, 0, p.stream>>>(part, nb, fhat, p.empty_off, p.n_empty);
+        sum_y_stage1<<<nb, 256, 0, p.stream>>>(y, p.M, part, p.skip);
+        sum_y_stage2<<<1, 32, 0, p.stream>>>(part, nb, fhat, p.empty_off, p.n_empty, p.skip);
         stage_end(p, ST_SUMY);
     }
-    if (p.n_terms == 0) return cuda_status(cudaGetLastError());
+    if (p.n_act == 0) return cuda_status(cudaGetLastError());
     if (p.M == 0) {
         cudaMemsetAsync(fhat, 0, sizeof(float2) * p.n_coeffs, p.stream);
         if (p.n_empty > 0) {
             double2 *part = (double2 *)p.scratch;
-            sum_y_stage2<<<1, 32, 0, p.stream>>>(part, 0, fhat, p.empty_off, p.n_empty);
+            sum_y_stage2<<<1, 32, 0, p.stream>>>(part, 0, fhat, p.empty_off, p.n_empty, p.skip);
         }
         return cuda_status(cudaGetLastError());
     }
@@ -338,11 +343,11 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
     int rb = (int)std::min<long long>(p.sm_count * 8LL, (n4 + 255) / 256);
     stage_begin(p, ST_REDUCE);
     reduce_partials_f32<<<rb, 256, 0, p.stream>>>((const float4 *)p.partials, (float4 *)p.grids, n4,
-                                                  p.spread_ctas, n4);
+                                                  p.spread_ctas, n4, p.skip);
     stage_end(p, ST_REDUCE);
     size_t post_smem = (size_t)p.max_fft_elems * 2 * sizeof(float2);
     stage_begin(p, ST_POST);
-    adjoint_post_f32<<<p.n_terms, 256, post_smem, p.stream>>>(v, (const float2 *)p.grids, fhat);
+    adjoint_post_f32<<<p.n_act, 256, post_smem, p.stream>>>(v, (const float2 *)p.grids, fhat);
     stage_end(p, ST_POST);
     return cuda_status(cudaGetLastError());
 }

@@ -40,9 +40,10 @@ gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restric
     const int hw = (tid >> 5) * 2 + (lane >> 4);
     const int pbase = hw * G2_PTS;
     const long long M = P.M;
-    const int nt = P.n_terms, d = P.d;
+    const int nt = P.n_act, d = P.d;
     const float *__restrict__ X = P.x;
 
+    if (P.skip && *P.skip) return;
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -60,7 +61,7 @@ gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restric
     const int my_tiles = (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
     const long long total_it = (long long)my_tiles * nt;
     if (total_it > 0 && tid == 0) {
-        const Term &T0 = P.terms[0];
+        const Term &T0 = P.terms[P.act[0]];
         mbar_expect_tx(&bars[0], (uint32_t)T0.grid_bytes);
         bulk_g2s(sm2, grids + T0.grid_off, (uint32_t)T0.grid_bytes, &bars[0]);
     }
@@ -92,12 +93,12 @@ gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restric
             const int b = (int)(it & 1);
             const uint32_t parity = (uint32_t)((it >> 1) & 1);
             if (tid == 0 && it + 1 < total_it) {
-                const Term &Tn = P.terms[(s + 1) % nt];
+                const Term &Tn = P.terms[P.act[(s + 1) % nt]];
                 fence_proxy_async();
                 mbar_expect_tx(&bars[b ^ 1], (uint32_t)Tn.grid_bytes);
                 bulk_g2s(sm2 + (b ? 0 : gb_el), grids + Tn.grid_off, (uint32_t)Tn.grid_bytes, &bars[b ^ 1]);
             }
-            const Term &T = P.terms[s];
+            const Term &T = P.terms[P.act[s]];
             const int order = T.order, n = T.n;
             const float nf = (float)n, hn = 0.5f * (float)n, nm1 = (float)(n - 1);
             if (T.wc != cur_wc) {
@@ -106,7 +107,7 @@ gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restric
                 for (int i = 0; i < NCOEF; ++i) cc[i] = __ldg(wsrc + i);
                 cur_wc = T.wc;
             }
-            if (order == 2 && T.new_rowgroup) {
+            if (order == 2 && P.act_newgroup[s]) {
                 float rc[MR][NCOEF];
 #pragma unroll
                 for (int j = 0; j < MR; ++j)

@@ -84,6 +84,10 @@ struct DevPlan {
     long long grid_elems;     // total grid elements (complex)
     long long max_grid_bytes;
     int *err;                 // device error word (bounded waits)
+    const int *act;           // active schedule: indices into terms, n_act entries
+    const unsigned char *act_newgroup;  // per active entry: recompute row weights
+    int n_act;
+    const int *skip;          // if non-null and nonzero, kernels return at once
 };
 
 constexpr int N_STAGES = 7;
@@ -94,6 +98,7 @@ struct Plan {
     int device;
     cudaStream_t stream;
     int precision;
+    double eps;             // target relative error of the transforms
     int d;
     long long M;
     int n_user_terms;
@@ -118,6 +123,12 @@ struct Plan {
     long long max_grid_bytes;
     int max_fft_elems;      // largest n^order
     int pitch2;             // row pitch shared by all order-2 grids
+    // active term list (all scheduled terms unless a group mask restricts it)
+    int *act;
+    unsigned char *act_newgroup;
+    int n_act;
+    int *h_act;
+    const int *skip;        // device flag read by every transform kernel (or null)
     void *partials;         // adjoint partial grids [spread_ctas][grid_elems]
     int spread_ctas;
     int gather_ctas;
@@ -125,9 +136,13 @@ struct Plan {
     void *scratch;          // reduction scratch
     size_t scratch_bytes;
     int sm_count;
+    void *solver;           // solver workspaces (solvers.cu), created on first use
+    void (*solver_free)(void *);
 };
 
 DevPlan dev_view(const Plan &p);
+int set_active_terms(Plan &p, const unsigned char *user_mask);
+inline cudaError_t cuda_err_of(int status) { return status == ANOVA_OK ? cudaSuccess : cudaErrorUnknown; }
 
 // host-side table builders shared with plan construction (plan.cu)
 double deconv_factor(int k, int n, int m, double b);

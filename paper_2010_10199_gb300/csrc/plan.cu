@@ -142,6 +142,32 @@ __global__ void wrap_nodes_f64(const double *in, double *out, long long total) {
     }
 }
 
+// Active term list: the scheduled terms whose user term is enabled in
+// `user_mask` (all when null), with the row-group flags recomputed for that
+// list.  Uploaded on the plan's stream.
+int set_active_terms(Plan &p, const unsigned char *user_mask) {
+    static thread_local std::vector<unsigned char> flags;
+    flags.assign(std::max(1, p.n_terms), 0);
+    int n = 0;
+    for (int s = 0; s < p.n_terms; ++s) {
+        const Term &T = p.h_terms[s];
+        if (user_mask && !user_mask[T.user_index]) continue;
+        unsigned char ng = 1;
+        if (T.order == 2 && n > 0) {
+            const Term &P = p.h_terms[p.h_act[n - 1]];
+            if (P.order == 2 && P.row0 == T.row0 && P.wr == T.wr && P.n == T.n) ng = 0;
+        }
+        flags[n] = ng;
+        p.h_act[n++] = s;
+    }
+    p.n_act = n;
+    if (n == 0) return ANOVA_OK;
+    cudaError_t e = cudaMemcpyAsync(p.act, p.h_act, sizeof(int) * n, cudaMemcpyHostToDevice, p.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.act_newgroup, flags.data(), n, cudaMemcpyHostToDevice, p.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);   // flags is reused by the next call
+    return cuda_status(e);
+}
+
 DevPlan dev_view(const Plan &p) {
     DevPlan v;
     v.d = p.d;
@@ -158,13 +184,19 @@ DevPlan dev_view(const Plan &p) {
     v.grid_elems = p.grid_elems;
     v.max_grid_bytes = p.max_grid_bytes;
     v.err = p.err;
+    v.act = p.act;
+    v.act_newgroup = p.act_newgroup;
+    v.n_act = p.n_act;
+    v.skip = p.skip;
     return v;
 }
 
 static void free_plan(Plan &p) {
     profiler_free(p);
+    if (p.solver && p.solver_free) p.solver_free(p.solver);
+    p.solver = nullptr;
     void *bufs[] = {p.x, p.terms, p.windows, p.deconv, p.deconvd, p.empty_off, p.grids, p.partials,
-                    p.err, p.scratch};
+                    p.err, p.scratch, p.act, p.act_newgroup};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete[] p.h_terms;
@@ -173,6 +205,7 @@ static void free_plan(Plan &p) {
     delete[] p.h_user_n;
     delete[] p.h_user_mc;
     delete[] p.h_user_mr;
+    delete[] p.h_act;
 }
 
 }  // namespace agft
@@ -202,6 +235,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
                       void *stream) {
     if (!out) return ANOVA_ERR_INVALID;
     *out = nullptr;
+    cudaGetLastError();   // do not report an earlier, unrelated error
     if (d < 1 || M < 0 || M >= (1LL << 31) || n_terms < 1 || !term_dims || !bandwidth) return ANOVA_ERR_INVALID;
     if (M > 0 && !x_dev) return ANOVA_ERR_INVALID;
     anova_plan_options o;
@@ -237,6 +271,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     Plan &p = h->p;
     p.stream = (cudaStream_t)stream;
     p.precision = o.precision;
+    p.eps = o.eps;
     p.d = d;
     p.M = M;
     p.n_user_terms = n_terms;
@@ -419,6 +454,9 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     chk(cudaMalloc(&p.empty_off, sizeof(long long) * std::max<size_t>(1, empties.size())));
     chk(cudaMalloc(&p.grids, (size_t)std::max<long long>(1, p.grid_elems) * 8));
     chk(cudaMalloc(&p.err, sizeof(int) * 4));
+    chk(cudaMalloc(&p.act, sizeof(int) * std::max(1, p.n_terms)));
+    chk(cudaMalloc(&p.act_newgroup, std::max(1, p.n_terms)));
+    p.h_act = new int[std::max(1, p.n_terms)];
     // adjoint partial grids
     // spread: several CTAs per SM hide the shared-memory atomic latency; the
     // partial grids they produce are bounded to 8 GB
@@ -462,6 +500,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
             wrap_nodes_f32<<<blocks, 256, 0, p.stream>>>((const float *)x_dev, (float *)p.x, total);
         chk(cudaGetLastError());
     }
+    if (e == cudaSuccess) chk(cuda_err_of(set_active_terms(p, nullptr)));
     chk(cudaStreamSynchronize(p.stream));
     // wins vector is copied; keep host term table
     if (e != cudaSuccess) {
@@ -503,6 +542,7 @@ int grouped_trafo(anova_plan_t plan, const void *fhat_dev, void *f_dev) {
     if (p.M > 0 && !f_dev) return ANOVA_ERR_INVALID;
     if (p.n_coeffs > 0 && !fhat_dev) return ANOVA_ERR_INVALID;
     if (p.M == 0) return ANOVA_OK;
+    cudaGetLastError();
     return launch_trafo_f32(p, (const float2 *)fhat_dev, (float2 *)f_dev);
 }
 
@@ -511,6 +551,7 @@ int grouped_adjoint(anova_plan_t plan, const void *y_dev, void *fhat_dev) {
     Plan &p = plan->p;
     if (!fhat_dev) return ANOVA_ERR_INVALID;
     if (p.M > 0 && !y_dev) return ANOVA_ERR_INVALID;
+    cudaGetLastError();
     return launch_adjoint_f32(p, (const float2 *)y_dev, (float2 *)fhat_dev);
 }
 

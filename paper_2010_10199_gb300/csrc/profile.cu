@@ -52,8 +52,14 @@ struct Profiler {
     }
 };
 
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 void stage_begin(Plan &p, int stage) {
-    if (!p.prof || !p.prof->on) return;
+    if (!p.prof || !p.prof->on || capturing(p.stream)) return;
     cudaEvent_t e = p.prof->get();
     cudaEventRecord(e, p.stream);
     p.prof->open[stage] = e;

@@ -24,7 +24,8 @@ __device__ __forceinline__ int freq_index(int q, int N) { return q < N / 2 ? q -
 
 __global__ void trafo_pre_f32(DevPlan P, const float2 *__restrict__ fhat, float2 *__restrict__ grids) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const Term T = P.terms[blockIdx.x];
+    if (P.skip && *P.skip) return;
+    const Term T = P.terms[P.act[blockIdx.x]];
     const int n = T.n, s = T.order, N = T.N;
     int fe = n;
     for (int j = 1; j < s; ++j) fe *= n;
@@ -156,7 +157,8 @@ __global__ void trafo_pre_f32(DevPlan P, const float2 *__restrict__ fhat, float2
 // ------------------------------------------------------- empty plan case --
 
 __global__ void fill_const_f32(float2 *f, long long M, const float2 *__restrict__ fhat, const long long *eoff,
-                               int n_empty) {
+                               int n_empty, const int *skip) {
+    if (skip && *skip) return;
     float2 c0 = make_float2(0.f, 0.f);
     for (int e = 0; e < n_empty; ++e) {
         float2 c = fhat[eoff[e]];
@@ -169,9 +171,9 @@ __global__ void fill_const_f32(float2 *f, long long M, const float2 *__restrict_
 
 int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f) {
     DevPlan v = dev_view(p);
-    if (p.n_terms == 0) {
+    if (p.n_act == 0) {
         int blocks = (int)std::min<long long>(1024, (p.M + 255) / 256);
-        fill_const_f32<<<blocks, 256, 0, p.stream>>>(f, p.M, fhat, p.empty_off, p.n_empty);
+        fill_const_f32<<<blocks, 256, 0, p.stream>>>(f, p.M, fhat, p.empty_off, p.n_empty, p.skip);
         return cuda_status(cudaGetLastError());
     }
     size_t pre_smem = (size_t)p.max_fft_elems * 2 * sizeof(float2);
@@ -181,7 +183,7 @@ int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f) {
         attr_done = true;
     }
     stage_begin(p, ST_PRE);
-    trafo_pre_f32<<<p.n_terms, 256, pre_smem, p.stream>>>(v, fhat, (float2 *)p.grids);
+    trafo_pre_f32<<<p.n_act, 256, pre_smem, p.stream>>>(v, fhat, (float2 *)p.grids);
     stage_end(p, ST_PRE);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);

@@ -86,6 +86,9 @@ def load(path: str | None = None):
                                        ctypes.POINTER(ctypes.c_char_p), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.c_int]
     lib.anova_profile_read.restype = ctypes.c_int
+    lib.anova_kkt_check.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    lib.anova_kkt_check.restype = ctypes.c_int
     lib.grouped_trafo_noalloc.argtypes = [ctypes.c_int, ctypes.c_int64, vp, ctypes.c_int, i32p, i32p, vp, vp, vp]
     lib.grouped_trafo_noalloc.restype = ctypes.c_int
     lib.anova_status_string.argtypes = [ctypes.c_int]
@@ -197,6 +200,16 @@ def fista_solve(h, y_ptr, w_ptr, lambdas, max_it, tol, step_mode, L0, eta, group
     return rc, [infos[i] for i in range(n)]
 
 
+def anova_kkt_check(h, y_ptr, w_ptr, fhat_ptr, lam, rtol, n_terms):
+    viol = (ctypes.c_double * max(1, n_terms))()
+    nv = ctypes.c_int()
+    _check("anova_kkt_check", load().anova_kkt_check(h, ctypes.c_void_p(int(y_ptr) or None),
+                                                     ctypes.c_void_p(int(w_ptr) or None),
+                                                     ctypes.c_void_p(int(fhat_ptr) or None), float(lam), float(rtol),
+                                                     viol, ctypes.byref(nv)))
+    return [viol[i] for i in range(n_terms)], nv.value
+
+
 def anova_profile_enable(h, on: bool = True):
     return _check("anova_profile_enable", load().anova_profile_enable(h, 1 if on else 0))
 
@@ -277,6 +290,42 @@ class Plan:
         self._vec(out, self.n_coeffs, "out")
         grouped_adjoint(self.handle, y.data_ptr() if self.M else 0, out.data_ptr())
         return out
+
+    def _weights(self, w):
+        import torch
+        if w is None:
+            return 0
+        if not (isinstance(w, torch.Tensor) and w.is_cuda and w.dtype == torch.float64 and w.numel() == self.n_coeffs
+                and w.is_contiguous()):
+            raise TypeError(f"w must be a contiguous CUDA float64 tensor with {self.n_coeffs} entries")
+        return w.data_ptr()
+
+    def lsqr(self, y, lam, max_it=50, atol=0.0, btol=0.0, w=None, out=None):
+        """Tikhonov minimiser of eq. (new_min_prob) by LSQR; returns (fhat, info dict, status)."""
+        import torch
+        self._vec(y, self.M, "y")
+        out = torch.empty(self.n_coeffs, dtype=self.cplx, device=self.device) if out is None else out
+        rc, info = lsqr_solve(self.handle, y.data_ptr() if self.M else 0, self._weights(w), lam, max_it, atol, btol,
+                              out.data_ptr())
+        return out, info.as_dict(), rc
+
+    def fista(self, y, lambdas, max_it=500, tol=1e-6, step_mode=0, L0=0.0, eta=2.0, w=None, group_mask=None,
+              warm_start=None):
+        """Group-lasso path of eq. (alligatoah); returns (path [n_lambda, n_coeffs], infos, status)."""
+        import torch
+        self._vec(y, self.M, "y")
+        path = torch.zeros((len(lambdas), self.n_coeffs), dtype=self.cplx, device=self.device)
+        if warm_start is not None:
+            path[0].copy_(warm_start)
+        rc, infos = fista_solve(self.handle, y.data_ptr(), self._weights(w), list(lambdas), max_it, tol, step_mode,
+                                L0, eta, group_mask, 1 if warm_start is not None else 0, path.data_ptr())
+        return path, [i.as_dict() for i in infos], rc
+
+    def kkt(self, y, fhat, lam, rtol=1e-3, w=None):
+        self._vec(y, self.M, "y")
+        self._vec(fhat, self.n_coeffs, "fhat")
+        return anova_kkt_check(self.handle, y.data_ptr(), self._weights(w), fhat.data_ptr(), lam, rtol,
+                               len(self.terms))
 
     def profile(self, on: bool = True):
         anova_profile_enable(self.handle, on)

@@ -212,3 +212,16 @@ def test_sobol_indices_sum_to_one():
     rho = solvers.sobol_indices(f, offs, lens)
     assert rho[0] == 0 and abs(rho.sum() - 1) < 1e-14
     assert solvers.active_set(rho, [(), (0,), (0, 1)], [0.5, 0.5]) == [0] + [i for i in (1, 2) if rho[i] > 0.5]
+
+
+def test_lsqr_residual_estimate_is_the_damped_residual():
+    # Paige--Saunders: rnorm = sqrt(||b - A x||^2 + damp^2 ||x||^2), from the
+    # accumulated psi_k^2 and phibar (exact in exact arithmetic)
+    w_ = inputs.c1_small()
+    x, terms, bw, y = w_["x"][:, :500], w_["terms"], w_["bandwidths"], w_["y"][:500]
+    Fm = ndft.matrix(x, terms, bw)
+    n = Fm.shape[1]
+    for lam, iters in ((1e-3, 7), (0.5, 30)):
+        r = solvers.tikhonov_lsqr(lambda f: Fm @ f, lambda q: Fm.conj().T @ q, y, n, lam, None, iters=iters)
+        true = math.sqrt(np.linalg.norm(y - Fm @ r.x) ** 2 + 2 * lam * np.linalg.norm(r.x) ** 2)
+        assert abs(r.rnorm - true) <= 1e-10 * true
