@@ -204,6 +204,60 @@ int fista_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, const
 int anova_kkt_check(anova_plan_t plan, const void *y_dev, const double *w_dev, const void *fhat_dev,
                     double lambda, double rtol, double *viol_out, int *n_viol);
 
+/* ------------------------------------------------------------------------
+ * Learned group screening (no counterpart in the paper).  A two-hidden-layer
+ * MLP (ReLU, sigmoid output, FP32) proposes, along a group-lasso lambda path,
+ * which groups will be nonzero; fista_screened_path verifies every proposal
+ * with the full KKT conditions, so the network changes only the work done.
+ * ------------------------------------------------------------------------ */
+typedef struct anova_mlp_s *anova_mlp_t;
+
+/* Create a network with n_features inputs and two hidden layers of `hidden`
+ * units from initial parameters (host, FP32, packed W1[F][H] | b1[H] |
+ * W2[H][H] | b2[H] | W3[H] | b3[1], row-major).  Work runs on `stream`. */
+int anova_mlp_create(anova_mlp_t *out, int n_features, int hidden, const float *params_host, void *stream);
+void anova_mlp_destroy(anova_mlp_t mlp);
+int64_t anova_mlp_num_params(anova_mlp_t mlp);
+/* Copy the current parameters and the last computed gradients (either may be NULL); synchronises. */
+int anova_mlp_get_params(anova_mlp_t mlp, float *params_host, float *grads_host);
+/* prob_dev[g] = sigmoid(z_g) for the G feature rows X_dev [G][n_features] (device). */
+int anova_mlp_forward(anova_mlp_t mlp, const float *X_dev, int G, float *prob_dev);
+/* Forward + backward of the positive-weighted binary cross-entropy on logits,
+ * loss = mean_g [pw y_g softplus(-z_g) + (1 - y_g) softplus(z_g)], labels y_dev [G]
+ * in {0, 1}; gradients are kept for anova_mlp_get_params; *loss_out gets the loss. */
+int anova_mlp_gradients(anova_mlp_t mlp, const float *X_dev, const float *y_dev, int G, float pos_weight,
+                        double *loss_out);
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8) over `epochs` passes of consecutive
+ * mini-batches of `batch` rows; loss_history (host, may be NULL) gets the mean
+ * loss per epoch. */
+int anova_mlp_train(anova_mlp_t mlp, const float *X_dev, const float *y_dev, int n_samples, int batch, int epochs,
+                    float lr, float pos_weight, double *loss_history);
+
+/* Screening features of every group (device X_dev [n_terms][7]) for the step
+ * lambda_prev -> lambda at the solution fhat_dev of lambda_prev (one
+ * grouped_trafo and one grouped_adjoint over all terms); see screen.cu. */
+int anova_screen_features(anova_plan_t plan, const void *y_dev, const double *w_dev, const void *fhat_dev,
+                          double lambda, double lambda_prev, float *X_dev);
+
+typedef struct {
+    int64_t proposed_groups;      /* groups the network (or a nonzero warm start) proposed, summed over lambdas */
+    int64_t readmitted_groups;    /* groups added back by the KKT check */
+    int64_t rounds;               /* FISTA solves (proposal + re-admission rounds) */
+    int64_t term_iterations;      /* sum over FISTA iterations of the terms transformed */
+    int64_t full_term_iterations; /* the same iterations times all terms (work without screening) */
+    double seconds;               /* wall time of the path */
+} anova_screen_stats;
+
+/* Group-lasso path (eq. (alligatoah)) with learned screening: per lambda
+ * (largest first, warm started) propose groups with prob > threshold (plus
+ * groups nonzero at the previous lambda and the empty set), run constant-step
+ * FISTA with the transforms restricted to them, then re-admit every held-out
+ * group whose KKT score ||W^{-1/2} (F^H r)_u|| exceeds lambda (1 + kkt_tol) and
+ * re-solve until none does.  Output layout as fista_solve. */
+int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, const double *w_dev,
+                        const double *lambdas, int n_lambda, int max_it, double tol, double threshold,
+                        double kkt_tol, void *fhat_path_dev, anova_solve_info *info, anova_screen_stats *stats);
+
 /*
  * Per-kernel timing (no counterpart in the paper; measurement support).
  * anova_profile_enable(plan, 1) makes every later call record CUDA events on

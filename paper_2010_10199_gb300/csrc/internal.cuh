@@ -109,7 +109,7 @@ struct Plan {
     int n_empty;
     long long *h_user_off;  // per user term: coefficient offset
     long long *h_user_len;
-    int *h_user_n, *h_user_mc, *h_user_mr;
+    int *h_user_n, *h_user_mc, *h_user_mr, *h_user_order;
     // device buffers
     void *x;                // FP32 or FP64 nodes [d][M]
     Term *terms;
@@ -161,6 +161,9 @@ enum { ST_PRE = 0, ST_GATHER = 1, ST_SPREAD = 2, ST_REDUCE = 3, ST_POST = 4, ST_
 int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
+int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas, int n_lambda, int max_it,
+               double tol, int step_mode, double L0, double eta, const uint8_t *mask, const float2 *f0,
+               float2 *path, anova_solve_info *info, double *L_out);
 
 // status from a CUDA error
 inline int cuda_status(cudaError_t e) {

@@ -205,6 +205,7 @@ static void free_plan(Plan &p) {
     delete[] p.h_user_n;
     delete[] p.h_user_mc;
     delete[] p.h_user_mr;
+    delete[] p.h_user_order;
     delete[] p.h_act;
 }
 
@@ -298,6 +299,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     p.h_user_n = new int[n_terms];
     p.h_user_mc = new int[n_terms];
     p.h_user_mr = new int[n_terms];
+    p.h_user_order = new int[n_terms];
     long long off = 0;
     std::vector<int> order(n_terms);
     std::vector<long long> empties;
@@ -312,6 +314,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         p.h_user_n[i] = ord ? fft_size(bandwidth[i], o.sigma) : 0;
         p.h_user_mc[i] = ord ? mc : 0;
         p.h_user_mr[i] = ord > 1 ? mr : 0;
+        p.h_user_order[i] = ord;
         if (ord == 0) empties.push_back(off);
         off += len;
     }

@@ -21,59 +21,9 @@
 #include <cstring>
 #include <vector>
 
-#include "internal.cuh"
+#include "solvers.cuh"
 
 namespace agft {
-
-// Every kernel that produces partial sums runs exactly RED_BLOCKS blocks
-// (grid-stride loops; a block without work writes 0), so finish_sums always
-// adds the same slots in the same order: deterministic and free of stale data.
-constexpr int RED_BLOCKS = 304;
-constexpr int RED_THREADS = 256;
-
-struct SolverState {
-    // LSQR
-    double alpha, beta, rhobar, phibar, anorm2, bnorm, xnorm2, rnorm, arnorm, damp, res2;
-    double phi_rho, theta_rho, atol, btol, tiny_rel;
-    double red[8];          // finished reductions
-    // FISTA
-    double t, L, lam, tol, diff2, fn2, rh2, rf2, cross, dh2, eta;
-    int done, iters, stop, status, max_it, accepted;
-};
-
-struct SolverWork {
-    long long M = 0, n = 0;
-    float2 *uM = nullptr, *tM = nullptr, *rM = nullptr;                          // node-sized
-    float2 *v = nullptr, *w = nullptr, *x = nullptr, *tn = nullptr, *h = nullptr;  // coefficient-sized
-    float2 *f = nullptr, *fp = nullptr, *g = nullptr;
-    float *ws = nullptr;          // omega^{-1/2} (LSQR) or omega (FISTA) per coefficient
-    double *wd = nullptr;         // omega per coefficient (FP64)
-    double *part = nullptr;       // [8][RED_BLOCKS] partial sums
-    double *gnorm = nullptr;      // per-group values
-    long long *goff = nullptr, *glen = nullptr;
-    unsigned char *gmask = nullptr;
-    SolverState *st = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr, join = nullptr;
-    cudaStream_t stream = nullptr;   // own non-blocking stream: graph capture needs one
-};
-
-// Runs the solver on its own stream, ordered after the caller's stream and
-// joined back into it at the end.
-struct StreamScope {
-    Plan &p;
-    SolverWork *W;
-    cudaStream_t user;
-    StreamScope(Plan &p_, SolverWork *W_) : p(p_), W(W_), user(p_.stream) {
-        cudaEventRecord(W->join, user);
-        cudaStreamWaitEvent(W->stream, W->join, 0);
-        p.stream = W->stream;
-    }
-    ~StreamScope() {
-        cudaEventRecord(W->join, W->stream);
-        cudaStreamWaitEvent(user, W->join, 0);
-        p.stream = user;
-    }
-};
 
 static void free_work(SolverWork *W) {
     if (!W) return;
@@ -597,7 +547,7 @@ __global__ void k_kkt(const float2 *g, const float2 *f, const double *wd, const 
 
 static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>(RED_BLOCKS, (n + 255) / 256)); }
 
-static SolverWork *get_work(Plan &p, int &rc) {
+SolverWork *get_work(Plan &p, int &rc) {
     rc = ANOVA_OK;
     SolverWork *W = (SolverWork *)p.solver;
     if (W) return W;
@@ -827,9 +777,9 @@ static int power_estimate(Plan &p, SolverWork *W, int iters, bool masked, double
     return cuda_status(cudaGetLastError());
 }
 
-static int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas, int n_lambda, int max_it,
-                      double tol, int step_mode, double L0, double eta, const uint8_t *mask, int warm_start,
-                      float2 *path, anova_solve_info *info) {
+int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas, int n_lambda, int max_it,
+               double tol, int step_mode, double L0, double eta, const uint8_t *mask, const float2 *f0,
+               float2 *path, anova_solve_info *info, double *L_out) {
     int rc;
     SolverWork *W = get_work(p, rc);
     if (!W) return rc;
@@ -855,10 +805,12 @@ static int fista_impl(Plan &p, const float2 *y, const double *w, const double *l
     std::vector<int> ord(n_lambda);
     for (int i = 0; i < n_lambda; ++i) ord[i] = i;
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return lambdas[a] > lambdas[b]; });
-    if (warm_start)
-        cudaMemcpyAsync(W->f, path, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s);
-    else
+    if (f0) {
+        cudaMemcpyAsync(W->f, f0, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s);
+        if (mask) k_mask_groups<<<G, 256, 0, s>>>(W->f, W->goff, W->glen, W->gmask);
+    } else {
         k_zero<<<gn, 256, 0, s>>>(W->f, n);
+    }
     for (int li = 0; li < n_lambda; ++li) {
         const int idx = ord[li];
         SolverState h0;
@@ -980,6 +932,7 @@ static int fista_impl(Plan &p, const float2 *y, const double *w, const double *l
             return hf.status;
         }
     }
+    if (L_out) *L_out = L;
     return set_active_terms(p, nullptr);
 }
 
@@ -1018,7 +971,8 @@ int fista_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, const
     if (p.precision != ANOVA_PREC_F32) return ANOVA_ERR_UNSUPPORTED;
     if (p.M == 0) return ANOVA_ERR_INVALID;
     return fista_impl(p, (const float2 *)y_dev, w_dev, lambdas, n_lambda, max_it, tol, step_mode, L0, eta,
-                      group_mask, warm_start, (float2 *)fhat_path_dev, info);
+                      group_mask, warm_start ? (const float2 *)fhat_path_dev : nullptr, (float2 *)fhat_path_dev,
+                      info, nullptr);
 }
 
 // KKT check of a group-lasso solution: viol_out[u] for every user term (host

@@ -43,6 +43,18 @@ class SolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ScreenStats(ctypes.Structure):
+    _fields_ = [("proposed_groups", ctypes.c_int64), ("readmitted_groups", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("term_iterations", ctypes.c_int64), ("full_term_iterations", ctypes.c_int64),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+N_SCREEN_FEATURES = 7
+
+
 def library_path() -> str:
     return LIB_PATH
 
@@ -86,6 +98,27 @@ def load(path: str | None = None):
                                        ctypes.POINTER(ctypes.c_char_p), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.c_int]
     lib.anova_profile_read.restype = ctypes.c_int
+    lib.anova_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.anova_mlp_create.restype = ctypes.c_int
+    lib.anova_mlp_destroy.argtypes = [vp]
+    lib.anova_mlp_destroy.restype = None
+    lib.anova_mlp_num_params.argtypes = [vp]
+    lib.anova_mlp_num_params.restype = ctypes.c_int64
+    lib.anova_mlp_get_params.argtypes = [vp, vp, vp]
+    lib.anova_mlp_get_params.restype = ctypes.c_int
+    lib.anova_mlp_forward.argtypes = [vp, vp, ctypes.c_int, vp]
+    lib.anova_mlp_forward.restype = ctypes.c_int
+    lib.anova_mlp_gradients.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    lib.anova_mlp_gradients.restype = ctypes.c_int
+    lib.anova_mlp_train.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                    ctypes.c_float, vp]
+    lib.anova_mlp_train.restype = ctypes.c_int
+    lib.anova_screen_features.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp]
+    lib.anova_screen_features.restype = ctypes.c_int
+    lib.fista_screened_path.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, vp,
+                                        ctypes.POINTER(SolveInfo), ctypes.POINTER(ScreenStats)]
+    lib.fista_screened_path.restype = ctypes.c_int
     lib.anova_kkt_check.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double,
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     lib.anova_kkt_check.restype = ctypes.c_int
@@ -338,3 +371,125 @@ class Plan:
 
     def term_grid(self, u):
         return anova_term_grid(self.handle, u)
+
+
+# ------------------------------------------------------------- screening --
+
+class Mlp:
+    """The group-screening network (two hidden ReLU layers, sigmoid output)."""
+
+    def __init__(self, params, n_features: int = N_SCREEN_FEATURES, hidden: int = 128, stream=None):
+        import numpy as np
+        import torch
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        self.F, self.H = int(n_features), int(hidden)
+        expect = self.F * self.H + self.H + self.H * self.H + self.H + self.H + 1
+        if p.size != expect:
+            raise ValueError(f"expected {expect} parameters, got {p.size}")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check("anova_mlp_create", load().anova_mlp_create(ctypes.byref(h), self.F, self.H,
+                                                           ctypes.c_void_p(p.ctypes.data),
+                                                           ctypes.c_void_p(self.stream.cuda_stream or None)))
+        self.handle = h
+        self.n_params = expect
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().anova_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self, grads: bool = False):
+        import numpy as np
+        p = np.empty(self.n_params, dtype=np.float32)
+        g = np.empty(self.n_params, dtype=np.float32) if grads else None
+        _check("anova_mlp_get_params", load().anova_mlp_get_params(
+            self.handle, ctypes.c_void_p(p.ctypes.data), ctypes.c_void_p(g.ctypes.data) if grads else None))
+        return (p, g) if grads else p
+
+    def forward(self, X):
+        import torch
+        G = int(X.shape[0])
+        out = torch.empty(G, dtype=torch.float32, device=X.device)
+        _check("anova_mlp_forward", load().anova_mlp_forward(self.handle, ctypes.c_void_p(X.data_ptr() or None), G,
+                                                             ctypes.c_void_p(out.data_ptr() or None)))
+        return out
+
+    def gradients(self, X, y, pos_weight: float = 1.0):
+        loss = ctypes.c_double()
+        _check("anova_mlp_gradients", load().anova_mlp_gradients(self.handle, ctypes.c_void_p(X.data_ptr()),
+                                                                 ctypes.c_void_p(y.data_ptr()), int(X.shape[0]),
+                                                                 float(pos_weight), ctypes.byref(loss)))
+        return loss.value
+
+    def train(self, X, y, batch: int = 4096, epochs: int = 10, lr: float = 1e-3, pos_weight: float = 1.0):
+        import numpy as np
+        hist = np.zeros(epochs)
+        _check("anova_mlp_train", load().anova_mlp_train(self.handle, ctypes.c_void_p(X.data_ptr()),
+                                                         ctypes.c_void_p(y.data_ptr()), int(X.shape[0]), int(batch),
+                                                         int(epochs), float(lr), float(pos_weight),
+                                                         ctypes.c_void_p(hist.ctypes.data)))
+        return hist
+
+
+def mlp_init_params(seed: int, n_features: int = N_SCREEN_FEATURES, hidden: int = 128):
+    """He-normal weights, zero biases, packed W1 | b1 | W2 | b2 | W3 | b3."""
+    import numpy as np
+    from . import inputs
+    F, H = n_features, hidden
+    w1 = inputs.normal(seed, 71, F * H) * np.sqrt(2.0 / F)
+    w2 = inputs.normal(seed, 72, H * H) * np.sqrt(2.0 / H)
+    w3 = inputs.normal(seed, 73, H) * np.sqrt(1.0 / H)
+    return np.concatenate([w1, np.zeros(H), w2, np.zeros(H), w3, np.zeros(1)]).astype(np.float32)
+
+
+def screen_features(plan: "Plan", y, fhat, lam: float, lam_prev: float, w=None):
+    import torch
+    X = torch.empty((len(plan.terms), N_SCREEN_FEATURES), dtype=torch.float32, device=plan.device)
+    _check("anova_screen_features", load().anova_screen_features(
+        plan.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(plan._weights(w) or None),
+        ctypes.c_void_p(fhat.data_ptr()), float(lam), float(lam_prev), ctypes.c_void_p(X.data_ptr())))
+    return X
+
+
+def fista_screened_path(plan: "Plan", mlp: Mlp, y, lambdas, max_it=500, tol=1e-6, threshold=0.5, kkt_tol=1e-3,
+                        w=None):
+    """Screened group-lasso path; returns (path [n_lambda, n_coeffs], infos, stats)."""
+    import torch
+    n = len(lambdas)
+    path = torch.zeros((n, plan.n_coeffs), dtype=plan.cplx, device=plan.device)
+    lam = (ctypes.c_double * n)(*[float(v) for v in lambdas])
+    infos = (SolveInfo * n)()
+    st = ScreenStats()
+    _check("fista_screened_path", load().fista_screened_path(
+        plan.handle, mlp.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(plan._weights(w) or None), lam, n,
+        int(max_it), float(tol), float(threshold), float(kkt_tol), ctypes.c_void_p(path.data_ptr()), infos,
+        ctypes.byref(st)))
+    return path, [infos[i].as_dict() for i in range(n)], st.as_dict()
+
+
+def screening_training_set(plan: "Plan", y, lambdas, path, w=None):
+    """Features and labels along a solved path (labels: group nonzero at the next lambda)."""
+    import torch
+    lam = sorted([float(v) for v in lambdas], reverse=True)
+    order = sorted(range(len(lambdas)), key=lambda i: -float(lambdas[i]))
+    Xs, ys = [], []
+    prev = torch.zeros(plan.n_coeffs, dtype=plan.cplx, device=plan.device)
+    lam_prev = lam[0]
+    for j, i in enumerate(order):
+        Xs.append(screen_features(plan, y, prev, lam[j], lam_prev, w))
+        lab = torch.zeros(len(plan.terms), dtype=torch.float32, device=plan.device)
+        for u in range(len(plan.terms)):
+            o, ln = plan.term_offset(u)
+            lab[u] = float(bool(torch.any(path[i, o:o + ln] != 0)))
+        ys.append(lab)
+        prev = path[i].contiguous()
+        lam_prev = lam[j]
+    return torch.cat(Xs).contiguous(), torch.cat(ys).contiguous()
+
