@@ -205,6 +205,34 @@ int anova_kkt_check(anova_plan_t plan, const void *y_dev, const double *w_dev, c
                     double lambda, double rtol, double *viol_out, int *n_viol);
 
 /* ------------------------------------------------------------------------
+ * Many independent problems in one launch per kernel.  A batch holds one
+ * plan per problem (same options); its vectors are the concatenation of the
+ * problems' vectors (problem p's nodes at node_off[p] .. node_off[p+1], its
+ * coefficients at coef_off[p] .. coef_off[p+1]).  Every problem needs at
+ * least one non-empty term.  The problems are independent as the terms are
+ * (Sec. 3, after eq. (somafm)); each kernel runs once for all of them.
+ * ------------------------------------------------------------------------ */
+typedef struct anova_batch_s *anova_batch_t;
+
+/* x_dev[p]: device nodes [d[p]][M[p]] of problem p; term_dims[p] / bandwidth[p]
+ * as for anova_plan_create.  Synchronises `stream`. */
+int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const int64_t *M,
+                       const float *const *x_dev, const int *n_terms, const int32_t *const *term_dims,
+                       const int32_t *const *bandwidth, const anova_plan_options *opts, void *stream);
+void anova_batch_destroy(anova_batch_t batch);
+/* node_off / coef_off: host arrays of n_problems + 1 entries (either may be NULL). */
+int anova_batch_layout(anova_batch_t batch, int64_t *node_off, int64_t *coef_off);
+/* f = F fhat for every problem (concatenated vectors, FP32 complex). */
+int grouped_trafo_batch(anova_batch_t batch, const void *fhat_dev, void *f_dev);
+/* fhat = F^H y for every problem. */
+int grouped_adjoint_batch(anova_batch_t batch, const void *y_dev, void *fhat_dev);
+/* One Tikhonov LSQR (eq. (new_min_prob), W = I, damping sqrt(2 lambda)) per
+ * problem, all in the same launches, each with its own FP64 scalars and
+ * stopping tests; info: host [n_problems] (may be NULL).  Synchronises. */
+int lsqr_solve_batch(anova_batch_t batch, const void *y_dev, double lambda, int max_it, void *fhat_dev,
+                     anova_solve_info *info);
+
+/* ------------------------------------------------------------------------
  * Learned group screening (no counterpart in the paper).  A two-hidden-layer
  * MLP (ReLU, sigmoid output, FP32) proposes, along a group-lasso lambda path,
  * which groups will be nonzero; fista_screened_path verifies every proposal

@@ -13,6 +13,7 @@
 //      (I_N minus {0})^{|u|}.
 //   4. empty-set terms: sum_j y_j by a two-stage reduction.
 #include <algorithm>
+#include <cstring>
 
 #include "device.cuh"
 #include "internal.cuh"
@@ -28,7 +29,7 @@ __device__ __forceinline__ int freq_index_a(int q, int N) { return q < N / 2 ? q
 
 template <int MR>
 __global__ void __launch_bounds__(SPREAD_THREADS)
-spread_f32(DevPlan P, const float2 *__restrict__ y, float2 *__restrict__ partials) {
+spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n_items) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *S = (float2 *)smem_raw;
     const int tid = threadIdx.x;
@@ -37,13 +38,17 @@ spread_f32(DevPlan P, const float2 *__restrict__ y, float2 *__restrict__ partial
     const int r = sub >> 3, k = sub & 7;
     const int hw = (tid >> 5) * 2 + (lane >> 4);
     const int nhw = SPREAD_THREADS / 16;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int pb = B.plans ? B.item_prob[item] : 0;
+    const DevPlan &P = B.plans ? B.plans[pb] : single;
+    const int kc = B.plans ? item - B.item0[pb] : item;   // node chunk of this problem
+    if (P.skip && *P.skip) continue;
     const long long M = P.M;
-    const long long j0 = M * (long long)blockIdx.x / gridDim.x;
-    const long long j1 = M * (long long)(blockIdx.x + 1) / gridDim.x;
+    const long long j0 = M * (long long)kc / P.spread_chunks;
+    const long long j1 = M * (long long)(kc + 1) / P.spread_chunks;
     const float *__restrict__ X = P.x;
-    float2 *mypart = partials + (long long)blockIdx.x * P.grid_elems;
-
-    if (P.skip && *P.skip) return;
+    const float2 *__restrict__ y = y_base + P.vec_node_off;
+    float2 *mypart = P.partials + (long long)kc * P.grid_elems;
     for (int s = 0; s < P.n_act; ++s) {
         const Term &T = P.terms[P.act[s]];
         const int order = T.order, n = T.n, stride = T.stride;
@@ -124,11 +129,16 @@ spread_f32(DevPlan P, const float2 *__restrict__ y, float2 *__restrict__ partial
         for (long long e = tid; e < elems / 2; e += blockDim.x) dst[e] = S4[e];
         __syncthreads();
     }
+  }
 }
 
-__global__ void reduce_partials_f32(const float4 *__restrict__ partials, float4 *__restrict__ out, long long n4,
-                                    int nparts, long long pstride4, const int *skip) {
-    if (skip && *skip) return;
+__global__ void reduce_partials_f32(DevPlan single, BatchArgs B) {
+    const DevPlan &P = B.plans ? B.plans[blockIdx.y] : single;
+    if (P.skip && *P.skip) return;
+    const float4 *__restrict__ partials = (const float4 *)P.partials;
+    float4 *__restrict__ out = (float4 *)P.grids;
+    const long long n4 = P.grid_elems / 2, pstride4 = n4;
+    const int nparts = P.spread_chunks;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int c = 0; c < nparts; ++c) {
@@ -142,10 +152,15 @@ __global__ void reduce_partials_f32(const float4 *__restrict__ partials, float4 
     }
 }
 
-__global__ void adjoint_post_f32(DevPlan P, const float2 *__restrict__ grids, float2 *__restrict__ fhat) {
+__global__ void adjoint_post_f32(DevPlan single, BatchArgs B, float2 *__restrict__ fhat_base) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int pb = B.plans ? B.blk_prob[blockIdx.x] : 0;
+    const DevPlan &P = B.plans ? B.plans[pb] : single;
+    const int sblk = B.plans ? (int)blockIdx.x - B.blk0[pb] : (int)blockIdx.x;
     if (P.skip && *P.skip) return;
-    const Term T = P.terms[P.act[blockIdx.x]];
+    const float2 *__restrict__ grids = P.grids;
+    float2 *__restrict__ fhat = fhat_base + P.vec_coef_off;
+    const Term T = P.terms[P.act[sblk]];
     const int n = T.n, s = T.order, N = T.N;
     int fe = n;
     for (int j = 1; j < s; ++j) fe *= n;
@@ -269,8 +284,13 @@ __global__ void adjoint_post_f32(DevPlan P, const float2 *__restrict__ grids, fl
 }
 
 // two-stage sum of y for the empty-set coefficients
-__global__ void sum_y_stage1(const float2 *__restrict__ y, long long M, double2 *part, const int *skip) {
-    if (skip && *skip) return;
+__global__ void sum_y_stage1(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, double2 *part_base) {
+    const DevPlan &P = B.plans ? B.plans[blockIdx.y] : single;
+    if (P.skip && *P.skip) return;
+    if (P.n_empty == 0) return;
+    const float2 *__restrict__ y = y_base + P.vec_node_off;
+    const long long M = P.M;
+    double2 *part = part_base + (long long)blockIdx.y * gridDim.x;
     __shared__ double2 red[256];
     double sx = 0, sy = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
@@ -290,9 +310,13 @@ __global__ void sum_y_stage1(const float2 *__restrict__ y, long long M, double2 
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-__global__ void sum_y_stage2(const double2 *part, int nparts, float2 *fhat, const long long *eoff, int n_empty,
-                             const int *skip) {
-    if (threadIdx.x != 0 || (skip && *skip)) return;
+__global__ void sum_y_stage2(DevPlan single, BatchArgs B, const double2 *part_base, int nparts, float2 *fhat_base) {
+    const DevPlan &P = B.plans ? B.plans[blockIdx.x] : single;
+    if (threadIdx.x != 0 || (P.skip && *P.skip) || P.n_empty == 0) return;
+    const double2 *part = part_base + (long long)blockIdx.x * nparts;
+    float2 *fhat = fhat_base + P.vec_coef_off;
+    const long long *eoff = P.empty_off;
+    const int n_empty = P.n_empty;
     double sx = 0, sy = 0;
     for (int i = 0; i < nparts; ++i) {
         sx += part[i].x;
@@ -301,55 +325,61 @@ __global__ void sum_y_stage2(const double2 *part, int nparts, float2 *fhat, cons
     for (int e = 0; e < n_empty; ++e) fhat[eoff[e]] = make_float2((float)sx, (float)sy);
 }
 
-int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
-    DevPlan v = dev_view(p);
+static void adjoint_attrs() {
     static bool attr_done = false;
     if (!attr_done) {
         cudaFuncSetAttribute(adjoint_post_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(spread_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         attr_done = true;
     }
-    if (p.n_empty > 0) {
-        int nb = 256;
-        double2 *part = (double2 *)p.scratch;
-        stage_begin(p, ST_SUMY);
-        sum_y_stage1<<<nb, 256, 0, p.stream>>>(y, p.M, part, p.skip);
-        sum_y_stage2<<<1, 32, 0, p.stream>>>(part, nb, fhat, p.empty_off, p.n_empty, p.skip);
-        stage_end(p, ST_SUMY);
+}
+
+// The adjoint kernels for one problem (B.plans == null) or a batch of P problems.
+int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
+                   float2 *fhat, int n_items, int ctas, int n_blocks, int mr, long long max_grid_bytes,
+                   int max_fft_elems, int sm_count, long long max_grid_elems, bool any_empty, double2 *scratch) {
+    adjoint_attrs();
+    if (any_empty) {
+        const int nb = 256;
+        if (prof) stage_begin(*prof, ST_SUMY);
+        sum_y_stage1<<<dim3(nb, P), 256, 0, st>>>(v, B, y, scratch);
+        sum_y_stage2<<<P, 32, 0, st>>>(v, B, scratch, nb, fhat);
+        if (prof) stage_end(*prof, ST_SUMY);
     }
-    if (p.n_act == 0) return cuda_status(cudaGetLastError());
+    if (n_blocks == 0) return cuda_status(cudaGetLastError());
+    const size_t ssm = (size_t)max_grid_bytes;
+    if (prof) stage_begin(*prof, ST_SPREAD);
+    if (mr <= 3)
+        spread_f32<3><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items);
+    else
+        spread_f32<4><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items);
+    if (prof) stage_end(*prof, ST_SPREAD);
+    const long long n4 = max_grid_elems / 2;
+    const int rb = (int)std::max<long long>(1, std::min<long long>(sm_count * 8LL / std::max(1, P) + 1, (n4 + 255) / 256));
+    if (prof) stage_begin(*prof, ST_REDUCE);
+    reduce_partials_f32<<<dim3(rb, P), 256, 0, st>>>(v, B);
+    if (prof) stage_end(*prof, ST_REDUCE);
+    const size_t post_smem = (size_t)max_fft_elems * 2 * sizeof(float2);
+    if (prof) stage_begin(*prof, ST_POST);
+    adjoint_post_f32<<<n_blocks, 256, post_smem, st>>>(v, B, fhat);
+    if (prof) stage_end(*prof, ST_POST);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
+    DevPlan v = dev_view(p);
+    BatchArgs B;
+    std::memset(&B, 0, sizeof(B));
     if (p.M == 0) {
         cudaMemsetAsync(fhat, 0, sizeof(float2) * p.n_coeffs, p.stream);
-        if (p.n_empty > 0) {
-            double2 *part = (double2 *)p.scratch;
-            sum_y_stage2<<<1, 32, 0, p.stream>>>(part, 0, fhat, p.empty_off, p.n_empty, p.skip);
-        }
         return cuda_status(cudaGetLastError());
     }
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s) mr = p.h_terms[s].mr > 0 ? p.h_terms[s].mr : mr;
-    size_t ssm = (size_t)p.max_grid_bytes;
-    stage_begin(p, ST_SPREAD);
-    if (mr <= 2)
-        spread_f32<2><<<p.spread_ctas, SPREAD_THREADS, ssm, p.stream>>>(v, y, (float2 *)p.partials);
-    else if (mr == 3)
-        spread_f32<3><<<p.spread_ctas, SPREAD_THREADS, ssm, p.stream>>>(v, y, (float2 *)p.partials);
-    else
-        spread_f32<4><<<p.spread_ctas, SPREAD_THREADS, ssm, p.stream>>>(v, y, (float2 *)p.partials);
-    stage_end(p, ST_SPREAD);
-    long long n4 = p.grid_elems / 2;
-    int rb = (int)std::min<long long>(p.sm_count * 8LL, (n4 + 255) / 256);
-    stage_begin(p, ST_REDUCE);
-    reduce_partials_f32<<<rb, 256, 0, p.stream>>>((const float4 *)p.partials, (float4 *)p.grids, n4,
-                                                  p.spread_ctas, n4, p.skip);
-    stage_end(p, ST_REDUCE);
-    size_t post_smem = (size_t)p.max_fft_elems * 2 * sizeof(float2);
-    stage_begin(p, ST_POST);
-    adjoint_post_f32<<<p.n_act, 256, post_smem, p.stream>>>(v, (const float2 *)p.grids, fhat);
-    stage_end(p, ST_POST);
-    return cuda_status(cudaGetLastError());
+    return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.spread_ctas, p.spread_ctas, p.n_act, mr,
+                          p.max_grid_bytes, p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0,
+                          (double2 *)p.scratch);
 }
 
 }  // namespace agft

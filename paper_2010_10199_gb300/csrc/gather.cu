@@ -13,6 +13,7 @@
 // evaluates one window polynomial.  Lanes accumulate over all terms in
 // registers; a transposed reduce-scatter per tile finishes each node.
 #include <algorithm>
+#include <cstring>
 
 #include "device.cuh"
 #include "internal.cuh"
@@ -23,15 +24,29 @@ constexpr int G2_THREADS = 256;
 constexpr int G2_PTS = 8;                              // nodes per half-warp
 constexpr int G2_TILE = (G2_THREADS / 16) * G2_PTS;    // 128 nodes per CTA tile
 
+// Problem of a tile and the number of its terms still to run (0 when the
+// problem's skip flag is set).
+__device__ __forceinline__ const DevPlan &tile_plan(const DevPlan &single, const BatchArgs &B, int tile, int &lt) {
+    if (!B.plans) {
+        lt = tile;
+        return single;
+    }
+    const int p = B.tile_prob[tile];
+    lt = tile - B.tile0[p];
+    return B.plans[p];
+}
+
+__device__ __forceinline__ int tile_terms(const DevPlan &D) { return (D.skip && *D.skip) ? 0 : D.n_act; }
+
 template <int MR, int PITCH>
 __global__ void __launch_bounds__(G2_THREADS, 2)
-gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restrict__ fhat, float2 *__restrict__ f,
-            int n_tiles, int pitch_rt) {
+gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, float2 *__restrict__ f_base,
+            int n_tiles, int pitch_rt, long long max_grid_bytes, int dmax) {
     extern __shared__ __align__(128) float2 sm2[];
-    const int gb_el = (int)(P.max_grid_bytes / 8);
+    const int gb_el = (int)(max_grid_bytes / 8);
     float *xs = (float *)(sm2 + 2 * gb_el);                     // [d][G2_TILE]
-    uint64_t *bars = (uint64_t *)(xs + P.d * G2_TILE);
-    const int pitch = PITCH ? PITCH : pitch_rt;
+    uint64_t *bars = (uint64_t *)(xs + dmax * G2_TILE);
+    (void)pitch_rt;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -39,11 +54,7 @@ gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restric
     const int r = sub >> 3, k = sub & 7;
     const int hw = (tid >> 5) * 2 + (lane >> 4);
     const int pbase = hw * G2_PTS;
-    const long long M = P.M;
-    const int nt = P.n_act, d = P.d;
-    const float *__restrict__ X = P.x;
 
-    if (P.skip && *P.skip) return;
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -51,29 +62,48 @@ gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restric
     }
     __syncthreads();
 
-    float2 c0 = make_float2(0.f, 0.f);
-    for (int e = 0; e < P.n_empty; ++e) {
-        float2 c = fhat[P.empty_off[e]];
-        c0.x += c.x;
-        c0.y += c.y;
+    // first item of this CTA: its first tile whose problem has terms to run
+    int tile = blockIdx.x;
+    {
+        int lt;
+        while (tile < n_tiles && tile_terms(tile_plan(single, B, tile, lt)) == 0) tile += gridDim.x;
     }
-
-    const int my_tiles = (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-    const long long total_it = (long long)my_tiles * nt;
-    if (total_it > 0 && tid == 0) {
-        const Term &T0 = P.terms[P.act[0]];
+    if (tile < n_tiles && tid == 0) {
+        int lt;
+        const DevPlan &D0 = tile_plan(single, B, tile, lt);
+        const Term &T0 = D0.terms[D0.act[0]];
         mbar_expect_tx(&bars[0], (uint32_t)T0.grid_bytes);
-        bulk_g2s(sm2, grids + T0.grid_off, (uint32_t)T0.grid_bytes, &bars[0]);
+        bulk_g2s(sm2, D0.grids + T0.grid_off, (uint32_t)T0.grid_bytes, &bars[0]);
     }
 
     long long it = 0;
-    for (int ti = 0; ti < my_tiles; ++ti) {
-        const long long p0 = ((long long)blockIdx.x + (long long)ti * gridDim.x) * G2_TILE;
+    for (; tile < n_tiles;) {
+        int lt;
+        const DevPlan &D = tile_plan(single, B, tile, lt);
+        const int nt = tile_terms(D);
+        // the next tile of this CTA with terms to run (for the prefetch chain)
+        int next_tile = tile + gridDim.x;
+        {
+            int l2;
+            while (next_tile < n_tiles && tile_terms(tile_plan(single, B, next_tile, l2)) == 0) next_tile += gridDim.x;
+        }
+        const long long M = D.M;
+        const int d = D.d;
+        const float *__restrict__ X = D.x;
+        const float2 *fhat = fhat_base + D.vec_coef_off;
+        float2 *f = f_base + D.vec_node_off;
+        const long long p0 = (long long)lt * G2_TILE;
+        float2 c0 = make_float2(0.f, 0.f);
+        for (int e = 0; e < D.n_empty; ++e) {
+            float2 c = fhat[D.empty_off[e]];
+            c0.x += c.x;
+            c0.y += c.y;
+        }
         // stage the tile's coordinates (the previous tile ended with a barrier)
         for (int e = tid; e < d * G2_TILE; e += G2_THREADS) {
             const int c = e / G2_TILE, i = e - c * G2_TILE;
-            const long long p = p0 + i;
-            xs[e] = p < M ? __ldg(X + (long long)c * M + p) : 0.f;
+            const long long pp = p0 + i;
+            xs[e] = pp < M ? __ldg(X + (long long)c * M + pp) : 0.f;
         }
         __syncthreads();
 
@@ -92,27 +122,40 @@ gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restric
         for (int s = 0; s < nt; ++s, ++it) {
             const int b = (int)(it & 1);
             const uint32_t parity = (uint32_t)((it >> 1) & 1);
-            if (tid == 0 && it + 1 < total_it) {
-                const Term &Tn = P.terms[P.act[(s + 1) % nt]];
-                fence_proxy_async();
-                mbar_expect_tx(&bars[b ^ 1], (uint32_t)Tn.grid_bytes);
-                bulk_g2s(sm2 + (b ? 0 : gb_el), grids + Tn.grid_off, (uint32_t)Tn.grid_bytes, &bars[b ^ 1]);
+            if (tid == 0) {
+                const Term *Tn = nullptr;
+                const float2 *gn = nullptr;
+                if (s + 1 < nt) {
+                    Tn = &D.terms[D.act[s + 1]];
+                    gn = D.grids;
+                } else if (next_tile < n_tiles) {
+                    int l2;
+                    const DevPlan &Dn = tile_plan(single, B, next_tile, l2);
+                    Tn = &Dn.terms[Dn.act[0]];
+                    gn = Dn.grids;
+                }
+                if (Tn) {
+                    fence_proxy_async();
+                    mbar_expect_tx(&bars[b ^ 1], (uint32_t)Tn->grid_bytes);
+                    bulk_g2s(sm2 + (b ? 0 : gb_el), gn + Tn->grid_off, (uint32_t)Tn->grid_bytes, &bars[b ^ 1]);
+                }
             }
-            const Term &T = P.terms[P.act[s]];
+            const Term &T = D.terms[D.act[s]];
             const int order = T.order, n = T.n;
+            const int pitch = PITCH ? PITCH : T.stride;   // order-2 row pitch of this problem
             const float nf = (float)n, hn = 0.5f * (float)n, nm1 = (float)(n - 1);
             if (T.wc != cur_wc) {
-                const float *wsrc = P.windows[T.wc].c[k];
+                const float *wsrc = D.windows[T.wc].c[k];
 #pragma unroll
                 for (int i = 0; i < NCOEF; ++i) cc[i] = __ldg(wsrc + i);
                 cur_wc = T.wc;
             }
-            if (order == 2 && P.act_newgroup[s]) {
+            if (order == 2 && D.act_newgroup[s]) {
                 float rc[MR][NCOEF];
 #pragma unroll
                 for (int j = 0; j < MR; ++j)
 #pragma unroll
-                    for (int i = 0; i < NCOEF; ++i) rc[j][i] = __ldg(&P.windows[T.wr].c[r + 2 * j][i]);
+                    for (int i = 0; i < NCOEF; ++i) rc[j][i] = __ldg(&D.windows[T.wr].c[r + 2 * j][i]);
                 const float *xr = xs + T.row0 * G2_TILE + pbase;
 #pragma unroll
                 for (int i = 0; i < G2_PTS; ++i) {
@@ -124,7 +167,7 @@ gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restric
                     rbase[i] = ((int)fl + r) * pitch + k;   // stored row fl + r (row halo MR - 1)
                 }
             }
-            mbar_wait(&bars[b], parity, P.err, 1);
+            mbar_wait(&bars[b], parity, D.err, 1);
             const int boff = b ? gb_el : 0;
             const float *xc = xs + T.col * G2_TILE + pbase;
             if (order == 2) {
@@ -158,7 +201,7 @@ gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restric
                 }
             } else {
                 // order 3: rows (first, second) wrap modulo n; row weights evaluated directly
-                const Window &W = P.windows[T.wr];
+                const Window &W = D.windows[T.wr];
                 const int mr = T.mr, mc = T.mc, stride = T.stride;
                 const float *xa_p = xs + T.row0 * G2_TILE + pbase;
                 const float *xb_p = xs + T.row1 * G2_TILE + pbase;
@@ -210,48 +253,56 @@ gather2_f32(DevPlan P, const float2 *__restrict__ grids, const float2 *__restric
                 ay[i] = ky + __shfl_xor_sync(0xffffffffu, sy, o);
             }
         }
-        const long long p = p0 + pbase + (sub & 7);
-        if (sub < 8 && p < M) f[p] = make_float2(ax[0] + c0.x, ay[0] + c0.y);
+        const long long pp = p0 + pbase + (sub & 7);
+        if (sub < 8 && pp < M) f[pp] = make_float2(ax[0] + c0.x, ay[0] + c0.y);
+        tile = next_tile;
     }
 }
 
 template <int MR, int PITCH>
-static void launch_one(Plan &p, const DevPlan &v, const float2 *fhat, float2 *f, int n_tiles, size_t smem,
-                       int ctas) {
+static void launch_one(cudaStream_t st, const DevPlan &v, const BatchArgs &B, const float2 *fhat, float2 *f,
+                       int n_tiles, size_t smem, int ctas, int pitch, long long max_grid_bytes, int dmax) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(gather2_f32<MR, PITCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         attr = true;
     }
-    gather2_f32<MR, PITCH><<<ctas, G2_THREADS, smem, p.stream>>>(v, (const float2 *)p.grids, fhat, f, n_tiles,
-                                                                 p.pitch2);
+    gather2_f32<MR, PITCH><<<ctas, G2_THREADS, smem, st>>>(v, B, fhat, f, n_tiles, pitch, max_grid_bytes, dmax);
 }
 
 template <int MR>
-static void launch_mr(Plan &p, const DevPlan &v, const float2 *fhat, float2 *f, int n_tiles, size_t smem,
-                      int ctas) {
-    switch (p.pitch2) {
-        case 40: launch_one<MR, 40>(p, v, fhat, f, n_tiles, smem, ctas); break;
-        case 72: launch_one<MR, 72>(p, v, fhat, f, n_tiles, smem, ctas); break;
-        default: launch_one<MR, 0>(p, v, fhat, f, n_tiles, smem, ctas); break;
+static void launch_mr(cudaStream_t st, const DevPlan &v, const BatchArgs &B, const float2 *fhat, float2 *f,
+                      int n_tiles, size_t smem, int ctas, int pitch, long long max_grid_bytes, int dmax) {
+    switch (pitch) {
+        case 40: launch_one<MR, 40>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax); break;
+        case 72: launch_one<MR, 72>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax); break;
+        default: launch_one<MR, 0>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax); break;
     }
+}
+
+int gather_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, const float2 *fhat, float2 *f,
+                  int n_tiles, int mr, int pitch, long long max_grid_bytes, int dmax, int sm_count) {
+    const size_t smem = (size_t)max_grid_bytes * 2 + (size_t)dmax * G2_TILE * 4 + 64;
+    if (smem > (size_t)MAX_SMEM) return ANOVA_ERR_UNSUPPORTED;
+    if (n_tiles <= 0) return ANOVA_OK;
+    const int per_sm = smem * 2 <= (size_t)MAX_SMEM ? 2 : 1;
+    const int ctas = std::max(1, std::min(n_tiles, per_sm * sm_count));
+    if (mr <= 3)
+        launch_mr<3>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax);
+    else
+        launch_mr<4>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax);
+    return cuda_status(cudaGetLastError());
 }
 
 int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f) {
     DevPlan v = dev_view(p);
+    BatchArgs B;
+    std::memset(&B, 0, sizeof(B));
     const int n_tiles = (int)((p.M + G2_TILE - 1) / G2_TILE);
-    const size_t smem = (size_t)p.max_grid_bytes * 2 + (size_t)p.d * G2_TILE * 4 + 64;
-    if (smem > (size_t)MAX_SMEM) return ANOVA_ERR_UNSUPPORTED;
-    const int per_sm = smem * 2 <= (size_t)MAX_SMEM ? 2 : 1;
-    const int ctas = std::max(1, std::min(n_tiles, per_sm * p.sm_count));
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s)
         if (p.h_terms[s].mr > 0) mr = p.h_terms[s].mr;
-    if (mr <= 3)
-        launch_mr<3>(p, v, fhat, f, n_tiles, smem, ctas);
-    else
-        launch_mr<4>(p, v, fhat, f, n_tiles, smem, ctas);
-    return cuda_status(cudaGetLastError());
+    return gather_launch(p.stream, v, B, fhat, f, n_tiles, mr, p.pitch2, p.max_grid_bytes, p.d, p.sm_count);
 }
 
 }  // namespace agft

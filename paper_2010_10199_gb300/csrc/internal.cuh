@@ -88,6 +88,25 @@ struct DevPlan {
     const unsigned char *act_newgroup;  // per active entry: recompute row weights
     int n_act;
     const int *skip;          // if non-null and nonzero, kernels return at once
+    const float2 *grids;      // stored grids of this problem
+    float2 *partials;         // adjoint partial grids [spread_chunks][grid_elems]
+    int spread_chunks;        // node chunks of the adjoint (one partial grid each)
+    long long vec_node_off;   // offset of this problem's nodes in batched node vectors
+    long long vec_coef_off;   // offset of this problem's coefficients in batched coefficient vectors
+};
+
+// Work lists of a launch over several problems (a batch).  With plans == null
+// the launch covers the single problem given by the DevPlan parameter and
+// every table below is unused.
+struct BatchArgs {
+    const DevPlan *plans;     // device array [P]
+    int P;
+    const int *tile_prob;     // gather: problem of each tile of 128 nodes
+    const int *tile0;         // first tile of each problem
+    const int *item_prob;     // spread: problem of each work item (node chunk)
+    const int *item0;         // first item of each problem
+    const int *blk_prob;      // pre/post: problem of each (problem, active term) block
+    const int *blk0;          // first block of each problem
 };
 
 constexpr int N_STAGES = 7;

@@ -188,6 +188,11 @@ DevPlan dev_view(const Plan &p) {
     v.act_newgroup = p.act_newgroup;
     v.n_act = p.n_act;
     v.skip = p.skip;
+    v.grids = (const float2 *)p.grids;
+    v.partials = (float2 *)p.partials;
+    v.spread_chunks = p.spread_ctas;
+    v.vec_node_off = 0;
+    v.vec_coef_off = 0;
     return v;
 }
 

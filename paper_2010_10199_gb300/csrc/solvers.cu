@@ -40,20 +40,6 @@ static void free_work(SolverWork *W) {
 
 // ------------------------------------------------------------ reductions --
 
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x < 32) {
-        s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    }
-    return s;   // valid in thread 0
-}
-
 // sum of the RED_BLOCKS partials of slot k into st->red[k]
 __global__ void finish_sums(SolverState *st, const double *part, int nslots) {
     __shared__ double sh[32];
@@ -137,55 +123,9 @@ __global__ void k_normalize(const SolverState *st, float2 *v, long long n, int w
     }
 }
 
-// LSQR initial scalars after beta u = y, alpha v = A^H u
-__global__ void k_lsqr_init(SolverState *st) {
-    st->bnorm = st->beta;
-    st->phibar = st->beta;
-    st->rhobar = st->alpha;
-    st->anorm2 = 0.0;
-    st->iters = 0;
-    st->stop = 0;
-    st->status = 0;
-    if (st->alpha == 0.0 || st->beta == 0.0) {
-        st->done = 1;
-        st->stop = 1;
-    }
-}
+__global__ void k_lsqr_init(SolverState *st) { lsqr_init_dev(st); }
 
-// rotations of one LSQR step: uses st->beta (new) and st->red[0] = |v_new|^2
-__global__ void k_lsqr_scalars(SolverState *st) {
-    if (st->done) return;
-    const double alpha_old = st->alpha;
-    const double beta = st->beta;
-    const double alpha = sqrt(st->red[0]);
-    st->anorm2 += alpha_old * alpha_old + beta * beta + st->damp * st->damp;
-    const double rhohat = hypot(st->rhobar, st->damp);
-    const double c1 = st->rhobar / rhohat, s1 = st->damp / rhohat;
-    const double psi = s1 * st->phibar;
-    const double phibar1 = c1 * st->phibar;
-    const double rho = hypot(rhohat, beta);
-    if (!(rho > 0)) {   // alpha = beta = 0: the Krylov space is exhausted
-        st->stop = 1;
-        st->done = 1;
-        return;
-    }
-    const double c = rhohat / rho, s = beta / rho;
-    const double theta = s * alpha;
-    st->rhobar = -c * alpha;
-    const double phi = c * phibar1;
-    st->phibar = s * phibar1;
-    st->phi_rho = phi / rho;
-    st->theta_rho = theta / rho;
-    st->alpha = alpha;
-    st->res2 += psi * psi;   // damped residual: sum of the psi_k^2 so far plus phibar^2
-    st->rnorm = sqrt(st->res2 + st->phibar * st->phibar);
-    st->arnorm = alpha * fabs(s * phi);
-    st->iters += 1;
-    if (!isfinite(rho) || !isfinite(phi) || !isfinite(theta)) {
-        st->status = ANOVA_ERR_NOT_FINITE;
-        st->done = 1;
-    }
-}
+__global__ void k_lsqr_scalars(SolverState *st) { lsqr_scalars_dev(st); }
 
 // x += phi/rho w ; w = v - theta/rho w ; partial |x|^2
 __global__ void k_lsqr_update(const SolverState *st, float2 *x, float2 *w, const float2 *v, long long n,
@@ -208,27 +148,7 @@ __global__ void k_lsqr_update(const SolverState *st, float2 *x, float2 *w, const
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// stopping tests after an LSQR step (st->red[0] = |x|^2 of the scaled unknown)
-__global__ void k_lsqr_test(SolverState *st) {
-    if (st->done) return;
-    const double xnorm = sqrt(st->red[0]);
-    const double anorm = sqrt(st->anorm2);
-    // breakdown: alpha or beta at the accuracy level of the transforms
-    const double tiny = st->tiny_rel * anorm;
-    if (st->beta <= tiny || st->alpha <= tiny) {
-        st->stop = 1;
-        st->done = 1;
-    } else if (st->btol > 0 && st->rnorm <= st->btol * st->bnorm + st->atol * anorm * xnorm) {
-        st->stop = 2;
-        st->done = 1;
-    } else if (st->atol > 0 && st->arnorm <= st->atol * anorm * st->rnorm) {
-        st->stop = 3;
-        st->done = 1;
-    } else if (st->iters >= st->max_it) {
-        st->stop = 0;
-        st->done = 1;
-    }
-}
+__global__ void k_lsqr_test(SolverState *st) { lsqr_test_dev(st); }
 
 __global__ void k_weights(const double *w, float *ws, double *wd, long long n, int mode) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {

@@ -12,6 +12,7 @@
 //      per-node partial sums over all terms in registers; one transposed
 //      reduce-scatter per tile leaves node i's value in lane i.
 #include <cstdio>
+#include <cstring>
 
 #include "device.cuh"
 #include "internal.cuh"
@@ -22,10 +23,15 @@ __device__ __forceinline__ int freq_index(int q, int N) { return q < N / 2 ? q -
 
 // ------------------------------------------------------------ pre-pass ----
 
-__global__ void trafo_pre_f32(DevPlan P, const float2 *__restrict__ fhat, float2 *__restrict__ grids) {
+__global__ void trafo_pre_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int pb = B.plans ? B.blk_prob[blockIdx.x] : 0;
+    const DevPlan &P = B.plans ? B.plans[pb] : single;
+    const int sblk = B.plans ? (int)blockIdx.x - B.blk0[pb] : (int)blockIdx.x;
     if (P.skip && *P.skip) return;
-    const Term T = P.terms[P.act[blockIdx.x]];
+    const float2 *fhat = fhat_base + P.vec_coef_off;
+    float2 *grids = (float2 *)P.grids;
+    const Term T = P.terms[P.act[sblk]];
     const int n = T.n, s = T.order, N = T.N;
     int fe = n;
     for (int j = 1; j < s; ++j) fe *= n;
@@ -183,7 +189,9 @@ int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f) {
         attr_done = true;
     }
     stage_begin(p, ST_PRE);
-    trafo_pre_f32<<<p.n_act, 256, pre_smem, p.stream>>>(v, fhat, (float2 *)p.grids);
+    BatchArgs B;
+    std::memset(&B, 0, sizeof(B));
+    trafo_pre_f32<<<p.n_act, 256, pre_smem, p.stream>>>(v, B, fhat);
     stage_end(p, ST_PRE);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);

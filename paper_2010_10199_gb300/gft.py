@@ -119,6 +119,20 @@ def load(path: str | None = None):
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, vp,
                                         ctypes.POINTER(SolveInfo), ctypes.POINTER(ScreenStats)]
     lib.fista_screened_path.restype = ctypes.c_int
+    lib.anova_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(i32p), ctypes.POINTER(i32p), ctypes.POINTER(PlanOptions), vp]
+    lib.anova_batch_create.restype = ctypes.c_int
+    lib.anova_batch_destroy.argtypes = [vp]
+    lib.anova_batch_destroy.restype = None
+    lib.anova_batch_layout.argtypes = [vp, i64p, i64p]
+    lib.anova_batch_layout.restype = ctypes.c_int
+    lib.grouped_trafo_batch.argtypes = [vp, vp, vp]
+    lib.grouped_trafo_batch.restype = ctypes.c_int
+    lib.grouped_adjoint_batch.argtypes = [vp, vp, vp]
+    lib.grouped_adjoint_batch.restype = ctypes.c_int
+    lib.lsqr_solve_batch.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, vp, ctypes.POINTER(SolveInfo)]
+    lib.lsqr_solve_batch.restype = ctypes.c_int
     lib.anova_kkt_check.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double,
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     lib.anova_kkt_check.restype = ctypes.c_int
@@ -492,4 +506,80 @@ def screening_training_set(plan: "Plan", y, lambdas, path, w=None):
         prev = path[i].contiguous()
         lam_prev = lam[j]
     return torch.cat(Xs).contiguous(), torch.cat(ys).contiguous()
+
+
+# --------------------------------------------------------------- batches --
+
+class Batch:
+    """Independent problems run by one launch per kernel; vectors concatenated."""
+
+    def __init__(self, xs, terms_list, bandwidths_list, stream=None):
+        import torch
+        P = len(xs)
+        self.P = P
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._xs = [x.to(torch.float32).contiguous() for x in xs]
+        self.terms = [[tuple(u) for u in t] for t in terms_list]
+        d = (ctypes.c_int * P)(*[int(x.shape[0]) for x in self._xs])
+        M = (ctypes.c_int64 * P)(*[int(x.shape[1]) for x in self._xs])
+        xp = (ctypes.c_void_p * P)(*[x.data_ptr() for x in self._xs])
+        nt = (ctypes.c_int * P)(*[len(t) for t in self.terms])
+        self._td, self._bw = [], []
+        for t, b in zip(self.terms, bandwidths_list):
+            td = (ctypes.c_int32 * (3 * len(t)))()
+            bw = (ctypes.c_int32 * len(t))()
+            for i, u in enumerate(t):
+                for j in range(3):
+                    td[3 * i + j] = u[j] if j < len(u) else -1
+                bw[i] = int(b[i]) if len(u) else 0
+            self._td.append(td)
+            self._bw.append(bw)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        tdp = (i32p * P)(*[ctypes.cast(t, i32p) for t in self._td])
+        bwp = (i32p * P)(*[ctypes.cast(b, i32p) for b in self._bw])
+        h = ctypes.c_void_p()
+        _check("anova_batch_create", load().anova_batch_create(ctypes.byref(h), P, d, M, xp, nt, tdp, bwp, None,
+                                                               ctypes.c_void_p(self.stream.cuda_stream or None)))
+        self.handle = h
+        no = (ctypes.c_int64 * (P + 1))()
+        co = (ctypes.c_int64 * (P + 1))()
+        _check("anova_batch_layout", load().anova_batch_layout(h, no, co))
+        self.node_off = [no[i] for i in range(P + 1)]
+        self.coef_off = [co[i] for i in range(P + 1)]
+        self.device = self._xs[0].device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().anova_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def trafo(self, fhat):
+        import torch
+        out = torch.empty(self.node_off[-1], dtype=torch.complex64, device=self.device)
+        _check("grouped_trafo_batch", load().grouped_trafo_batch(self.handle, ctypes.c_void_p(fhat.data_ptr()),
+                                                                 ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def adjoint(self, y):
+        import torch
+        out = torch.empty(self.coef_off[-1], dtype=torch.complex64, device=self.device)
+        _check("grouped_adjoint_batch", load().grouped_adjoint_batch(self.handle, ctypes.c_void_p(y.data_ptr()),
+                                                                     ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def lsqr(self, y, lam, max_it=30):
+        import torch
+        out = torch.empty(self.coef_off[-1], dtype=torch.complex64, device=self.device)
+        infos = (SolveInfo * self.P)()
+        rc = load().lsqr_solve_batch(self.handle, ctypes.c_void_p(y.data_ptr()), float(lam), int(max_it),
+                                     ctypes.c_void_p(out.data_ptr()), infos)
+        if rc not in (0, -5):
+            _check("lsqr_solve_batch", rc)
+        return out, [infos[i].as_dict() for i in range(self.P)], rc
 
