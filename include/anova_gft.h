@@ -79,7 +79,10 @@ typedef struct {
     int window_m_col;   /* window half-width along the fastest grid axis (0: auto) */
     int window_m_row;   /* window half-width along the other axes (0: auto) */
     double sigma;       /* minimal oversampling factor n_u / N_u (0: 2.0) */
-    int n_ctas;         /* persistent CTAs of the spreading/gathering kernels (0: auto) */
+    int n_ctas;         /* adjoint: most node chunks (partial grids) per term, <= 64 (0: auto) */
+    int node_sort;      /* adjoint: 0 = keep a copy of the nodes sorted by grid cell for every
+                           term of order <= 2 when it fits in half the free device memory
+                           (12 bytes per node and term); -1 = never */
 } anova_plan_options;
 
 /*

@@ -1,13 +1,12 @@
 // Adjoint grouped transform fhat = F^H y (stacked adjoint after the error
 // remark, Sec. 3), FP32.
 //
-//   1. spread: term-outer.  CTA c owns a contiguous range of nodes; for every
-//      term it accumulates y_j times the window into a shared-memory copy of
-//      the term's stored grid (halos included) with shared-memory atomics,
+//   1. spread: work items (term, node chunk) from a global queue.  An item
+//      accumulates y_j times the window into a shared-memory copy of the
+//      term's stored grid (halos included) with shared-memory atomics,
 //      half-warp per node (2 rows x 8 columns of the window per instruction),
-//      then writes its partial grid to partials[c].
-//   2. reduce_partials: grid = sum_c partials[c] in a fixed order
-//      (deterministic across runs for a fixed CTA count).
+//      then writes it to partial grid z of the term (z = chunk index).
+//   2. reduce_partials: grid = sum_z partials[z] in a fixed order.
 //   3. adjoint_post: per term, fold the halos back onto the periodic grid, FFT
 //      with sign -, multiply by the deconvolution factors and crop the block
 //      (I_N minus {0})^{|u|}.
@@ -27,109 +26,345 @@ __device__ __forceinline__ void red_add(float *addr, float v) {
 
 __device__ __forceinline__ int freq_index_a(int q, int N) { return q < N / 2 ? q - N / 2 : q - N / 2 + 1; }
 
+constexpr int SP_CH = 512;   // nodes staged per block of a work item
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// staging area after the grid: the larger of the unsorted layout
+// (float4 [2][SP_CH]) and the sorted one (float2 [3][SP_CH] coordinates,
+// int [3][SP_CH] node indices, float2 [2][SP_CH] values of y)
+constexpr size_t SP_STAGE_BYTES = 3 * SP_CH * 8 + 3 * SP_CH * 4 + 2 * SP_CH * 8;
+static_assert(SP_STAGE_BYTES >= 2 * SP_CH * 16, "staging area");
+
+size_t spread_smem_bytes(long long max_grid_bytes) {
+    return (size_t)max_grid_bytes + SP_STAGE_BYTES + 16;   // grid, node blocks, item slot
+}
+
+int spread_ctas_per_sm(long long max_grid_bytes) {
+    // shared memory per CTA plus the 1 KB the hardware reserves per CTA
+    const size_t per = spread_smem_bytes(max_grid_bytes) + 1024;
+    return (int)std::max<size_t>(1, std::min<size_t>(SPREAD_MAX_CTAS_PER_SM, (size_t)(MAX_SMEM + 1024) / per));
+}
+
+int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count) {
+    const long long resident = (long long)spread_ctas_per_sm(max_grid_bytes) * sm_count;
+    long long K = (3 * resident + std::max(1, n_act_total) - 1) / std::max(1, n_act_total);
+    K = std::min<long long>(K, (M + 2047) / 2048);
+    K = std::min<long long>(K, kmax);
+    return (int)std::max<long long>(1, K);
+}
+
+int append_spread_items(const Plan &p, int prob, int K, int4 *out) {
+    int n = 0;
+    for (int order = MAX_ORDER; order >= 1; --order)
+        for (int s = 0; s < p.n_act; ++s) {
+            if (p.h_terms[p.h_act[s]].order != order) continue;
+            for (int z = 0; z < K; ++z) out[n++] = make_int4(prob, s, z, K);
+        }
+    return n;
+}
+
+// Sorted item: the item's nodes in cell order of its term.  Blocks of SP_CH
+// nodes pass through shared memory: coordinates and original indices by
+// cp.async two blocks ahead, the values y[index] by cp.async one block ahead
+// (their addresses come from the staged indices).  Each half-warp walks a run
+// of SP_CH / 16 consecutive nodes and sums the contributions of a cell in
+// registers (lane (r, k): column tap k, rows r, r + 2, ..); when the cell
+// changes, or at the end of the run, it adds the sums to the shared grid.
+// Order 1: the two lane groups r = 0, 1 take alternate nodes of the run.
 template <int MR>
-__global__ void __launch_bounds__(SPREAD_THREADS)
-spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n_items) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float2 *S = (float2 *)smem_raw;
+__device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
+                                                   long long j0, long long j1, float2 *S, unsigned char *stg_raw,
+                                                   const float cc[NCOEF], const float rcf[NCOEF]) {
+    constexpr int RUN = SP_CH / 16;
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int sub = lane & 15;
+    const int lane = tid & 31, half = lane >> 4, sub = lane & 15;
     const int r = sub >> 3, k = sub & 7;
-    const int hw = (tid >> 5) * 2 + (lane >> 4);
-    const int nhw = SPREAD_THREADS / 16;
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int pb = B.plans ? B.item_prob[item] : 0;
-    const DevPlan &P = B.plans ? B.plans[pb] : single;
-    const int kc = B.plans ? item - B.item0[pb] : item;   // node chunk of this problem
-    if (P.skip && *P.skip) continue;
+    const int hw = (tid >> 5) * 2 + half;
+    const int n = T.n, stride = T.stride, order = T.order;
     const long long M = P.M;
-    const long long j0 = M * (long long)kc / P.spread_chunks;
-    const long long j1 = M * (long long)(kc + 1) / P.spread_chunks;
-    const float *__restrict__ X = P.x;
-    const float2 *__restrict__ y = y_base + P.vec_node_off;
-    float2 *mypart = P.partials + (long long)kc * P.grid_elems;
-    for (int s = 0; s < P.n_act; ++s) {
-        const Term &T = P.terms[P.act[s]];
-        const int order = T.order, n = T.n, stride = T.stride;
-        const long long elems = T.grid_bytes / 8;
-        float4 *S4 = (float4 *)S;
-        for (long long e = tid; e < elems / 2; e += blockDim.x) S4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-        float cc[NCOEF];
-        const float *wsrc = P.windows[T.wc].c[k];
-#pragma unroll
-        for (int i = 0; i < NCOEF; ++i) cc[i] = __ldg(wsrc + i);
+    const float2 *sxp = P.sx + (long long)T.sort_slot * M;
+    const int *spp = P.sperm + (long long)T.sort_slot * M;
+    float2 *cbuf = (float2 *)stg_raw;          // [3][SP_CH]
+    int *pbuf = (int *)(cbuf + 3 * SP_CH);     // [3][SP_CH]
+    float2 *ybuf = (float2 *)(pbuf + 3 * SP_CH);  // [2][SP_CH]
+    const long long nblk = (j1 - j0 + SP_CH - 1) / SP_CH;
+    auto count = [&](long long c) { return (int)min((long long)SP_CH, j1 - (j0 + c * SP_CH)); };
+    auto stage_a = [&](long long c) {
+        const long long a = j0 + c * SP_CH;
+        const int cnt = count(c), b = (int)(c % 3) * SP_CH;
+        for (int e = tid; e < cnt; e += SPREAD_THREADS) {
+            cp_async8(&cbuf[b + e], sxp + a + e);
+            cp_async4(&pbuf[b + e], spp + a + e);
+        }
+    };
+    // reads indices this thread staged itself (same e), so its own wait suffices
+    auto stage_b = [&](long long c) {
+        const int cnt = count(c), b = (int)(c % 3) * SP_CH, yb = (int)(c & 1) * SP_CH;
+        for (int e = tid; e < cnt; e += SPREAD_THREADS) cp_async8(&ybuf[yb + e], y + pbuf[b + e]);
+    };
+    if (nblk > 0) stage_a(0);
+    cp_async_commit();
+    if (nblk > 1) stage_a(1);
+    cp_async_commit();
+    cp_async_wait1();
+    if (nblk > 0) stage_b(0);
+    cp_async_commit();
+    for (long long c = 0; c < nblk; ++c) {
+        cp_async_wait0();
         __syncthreads();
-        const float *xc = X + (long long)T.col * M;
+        if (c + 1 < nblk) stage_b(c + 1);
+        cp_async_commit();
+        if (c + 2 < nblk) stage_a(c + 2);
+        cp_async_commit();
+        const float2 *cb = cbuf + (int)(c % 3) * SP_CH;
+        const float2 *yb = ybuf + (int)(c & 1) * SP_CH;
+        const int cnt = count(c);
+        const int i0 = hw * RUN;
         if (order == 2) {
-            float rc[MR][NCOEF];
+            int cfa = -1, cfb = 0;
+            float ax[MR], ay[MR];
 #pragma unroll
-            for (int j = 0; j < MR; ++j)
+            for (int j = 0; j < MR; ++j) ax[j] = ay[j] = 0.f;
+            auto flush = [&]() {
+                float *base = (float *)(S + (cfa + r) * stride + cfb + k);
 #pragma unroll
-                for (int i = 0; i < NCOEF; ++i) rc[j][i] = __ldg(&P.windows[T.wr].c[r + 2 * j][i]);
-            const float *xr = X + (long long)T.row0 * M;
-            for (long long p = j0 + hw; p < j1; p += nhw) {
-                float2 yv = __ldg(y + p);
+                for (int j = 0; j < MR; ++j) {
+                    red_add(base + 4 * j * stride, ax[j]);
+                    red_add(base + 4 * j * stride + 1, ay[j]);
+                    ax[j] = ay[j] = 0.f;
+                }
+            };
+            // both half-warps of a warp run RUN steps (shuffles); steps past
+            // the block end compute on node 0 and add nothing
+            for (int t = 0; t < RUN; ++t) {
+                const int i = i0 + t;
+                const bool ok = i < cnt;
+                const float2 q = cb[ok ? i : 0];
                 float ta, tb;
-                int fa = grid_pos(__ldg(xr + p), n, ta);
-                int fb = grid_pos(__ldg(xc + p), n, tb);
-                float cw = horner8(cc, 2.f * tb - 1.f);
-                float va = 2.f * ta - 1.f;
-                float yx = yv.x * cw, yy = yv.y * cw;
+                const int fa = grid_pos(q.x, n, ta);
+                const int fb = grid_pos(q.y, n, tb);
+                const float cw = horner8(cc, 2.f * tb - 1.f);
+                const float rw = horner8(rcf, 2.f * ta - 1.f);
+                float w[MR];
+#pragma unroll
+                for (int j = 0; j < MR; ++j) w[j] = __shfl_sync(0xffffffffu, rw, (half << 4) | (r + 2 * j));
+                if (ok) {
+                    if (fa != cfa || fb != cfb) {
+                        if (cfa >= 0) flush();
+                        cfa = fa;
+                        cfb = fb;
+                    }
+                    const float2 yv = yb[i];
+                    const float yx = yv.x * cw, yy = yv.y * cw;
+#pragma unroll
+                    for (int j = 0; j < MR; ++j) {
+                        ax[j] = fmaf(yx, w[j], ax[j]);
+                        ay[j] = fmaf(yy, w[j], ay[j]);
+                    }
+                }
+            }
+            if (cfa >= 0) flush();
+        } else {
+            int cfb = -1;
+            float ax = 0.f, ay = 0.f;
+            for (int t = r; t < RUN; t += 2) {
+                const int i = i0 + t;
+                if (i >= cnt) break;
+                const float2 q = cb[i];
+                float tb;
+                const int fb = grid_pos(q.y, n, tb);
+                if (fb != cfb) {
+                    if (cfb >= 0) {
+                        float *base = (float *)(S + cfb + k);
+                        red_add(base, ax);
+                        red_add(base + 1, ay);
+                        ax = ay = 0.f;
+                    }
+                    cfb = fb;
+                }
+                const float cw = horner8(cc, 2.f * tb - 1.f);
+                const float2 yv = yb[i];
+                ax = fmaf(yv.x, cw, ax);
+                ay = fmaf(yv.y, cw, ay);
+            }
+            if (cfb >= 0) {
+                float *base = (float *)(S + cfb + k);
+                red_add(base, ax);
+                red_add(base + 1, ay);
+            }
+        }
+        __syncthreads();
+    }
+    cp_async_wait0();
+}
+
+// Unsorted item (order 3, or a plan without sorted copies): the item's nodes
+// in their original order, staged as float4 (first-row coordinate, last
+// coordinate, y) one block ahead; every node adds its window to the shared
+// grid with shared-memory atomics.
+template <int MR>
+__device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
+                                                     long long j0, long long j1, float2 *S, unsigned char *stg_raw,
+                                                     const float cc[NCOEF], const float rcf[NCOEF]) {
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, half = lane >> 4, sub = lane & 15;
+    const int r = sub >> 3, k = sub & 7;
+    const int warp = tid >> 5;
+    constexpr int NW = SPREAD_THREADS / 32;
+    const int order = T.order, n = T.n, stride = T.stride;
+    const long long M = P.M;
+    float4 *stage = (float4 *)stg_raw;   // [2][SP_CH]
+    const float *__restrict__ X = P.x;
+    const float *xr = X + (long long)(order >= 2 ? T.row0 : T.col) * M;
+    const float *xc = X + (long long)T.col * M;
+    const float *xr1 = order == 3 ? X + (long long)T.row1 * M : nullptr;
+    const long long nblk = (j1 - j0 + SP_CH - 1) / SP_CH;
+    auto stage_block = [&](long long c, int buf) {
+        const long long a = j0 + c * SP_CH;
+        const int cnt = (int)min((long long)SP_CH, j1 - a);
+        float4 *dst = stage + buf * SP_CH;
+        for (int e = tid; e < cnt; e += SPREAD_THREADS) {
+            const long long j = a + e;
+            cp_async4(&dst[e].x, xr + j);
+            cp_async4(&dst[e].y, xc + j);
+            cp_async8(&dst[e].z, y + j);
+        }
+    };
+    if (nblk > 0) stage_block(0, 0);
+    cp_async_commit();
+    for (long long c = 0; c < nblk; ++c) {
+        if (c + 1 < nblk) stage_block(c + 1, (int)((c + 1) & 1));
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const float4 *stg = stage + (int)(c & 1) * SP_CH;
+        const long long a = j0 + c * SP_CH;
+        const int cnt = (int)min((long long)SP_CH, j1 - a);
+        if (order == 2) {
+            for (int i0 = 2 * warp; i0 < cnt; i0 += 2 * NW) {
+                const int i = i0 + half;
+                const bool ok = i < cnt;
+                const float4 q = stg[ok ? i : i0];
+                float ta, tb;
+                const int fa = grid_pos(q.x, n, ta);
+                const int fb = grid_pos(q.y, n, tb);
+                const float cw = horner8(cc, 2.f * tb - 1.f);
+                const float rw = horner8(rcf, 2.f * ta - 1.f);
+                const float yx = q.z * cw, yy = q.w * cw;
                 float *base = (float *)(S + (fa + r) * stride + fb + k);
 #pragma unroll
                 for (int j = 0; j < MR; ++j) {
-                    float w = horner8(rc[j], va);
-                    red_add(base + 4 * j * stride, yx * w);
-                    red_add(base + 4 * j * stride + 1, yy * w);
+                    const float w = __shfl_sync(0xffffffffu, rw, (half << 4) | (r + 2 * j));
+                    if (ok) {
+                        red_add(base + 4 * j * stride, yx * w);
+                        red_add(base + 4 * j * stride + 1, yy * w);
+                    }
                 }
             }
         } else if (order == 1) {
-            if (r == 0) {
-                for (long long p = j0 + hw; p < j1; p += nhw) {
-                    float2 yv = __ldg(y + p);
-                    float tb;
-                    int fb = grid_pos(__ldg(xc + p), n, tb);
-                    float cw = horner8(cc, 2.f * tb - 1.f);
-                    float *base = (float *)(S + fb + k);
-                    red_add(base, yv.x * cw);
-                    red_add(base + 1, yv.y * cw);
-                }
+            const int g = tid >> 3;
+            for (int i = g; i < cnt; i += SPREAD_THREADS / 8) {
+                const float4 q = stg[i];
+                float tb;
+                const int fb = grid_pos(q.y, n, tb);
+                const float cw = horner8(cc, 2.f * tb - 1.f);
+                float *base = (float *)(S + fb + k);
+                red_add(base, q.z * cw);
+                red_add(base + 1, q.w * cw);
             }
         } else {
             const Window &W = P.windows[T.wr];
             const int mr = T.mr, mc = T.mc;
-            const float *xa_p = X + (long long)T.row0 * M;
-            const float *xb_p = X + (long long)T.row1 * M;
-            for (long long p = j0 + hw; p < j1; p += nhw) {
-                float2 yv = __ldg(y + p);
+            const int hw = warp * 2 + half;
+            for (int i = hw; i < cnt; i += SPREAD_THREADS / 16) {
+                const float4 q = stg[i];
                 float ta, tb, tc;
-                int fa = grid_pos(__ldg(xa_p + p), n, ta);
-                int fb = grid_pos(__ldg(xb_p + p), n, tb);
-                int fc = grid_pos(__ldg(xc + p), n, tc);
-                float cw = horner8(cc, 2.f * tc - 1.f);
-                int cidx = wrap(fc - mc + 1 + k, n);
-                float yx = yv.x * cw, yy = yv.y * cw;
+                const int fa = grid_pos(q.x, n, ta);
+                const int fb = grid_pos(__ldg(xr1 + a + i), n, tb);
+                const int fc = grid_pos(q.y, n, tc);
+                const float cw = horner8(cc, 2.f * tc - 1.f);
+                const int cidx = wrap(fc - mc + 1 + k, n);
+                const float yx = q.z * cw, yy = q.w * cw;
                 for (int ia = 0; ia < 2 * mr; ++ia) {
-                    float wa = kb_direct(ta + (float)(mr - 1 - ia), mr, W.b, W.inv_psi0);
-                    int ra = wrap(fa - mr + 1 + ia, n);
+                    const float wa = kb_direct(ta + (float)(mr - 1 - ia), mr, W.b, W.inv_psi0);
+                    const int ra = wrap(fa - mr + 1 + ia, n);
                     for (int jb = r; jb < 2 * mr; jb += 2) {
-                        float wb = kb_direct(tb + (float)(mr - 1 - jb), mr, W.b, W.inv_psi0);
-                        int rb = wrap(fb - mr + 1 + jb, n);
-                        float *c = (float *)(S + (ra * n + rb) * stride + cidx);
-                        float w = wa * wb;
-                        red_add(c, yx * w);
-                        red_add(c + 1, yy * w);
+                        const float wb = kb_direct(tb + (float)(mr - 1 - jb), mr, W.b, W.inv_psi0);
+                        const int rb = wrap(fb - mr + 1 + jb, n);
+                        float *cp = (float *)(S + (ra * n + rb) * stride + cidx);
+                        const float w = wa * wb;
+                        red_add(cp, yx * w);
+                        red_add(cp + 1, yy * w);
                     }
                 }
             }
         }
         __syncthreads();
-        float4 *dst = (float4 *)(mypart + T.grid_off);
-        for (long long e = tid; e < elems / 2; e += blockDim.x) dst[e] = S4[e];
+    }
+    cp_async_wait0();
+}
+
+// One work item (x = problem, y = active term, z = node chunk, w = chunks per
+// term) spreads nodes [M z / w, M (z+1) / w) of one term (in the term's cell
+// order if the plan keeps sorted copies and the term has order <= 2, else in
+// the original order) into a shared-memory copy of the term's stored grid
+// (halos included) and writes it to partial grid z of its problem.  CTAs take
+// items from a global counter.
+template <int MR>
+__global__ void __launch_bounds__(SPREAD_THREADS, 3)
+spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n_items, int *counter,
+           long long max_grid_bytes) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2 *S = (float2 *)smem_raw;
+    unsigned char *stg_raw = smem_raw + max_grid_bytes;
+    int &s_item = *(int *)(stg_raw + SP_STAGE_BYTES);
+    const int tid = threadIdx.x;
+    const int k = tid & 7;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        const int4 itm = B.items[item];
+        const DevPlan &P = B.plans ? B.plans[itm.x] : single;
+        if (P.skip && *P.skip) continue;
+        const Term &T = P.terms[P.act[itm.y]];
+        const long long M = P.M;
+        const long long j0 = M * itm.z / itm.w, j1 = M * (itm.z + 1) / itm.w;
+        const long long elems = T.grid_bytes / 8;
+        float4 *S4 = (float4 *)S;
+        for (long long e = tid; e < elems / 2; e += SPREAD_THREADS) S4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 *y = y_base + P.vec_node_off;
+        float cc[NCOEF], rcf[NCOEF];
+        {
+            const float *wsrc = P.windows[T.wc].c[k];
+            const float *rsrc = P.windows[T.wr].c[min(k, 2 * MR - 1)];
+#pragma unroll
+            for (int i = 0; i < NCOEF; ++i) {
+                cc[i] = __ldg(wsrc + i);
+                rcf[i] = __ldg(rsrc + i);
+            }
+        }
+        __syncthreads();   // grid zeroed before any addition
+        if (T.sort_slot >= 0 && P.sx)
+            spread_sorted_item<MR>(P, T, y, j0, j1, S, stg_raw, cc, rcf);
+        else
+            spread_unsorted_item<MR>(P, T, y, j0, j1, S, stg_raw, cc, rcf);
+        __syncthreads();
+        float4 *dst = (float4 *)(P.partials + (long long)itm.z * P.grid_elems + T.grid_off);
+        for (long long e = tid; e < elems / 2; e += SPREAD_THREADS) dst[e] = S4[e];
         __syncthreads();
     }
-  }
 }
 
 __global__ void reduce_partials_f32(DevPlan single, BatchArgs B) {
@@ -337,7 +572,7 @@ static void adjoint_attrs() {
 
 // The adjoint kernels for one problem (B.plans == null) or a batch of P problems.
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
-                   float2 *fhat, int n_items, int ctas, int n_blocks, int mr, long long max_grid_bytes,
+                   float2 *fhat, int n_items, int *counter, int n_blocks, int mr, long long max_grid_bytes,
                    int max_fft_elems, int sm_count, long long max_grid_elems, bool any_empty, double2 *scratch) {
     adjoint_attrs();
     if (any_empty) {
@@ -348,12 +583,14 @@ int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArg
         if (prof) stage_end(*prof, ST_SUMY);
     }
     if (n_blocks == 0) return cuda_status(cudaGetLastError());
-    const size_t ssm = (size_t)max_grid_bytes;
+    const size_t ssm = spread_smem_bytes(max_grid_bytes);
+    const int ctas = std::max(1, std::min(n_items, spread_ctas_per_sm(max_grid_bytes) * sm_count));
     if (prof) stage_begin(*prof, ST_SPREAD);
+    cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (mr <= 3)
-        spread_f32<3><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items);
+        spread_f32<3><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items, counter, max_grid_bytes);
     else
-        spread_f32<4><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items);
+        spread_f32<4><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items, counter, max_grid_bytes);
     if (prof) stage_end(*prof, ST_SPREAD);
     const long long n4 = max_grid_elems / 2;
     const int rb = (int)std::max<long long>(1, std::min<long long>(sm_count * 8LL / std::max(1, P) + 1, (n4 + 255) / 256));
@@ -371,15 +608,15 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
     DevPlan v = dev_view(p);
     BatchArgs B;
     std::memset(&B, 0, sizeof(B));
+    B.items = p.items;
     if (p.M == 0) {
         cudaMemsetAsync(fhat, 0, sizeof(float2) * p.n_coeffs, p.stream);
         return cuda_status(cudaGetLastError());
     }
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s) mr = p.h_terms[s].mr > 0 ? p.h_terms[s].mr : mr;
-    return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.spread_ctas, p.spread_ctas, p.n_act, mr,
-                          p.max_grid_bytes, p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0,
-                          (double2 *)p.scratch);
+    return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.n_items, p.counter, p.n_act, mr, p.max_grid_bytes,
+                          p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0, (double2 *)p.scratch);
 }
 
 }  // namespace agft

@@ -4,7 +4,7 @@
 // other (after eq. (somafm) and after the stacked adjoint, Sec. 3); independent
 // problems are independent in the same way.  A batch holds one ordinary plan
 // per problem plus device work lists: (problem, tile of 128 nodes) for the
-// gather, (problem, node chunk) for the spread and (problem, term) for the
+// gather, (problem, term, node chunk) for the spread and (problem, term) for the
 // deconvolution/FFT passes, so each kernel is launched once for all problems
 // and the GPU is filled even when every single problem is small.  Vectors of a
 // batch are the concatenation of the problems' vectors.
@@ -23,9 +23,6 @@ namespace agft {
 
 int gather_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, const float2 *fhat, float2 *f, int n_tiles,
                   int mr, int pitch, long long max_grid_bytes, int dmax, int sm_count);
-int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
-                   float2 *fhat, int n_items, int ctas, int n_blocks, int mr, long long max_grid_bytes,
-                   int max_fft_elems, int sm_count, long long max_grid_elems, bool any_empty, double2 *scratch);
 __global__ void trafo_pre_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base);
 
 constexpr int BRB = 32;   // partial sums per problem segment
@@ -37,7 +34,9 @@ struct Batch {
     std::vector<long long> node_off, coef_off;   // [P + 1]
     std::vector<DevPlan> views;
     DevPlan *d_plans = nullptr;
-    int *d_tables = nullptr;   // tile_prob | tile0 | item_prob | item0 | blk_prob | blk0
+    int *d_tables = nullptr;   // tile_prob | tile0 | blk_prob | blk0
+    int4 *d_items = nullptr;   // spread work items
+    int *counter = nullptr;
     BatchArgs args;
     int n_tiles = 0, n_items = 0, n_blocks = 0, mr = 3, pitch = 0, dmax = 1, max_fft = 1, sm_count = 152;
     long long max_grid_bytes = 16, max_grid_elems = 0;
@@ -55,7 +54,7 @@ struct Batch {
 static void free_batch(Batch *b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    void *bufs[] = {b->d_plans, b->d_tables, b->scratch, b->u, b->tM, b->v, b->w, b->x, b->tn, b->st, b->part,
+    void *bufs[] = {b->d_plans, b->d_tables, b->d_items, b->counter, b->scratch, b->u, b->tM, b->v, b->w, b->x, b->tn, b->st, b->part,
                     b->d_node_off, b->d_coef_off};
     for (void *q : bufs)
         if (q) cudaFree(q);
@@ -88,8 +87,7 @@ static int batch_trafo(Batch &b, cudaStream_t st, const float2 *fhat, float2 *f)
 }
 
 static int batch_adjoint(Batch &b, cudaStream_t st, const float2 *y, float2 *fhat) {
-    const int ctas = std::max(1, std::min(b.n_items, 4 * b.sm_count));
-    return adjoint_launch(nullptr, st, b.views[0], b.args, b.P, y, fhat, b.n_items, ctas, b.n_blocks, b.mr,
+    return adjoint_launch(nullptr, st, b.views[0], b.args, b.P, y, fhat, b.n_items, b.counter, b.n_blocks, b.mr,
                           b.max_grid_bytes, b.max_fft, b.sm_count, b.max_grid_elems, b.any_empty, b.scratch);
 }
 
@@ -238,7 +236,8 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
     b->stream = (cudaStream_t)stream;
     b->node_off.assign(n_problems + 1, 0);
     b->coef_off.assign(n_problems + 1, 0);
-    std::vector<int> tile_prob, tile0, item_prob, item0, blk_prob, blk0;
+    std::vector<int> tile_prob, tile0, blk_prob, blk0;
+    int total_act = 0;
     int pitch = -1;
     bool mixed_pitch = false;
     for (int p = 0; p < n_problems; ++p) {
@@ -268,9 +267,7 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
         tile0.push_back(b->n_tiles);
         for (int t = 0; t < tiles; ++t) tile_prob.push_back(p);
         b->n_tiles += tiles;
-        item0.push_back(b->n_items);
-        for (int t = 0; t < pl.spread_ctas; ++t) item_prob.push_back(p);
-        b->n_items += pl.spread_ctas;
+        total_act += pl.n_act;
         blk0.push_back(b->n_blocks);
         for (int t = 0; t < pl.n_act; ++t) blk_prob.push_back(p);
         b->n_blocks += pl.n_act;
@@ -288,9 +285,23 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
         b->sm_count = pl.sm_count;
     }
     b->pitch = mixed_pitch || pitch < 0 ? 0 : pitch;
+    // spread items: every problem's active terms split into K_p node chunks,
+    // K_p sized for all problems sharing the GPU
+    std::vector<int4> items;
+    for (int p = 0; p < n_problems; ++p) {
+        Plan &pl = b->plans[p]->p;
+        const int K = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count);
+        b->views[p].spread_chunks = K;
+        const size_t at = items.size();
+        items.resize(at + (size_t)pl.n_act * K);
+        append_spread_items(pl, p, K, items.data() + at);
+    }
+    b->n_items = (int)items.size();
     cudaError_t e = cudaMalloc(&b->d_plans, sizeof(DevPlan) * n_problems);
-    const size_t nt = tile_prob.size() + tile0.size() + item_prob.size() + item0.size() + blk_prob.size() + blk0.size();
+    const size_t nt = tile_prob.size() + tile0.size() + blk_prob.size() + blk0.size();
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tables, sizeof(int) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int4) * std::max<size_t>(1, items.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->scratch, sizeof(double2) * 256 * n_problems);
     if (e != cudaSuccess) {
         free_batch(b);
@@ -308,11 +319,12 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
     b->args.P = n_problems;
     b->args.tile_prob = put(tile_prob);
     b->args.tile0 = put(tile0);
-    b->args.item_prob = put(item_prob);
-    b->args.item0 = put(item0);
+    b->args.items = b->d_items;
     b->args.blk_prob = put(blk_prob);
     b->args.blk0 = put(blk0);
     e = cudaMemcpyAsync(b->d_tables, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_status(e);

@@ -25,6 +25,8 @@ constexpr int GATHER_THREADS = 256;
 constexpr int PTS_PER_HALF = 16; // points per half-warp in the gather tile
 constexpr int GATHER_TILE = (GATHER_THREADS / 16) * PTS_PER_HALF;  // 256 points
 constexpr int SPREAD_THREADS = 256;
+constexpr int SPREAD_MAX_CTAS_PER_SM = 4;
+constexpr int SPREAD_MAX_K = 64;     // largest number of node chunks (partial grids) per term
 constexpr int MAX_SMEM = 227 * 1024;
 
 // One window shape (half-width m, oversampling sigma).  Tap j of a node with
@@ -58,7 +60,7 @@ struct Term {
     int new_rowgroup;   // 1 if the row weights cached by the gather must be recomputed
     int hr, hc;         // halo widths (rows, columns): stored index = periodic index + halo
     int erows;          // stored rows (order 2: n + 2 hr + 1; order 1: 1; order 3: n^2, no halo)
-    int pad_;
+    int sort_slot;      // slot of this term's cell-sorted node copy (-1: none)
     long long grid_off;   // element offset in the grid buffer
     long long grid_bytes; // bytes (multiple of 16)
     long long coef_off;   // offset in the coefficient vector
@@ -91,6 +93,8 @@ struct DevPlan {
     const float2 *grids;      // stored grids of this problem
     float2 *partials;         // adjoint partial grids [spread_chunks][grid_elems]
     int spread_chunks;        // node chunks of the adjoint (one partial grid each)
+    const float2 *sx;         // [slot][M] nodes sorted by grid cell: (row coordinate, column coordinate)
+    const int *sperm;         // [slot][M] original index of each sorted node
     long long vec_node_off;   // offset of this problem's nodes in batched node vectors
     long long vec_coef_off;   // offset of this problem's coefficients in batched coefficient vectors
 };
@@ -103,8 +107,7 @@ struct BatchArgs {
     int P;
     const int *tile_prob;     // gather: problem of each tile of 128 nodes
     const int *tile0;         // first tile of each problem
-    const int *item_prob;     // spread: problem of each work item (node chunk)
-    const int *item0;         // first item of each problem
+    const int4 *items;        // spread work items (problem, active term, node chunk, chunks)
     const int *blk_prob;      // pre/post: problem of each (problem, active term) block
     const int *blk0;          // first block of each problem
 };
@@ -148,8 +151,16 @@ struct Plan {
     int n_act;
     int *h_act;
     const int *skip;        // device flag read by every transform kernel (or null)
-    void *partials;         // adjoint partial grids [spread_ctas][grid_elems]
-    int spread_ctas;
+    void *partials;         // adjoint partial grids [spread_kmax][grid_elems]
+    int spread_kmax;        // partial grids allocated (largest chunk count per term)
+    int spread_K;           // node chunks per term for the current active list
+    int4 *items;            // spread work items (device, n_terms * spread_kmax slots)
+    int4 *h_items;
+    int n_items;
+    int *counter;           // work-queue counter of the spread
+    float2 *sx;             // cell-sorted node copies (null: none), n_sorted slots of M
+    int *sperm;
+    int n_sorted;
     int gather_ctas;
     int *err;
     void *scratch;          // reduction scratch
@@ -180,6 +191,20 @@ enum { ST_PRE = 0, ST_GATHER = 1, ST_SPREAD = 2, ST_REDUCE = 3, ST_POST = 4, ST_
 int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
+int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
+                   float2 *fhat, int n_items, int *counter, int n_blocks, int mr, long long max_grid_bytes,
+                   int max_fft_elems, int sm_count, long long max_grid_elems, bool any_empty, double2 *scratch);
+size_t spread_smem_bytes(long long max_grid_bytes);
+// Sorts the nodes by grid cell for every term with sort_slot >= 0 (sort.cu).
+int sort_nodes_by_cell(Plan &p);
+int spread_ctas_per_sm(long long max_grid_bytes);
+// Node chunks per term for a spread over n_act_total active terms (all
+// problems of a launch) on sm_count SMs: about three items per resident CTA,
+// at most kmax, at least 2048 nodes per chunk.
+int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count);
+// Appends the spread work items of one problem: active terms of higher order
+// first (they cost more), K chunks each.
+int append_spread_items(const Plan &p, int prob, int K, int4 *out);
 int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas, int n_lambda, int max_it,
                double tol, int step_mode, double L0, double eta, const uint8_t *mask, const float2 *f0,
                float2 *path, anova_solve_info *info, double *L_out);

@@ -139,6 +139,7 @@ extern "C" int grouped_trafo_noalloc(int d, int64_t M, const float *x_dev, int n
         const int32_t *t = term_dims + 3 * i;
         Term T;
         std::memset(&T, 0, sizeof(T));
+        T.sort_slot = -1;
         T.order = s_order[i];
         T.col = t[T.order - 1];
         T.row0 = T.order >= 2 ? t[0] : -1;

@@ -161,9 +161,14 @@ int set_active_terms(Plan &p, const unsigned char *user_mask) {
         p.h_act[n++] = s;
     }
     p.n_act = n;
+    p.n_items = 0;
     if (n == 0) return ANOVA_OK;
+    p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count);
+    if (p.h_items) p.n_items = append_spread_items(p, 0, p.spread_K, p.h_items);
     cudaError_t e = cudaMemcpyAsync(p.act, p.h_act, sizeof(int) * n, cudaMemcpyHostToDevice, p.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.act_newgroup, flags.data(), n, cudaMemcpyHostToDevice, p.stream);
+    if (e == cudaSuccess && p.n_items)
+        e = cudaMemcpyAsync(p.items, p.h_items, sizeof(int4) * p.n_items, cudaMemcpyHostToDevice, p.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);   // flags is reused by the next call
     return cuda_status(e);
 }
@@ -190,7 +195,9 @@ DevPlan dev_view(const Plan &p) {
     v.skip = p.skip;
     v.grids = (const float2 *)p.grids;
     v.partials = (float2 *)p.partials;
-    v.spread_chunks = p.spread_ctas;
+    v.spread_chunks = p.spread_K;
+    v.sx = p.sx;
+    v.sperm = p.sperm;
     v.vec_node_off = 0;
     v.vec_coef_off = 0;
     return v;
@@ -201,7 +208,7 @@ static void free_plan(Plan &p) {
     if (p.solver && p.solver_free) p.solver_free(p.solver);
     p.solver = nullptr;
     void *bufs[] = {p.x, p.terms, p.windows, p.deconv, p.deconvd, p.empty_off, p.grids, p.partials,
-                    p.err, p.scratch, p.act, p.act_newgroup};
+                    p.err, p.scratch, p.act, p.act_newgroup, p.items, p.counter, p.sx, p.sperm};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete[] p.h_terms;
@@ -212,6 +219,7 @@ static void free_plan(Plan &p) {
     delete[] p.h_user_mr;
     delete[] p.h_user_order;
     delete[] p.h_act;
+    delete[] p.h_items;
 }
 
 }  // namespace agft
@@ -380,6 +388,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         for (int j = 1; j < T.order; ++j) T.rows *= T.n;
         T.mc = mc;
         T.mr = T.order > 1 ? mr : 0;
+        T.sort_slot = -1;
         if (T.order <= 2) {
             T.hc = T.mc - 1;
             T.hr = T.order == 2 ? T.mr - 1 : 0;
@@ -465,21 +474,45 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     chk(cudaMalloc(&p.act, sizeof(int) * std::max(1, p.n_terms)));
     chk(cudaMalloc(&p.act_newgroup, std::max(1, p.n_terms)));
     p.h_act = new int[std::max(1, p.n_terms)];
-    // adjoint partial grids
-    // spread: several CTAs per SM hide the shared-memory atomic latency; the
-    // partial grids they produce are bounded to 8 GB
-    long long per_cta = 1024;
-    long long sc_cap = std::max<long long>(1, (8LL << 30) / std::max<long long>(1, p.grid_elems * 8));
-    int sc = (int)std::min<long long>(std::min<long long>(4LL * p.sm_count, sc_cap),
-                                      std::max<long long>(1, (M + per_cta - 1) / per_cta));
-    if (o.n_ctas > 0) sc = o.n_ctas;
-    p.spread_ctas = sc;
+    // adjoint partial grids: one per node chunk of a term (work items of the
+    // spread are (term, chunk) pairs), bounded to 8 GB
+    long long k_cap = std::max<long long>(1, (8LL << 30) / std::max<long long>(1, p.grid_elems * 8));
+    int kmax = (int)std::min<long long>(std::min<long long>(SPREAD_MAX_K, k_cap),
+                                        std::max<long long>(1, (M + 2047) / 2048));
+    if (o.n_ctas > 0) kmax = std::min(o.n_ctas, SPREAD_MAX_K);
+    p.spread_kmax = kmax;
     p.gather_ctas = (int)std::min<long long>((long long)p.sm_count,
                                              std::max<long long>(1, (M + GATHER_TILE - 1) / GATHER_TILE));
     if (e == cudaSuccess && p.n_terms > 0)
-        chk(cudaMalloc(&p.partials, (size_t)sc * (size_t)p.grid_elems * 8));
+        chk(cudaMalloc(&p.partials, (size_t)kmax * (size_t)p.grid_elems * 8));
+    chk(cudaMalloc(&p.items, sizeof(int4) * (size_t)std::max(1, p.n_terms) * kmax));
+    chk(cudaMalloc(&p.counter, sizeof(int)));
+    p.h_items = new int4[(size_t)std::max(1, p.n_terms) * kmax];
     p.scratch_bytes = 1 << 20;
     chk(cudaMalloc(&p.scratch, p.scratch_bytes));
+    // cell-sorted node copies for the adjoint (terms of order <= 2), if they
+    // fit in half the free device memory
+    if (e == cudaSuccess && o.node_sort >= 0 && M > 0 && p.precision == ANOVA_PREC_F32) {
+        int ns = 0;
+        for (int s = 0; s < p.n_terms; ++s) ns += p.h_terms[s].order <= 2;
+        size_t free_b = 0, total_b = 0;
+        const size_t need = (size_t)ns * (size_t)M * (sizeof(float2) + sizeof(int));
+        if (ns > 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need <= free_b / 2) {
+            if (cudaMalloc(&p.sx, (size_t)ns * M * sizeof(float2)) == cudaSuccess &&
+                cudaMalloc(&p.sperm, (size_t)ns * M * sizeof(int)) == cudaSuccess) {
+                int slot = 0;
+                for (int s = 0; s < p.n_terms; ++s)
+                    if (p.h_terms[s].order <= 2) p.h_terms[s].sort_slot = slot++;
+                p.n_sorted = ns;
+            } else {
+                cudaGetLastError();
+                if (p.sx) cudaFree(p.sx);
+                if (p.sperm) cudaFree(p.sperm);
+                p.sx = nullptr;
+                p.sperm = nullptr;
+            }
+        }
+    }
     if (e != cudaSuccess) {
         free_plan(p);
         delete h;
@@ -508,6 +541,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
             wrap_nodes_f32<<<blocks, 256, 0, p.stream>>>((const float *)x_dev, (float *)p.x, total);
         chk(cudaGetLastError());
     }
+    if (e == cudaSuccess) chk(cuda_err_of(sort_nodes_by_cell(p)));
     if (e == cudaSuccess) chk(cuda_err_of(set_active_terms(p, nullptr)));
     chk(cudaStreamSynchronize(p.stream));
     // wins vector is copied; keep host term table

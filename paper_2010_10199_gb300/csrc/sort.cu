@@ -1,0 +1,134 @@
+// Nodes sorted by grid cell, per term of order <= 2 (built once per plan).
+//
+// The adjoint spreads y_j psi(n x_j - l) onto the oversampled grid of every
+// term (stacked adjoint after the error remark, Sec. 3).  Nodes whose grid
+// position has the same integer part (the same cell) touch the same window
+// footprint, so with the nodes of a term in cell order the spread sums a
+// cell's contributions in registers and adds them to the grid once per cell.
+// This file builds that order: a counting sort of the node indices by cell,
+// one term per blockIdx.y, and a copy of the term's coordinates in that order.
+// The order inside a cell is left to the atomics of the scatter; it changes
+// only the rounding order of the sums.
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace agft {
+
+__device__ __forceinline__ int cell_bins(const Term &T) { return T.order == 2 ? T.n * T.n : T.n; }
+
+__device__ __forceinline__ int cell_of(const Term &T, float xr, float xc) {
+    float tc;
+    const int fc = grid_pos(xc, T.n, tc);
+    if (T.order != 2) return fc;
+    float tr;
+    const int fr = grid_pos(xr, T.n, tr);
+    return fr * T.n + fc;
+}
+
+// counts[slot][cell] += nodes of the block's range in that cell
+__global__ void k_cell_count(const Term *terms, const float *x, long long M, int *counts, int max_bins) {
+    extern __shared__ int hist[];
+    const Term &T = terms[blockIdx.y];
+    if (T.sort_slot < 0) return;
+    const int nb = cell_bins(T);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const float *xr = x + (long long)(T.order == 2 ? T.row0 : T.col) * M;
+    const float *xc = x + (long long)T.col * M;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M; j += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&hist[cell_of(T, xr[j], xc[j])], 1);
+    __syncthreads();
+    int *cnt = counts + (long long)T.sort_slot * max_bins;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (hist[b]) atomicAdd(&cnt[b], hist[b]);
+}
+
+// exclusive prefix sum of counts[slot][0..bins) in place, one block per term
+__global__ void k_cell_scan(const Term *terms, int *counts, int max_bins) {
+    __shared__ int wsum[32];
+    const Term &T = terms[blockIdx.x];
+    if (T.sort_slot < 0) return;
+    const int nb = cell_bins(T);
+    int *c = counts + (long long)T.sort_slot * max_bins;
+    const int per = (nb + blockDim.x - 1) / blockDim.x;
+    const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
+    int local = 0;
+    for (int b = b0; b < b1; ++b) local += c[b];
+    // inclusive scan of the per-thread sums across the block
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int v = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) wsum[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int run = v - local + (wid > 0 ? wsum[wid - 1] : 0);   // exclusive prefix of this thread's range
+    for (int b = b0; b < b1; ++b) {
+        const int t = c[b];
+        c[b] = run;
+        run += t;
+    }
+}
+
+// scatter: every node goes to the next free place of its cell
+__global__ void k_cell_scatter(const Term *terms, const float *x, long long M, int *cursor, int max_bins,
+                               float2 *sx, int *sperm) {
+    const Term &T = terms[blockIdx.y];
+    if (T.sort_slot < 0) return;
+    const float *xr = x + (long long)(T.order == 2 ? T.row0 : T.col) * M;
+    const float *xc = x + (long long)T.col * M;
+    int *cur = cursor + (long long)T.sort_slot * max_bins;
+    float2 *dx = sx + (long long)T.sort_slot * M;
+    int *dp = sperm + (long long)T.sort_slot * M;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M;
+         j += (long long)gridDim.x * blockDim.x) {
+        const float a = xr[j], b = xc[j];
+        const int pos = atomicAdd(&cur[cell_of(T, a, b)], 1);
+        dx[pos] = make_float2(T.order == 2 ? a : 0.f, b);
+        dp[pos] = (int)j;
+    }
+}
+
+int sort_nodes_by_cell(Plan &p) {
+    if (!p.sx || p.n_sorted == 0 || p.M == 0) return ANOVA_OK;
+    int max_bins = 1;
+    for (int s = 0; s < p.n_terms; ++s) {
+        const Term &T = p.h_terms[s];
+        if (T.sort_slot >= 0) max_bins = std::max(max_bins, T.order == 2 ? T.n * T.n : T.n);
+    }
+    int *counts = nullptr;
+    cudaError_t e = cudaMalloc(&counts, sizeof(int) * (size_t)p.n_sorted * max_bins);
+    if (e != cudaSuccess) return cuda_status(e);
+    const size_t hist_bytes = sizeof(int) * (size_t)max_bins;
+    if (hist_bytes > 48 * 1024) e = cudaFuncSetAttribute(k_cell_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)hist_bytes);
+    const int bx = (int)std::max<long long>(1, std::min<long long>(64, (p.M + 4095) / 4096));
+    const dim3 grid(bx, p.n_terms);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)p.n_sorted * max_bins, p.stream);
+    if (e == cudaSuccess) {
+        k_cell_count<<<grid, 256, hist_bytes, p.stream>>>(p.terms, (const float *)p.x, p.M, counts, max_bins);
+        k_cell_scan<<<p.n_terms, 1024, 0, p.stream>>>(p.terms, counts, max_bins);
+        k_cell_scatter<<<grid, 256, 0, p.stream>>>(p.terms, (const float *)p.x, p.M, counts, max_bins, p.sx,
+                                                   p.sperm);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
+    cudaFree(counts);
+    return cuda_status(e);
+}
+
+}  // namespace agft
