@@ -39,10 +39,14 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // staging area after the grid: the larger of the unsorted layout
-// (float4 [2][SP_CH]) and the sorted one (float2 [3][SP_CH] coordinates,
-// int [3][SP_CH] node indices, float2 [2][SP_CH] values of y)
-constexpr size_t SP_STAGE_BYTES = 3 * SP_CH * 8 + 3 * SP_CH * 4 + 2 * SP_CH * 8;
+// (float4 [2][SP_CH]) and the sorted one (float4 [3][SP_CH] node records,
+// float2 [2][SP_CH] values of y)
+constexpr size_t SP_STAGE_BYTES = 3 * SP_CH * 16 + 2 * SP_CH * 8;
 static_assert(SP_STAGE_BYTES >= 2 * SP_CH * 16, "staging area");
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
 
 size_t spread_smem_bytes(long long max_grid_bytes) {
     return (size_t)max_grid_bytes + SP_STAGE_BYTES + 16;   // grid, node blocks, item slot
@@ -72,44 +76,53 @@ int append_spread_items(const Plan &p, int prob, int K, int4 *out) {
     return n;
 }
 
-// Sorted item: the item's nodes in cell order of its term.  Blocks of SP_CH
-// nodes pass through shared memory: coordinates and original indices by
-// cp.async two blocks ahead, the values y[index] by cp.async one block ahead
-// (their addresses come from the staged indices).  Each half-warp walks a run
-// of SP_CH / 16 consecutive nodes and sums the contributions of a cell in
-// registers (lane (r, k): column tap k, rows r, r + 2, ..); when the cell
-// changes, or at the end of the run, it adds the sums to the shared grid.
-// Order 1: the two lane groups r = 0, 1 take alternate nodes of the run.
+// Window weights of one node for a half-warp, lane (r, k): lanes r = 0
+// evaluate the column tap k, lanes r = 1 the row tap k (clamped to the
+// window), each from its own coefficients wcf; shuffles hand every lane the
+// column weight of its tap and the row weights of rows r, r + 2, ...
+template <int MR>
+__device__ __forceinline__ void node_weights(const float wcf[NCOEF], float vrow, float vcol, int half, int r, int k,
+                                             float &cw, float w[MR]) {
+    const float wt = horner8(wcf, r ? vrow : vcol);
+    cw = __shfl_sync(0xffffffffu, wt, (half << 4) | k);
+#pragma unroll
+    for (int j = 0; j < MR; ++j) w[j] = __shfl_sync(0xffffffffu, wt, (half << 4) | 8 | (r + 2 * j));
+}
+
+// Sorted item: the item's nodes in cell order of its term, as records
+// (window arguments, first-tap grid offset, original index).  Blocks of SP_CH
+// records pass through shared memory by cp.async two blocks ahead, the values
+// y[index] one block ahead (their addresses come from the staged records).
+// Each half-warp walks a run of SP_CH / 16 consecutive nodes and sums the
+// contributions of a cell in registers (lane (r, k): column tap k, rows r,
+// r + 2, ..); when the cell changes, or at the end of the run, it adds the
+// sums to the shared grid.  Order 1: the lane groups r = 0, 1 take alternate
+// nodes of the run.
 template <int MR>
 __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                    long long j0, long long j1, float2 *S, unsigned char *stg_raw,
-                                                   const float cc[NCOEF], const float rcf[NCOEF]) {
+                                                   const float wcf[NCOEF]) {
     constexpr int RUN = SP_CH / 16;
     const int tid = threadIdx.x;
     const int lane = tid & 31, half = lane >> 4, sub = lane & 15;
     const int r = sub >> 3, k = sub & 7;
     const int hw = (tid >> 5) * 2 + half;
-    const int n = T.n, stride = T.stride, order = T.order;
-    const long long M = P.M;
-    const float2 *sxp = P.sx + (long long)T.sort_slot * M;
-    const int *spp = P.sperm + (long long)T.sort_slot * M;
-    float2 *cbuf = (float2 *)stg_raw;          // [3][SP_CH]
-    int *pbuf = (int *)(cbuf + 3 * SP_CH);     // [3][SP_CH]
-    float2 *ybuf = (float2 *)(pbuf + 3 * SP_CH);  // [2][SP_CH]
+    const int stride = T.stride;
+    const float4 *src = P.srec + (long long)T.sort_slot * P.M;
+    float4 *rbuf = (float4 *)stg_raw;            // [3][SP_CH]
+    float2 *ybuf = (float2 *)(rbuf + 3 * SP_CH); // [2][SP_CH]
     const long long nblk = (j1 - j0 + SP_CH - 1) / SP_CH;
     auto count = [&](long long c) { return (int)min((long long)SP_CH, j1 - (j0 + c * SP_CH)); };
     auto stage_a = [&](long long c) {
-        const long long a = j0 + c * SP_CH;
+        const float4 *g = src + j0 + c * SP_CH;
         const int cnt = count(c), b = (int)(c % 3) * SP_CH;
-        for (int e = tid; e < cnt; e += SPREAD_THREADS) {
-            cp_async8(&cbuf[b + e], sxp + a + e);
-            cp_async4(&pbuf[b + e], spp + a + e);
-        }
+        for (int e = tid; e < cnt; e += SPREAD_THREADS) cp_async16(&rbuf[b + e], g + e);
     };
-    // reads indices this thread staged itself (same e), so its own wait suffices
+    // reads records this thread staged itself (same e), so its own wait suffices
     auto stage_b = [&](long long c) {
         const int cnt = count(c), b = (int)(c % 3) * SP_CH, yb = (int)(c & 1) * SP_CH;
-        for (int e = tid; e < cnt; e += SPREAD_THREADS) cp_async8(&ybuf[yb + e], y + pbuf[b + e]);
+        for (int e = tid; e < cnt; e += SPREAD_THREADS)
+            cp_async8(&ybuf[yb + e], y + __float_as_int(rbuf[b + e].w));
     };
     if (nblk > 0) stage_a(0);
     cp_async_commit();
@@ -125,17 +138,17 @@ __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term 
         cp_async_commit();
         if (c + 2 < nblk) stage_a(c + 2);
         cp_async_commit();
-        const float2 *cb = cbuf + (int)(c % 3) * SP_CH;
+        const float4 *rb = rbuf + (int)(c % 3) * SP_CH;
         const float2 *yb = ybuf + (int)(c & 1) * SP_CH;
         const int cnt = count(c);
         const int i0 = hw * RUN;
-        if (order == 2) {
-            int cfa = -1, cfb = 0;
+        if (T.order == 2) {
+            int cur = -1;
             float ax[MR], ay[MR];
 #pragma unroll
             for (int j = 0; j < MR; ++j) ax[j] = ay[j] = 0.f;
             auto flush = [&]() {
-                float *base = (float *)(S + (cfa + r) * stride + cfb + k);
+                float *base = (float *)(S + cur + r * stride + k);
 #pragma unroll
                 for (int j = 0; j < MR; ++j) {
                     red_add(base + 4 * j * stride, ax[j]);
@@ -144,24 +157,19 @@ __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term 
                 }
             };
             // both half-warps of a warp run RUN steps (shuffles); steps past
-            // the block end compute on node 0 and add nothing
+            // the block end compute on record 0 and add nothing
+#pragma unroll 2
             for (int t = 0; t < RUN; ++t) {
                 const int i = i0 + t;
                 const bool ok = i < cnt;
-                const float2 q = cb[ok ? i : 0];
-                float ta, tb;
-                const int fa = grid_pos(q.x, n, ta);
-                const int fb = grid_pos(q.y, n, tb);
-                const float cw = horner8(cc, 2.f * tb - 1.f);
-                const float rw = horner8(rcf, 2.f * ta - 1.f);
-                float w[MR];
-#pragma unroll
-                for (int j = 0; j < MR; ++j) w[j] = __shfl_sync(0xffffffffu, rw, (half << 4) | (r + 2 * j));
+                const float4 q = rb[ok ? i : 0];
+                float cw, w[MR];
+                node_weights<MR>(wcf, q.x, q.y, half, r, k, cw, w);
                 if (ok) {
-                    if (fa != cfa || fb != cfb) {
-                        if (cfa >= 0) flush();
-                        cfa = fa;
-                        cfb = fb;
+                    const int off = __float_as_int(q.z);
+                    if (off != cur) {
+                        if (cur >= 0) flush();
+                        cur = off;
                     }
                     const float2 yv = yb[i];
                     const float yx = yv.x * cw, yy = yv.y * cw;
@@ -172,32 +180,31 @@ __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term 
                     }
                 }
             }
-            if (cfa >= 0) flush();
+            if (cur >= 0) flush();
         } else {
-            int cfb = -1;
+            int cur = -1;
             float ax = 0.f, ay = 0.f;
             for (int t = r; t < RUN; t += 2) {
                 const int i = i0 + t;
                 if (i >= cnt) break;
-                const float2 q = cb[i];
-                float tb;
-                const int fb = grid_pos(q.y, n, tb);
-                if (fb != cfb) {
-                    if (cfb >= 0) {
-                        float *base = (float *)(S + cfb + k);
+                const float4 q = rb[i];
+                const int off = __float_as_int(q.z);
+                if (off != cur) {
+                    if (cur >= 0) {
+                        float *base = (float *)(S + cur + k);
                         red_add(base, ax);
                         red_add(base + 1, ay);
                         ax = ay = 0.f;
                     }
-                    cfb = fb;
+                    cur = off;
                 }
-                const float cw = horner8(cc, 2.f * tb - 1.f);
+                const float cw = horner8(wcf, q.y);
                 const float2 yv = yb[i];
                 ax = fmaf(yv.x, cw, ax);
                 ay = fmaf(yv.y, cw, ay);
             }
-            if (cfb >= 0) {
-                float *base = (float *)(S + cfb + k);
+            if (cur >= 0) {
+                float *base = (float *)(S + cur + k);
                 red_add(base, ax);
                 red_add(base + 1, ay);
             }
@@ -214,7 +221,7 @@ __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term 
 template <int MR>
 __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                      long long j0, long long j1, float2 *S, unsigned char *stg_raw,
-                                                     const float cc[NCOEF], const float rcf[NCOEF]) {
+                                                     const float wcf[NCOEF]) {
     const int tid = threadIdx.x;
     const int lane = tid & 31, half = lane >> 4, sub = lane & 15;
     const int r = sub >> 3, k = sub & 7;
@@ -257,16 +264,15 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
                 float ta, tb;
                 const int fa = grid_pos(q.x, n, ta);
                 const int fb = grid_pos(q.y, n, tb);
-                const float cw = horner8(cc, 2.f * tb - 1.f);
-                const float rw = horner8(rcf, 2.f * ta - 1.f);
+                float cw, w[MR];
+                node_weights<MR>(wcf, 2.f * ta - 1.f, 2.f * tb - 1.f, half, r, k, cw, w);
                 const float yx = q.z * cw, yy = q.w * cw;
                 float *base = (float *)(S + (fa + r) * stride + fb + k);
+                if (ok) {
 #pragma unroll
-                for (int j = 0; j < MR; ++j) {
-                    const float w = __shfl_sync(0xffffffffu, rw, (half << 4) | (r + 2 * j));
-                    if (ok) {
-                        red_add(base + 4 * j * stride, yx * w);
-                        red_add(base + 4 * j * stride + 1, yy * w);
+                    for (int j = 0; j < MR; ++j) {
+                        red_add(base + 4 * j * stride, yx * w[j]);
+                        red_add(base + 4 * j * stride + 1, yy * w[j]);
                     }
                 }
             }
@@ -276,7 +282,7 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
                 const float4 q = stg[i];
                 float tb;
                 const int fb = grid_pos(q.y, n, tb);
-                const float cw = horner8(cc, 2.f * tb - 1.f);
+                const float cw = horner8(wcf, 2.f * tb - 1.f);
                 float *base = (float *)(S + fb + k);
                 red_add(base, q.z * cw);
                 red_add(base + 1, q.w * cw);
@@ -291,7 +297,7 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
                 const int fa = grid_pos(q.x, n, ta);
                 const int fb = grid_pos(__ldg(xr1 + a + i), n, tb);
                 const int fc = grid_pos(q.y, n, tc);
-                const float cw = horner8(cc, 2.f * tc - 1.f);
+                const float cw = horner8(wcf, 2.f * tc - 1.f);
                 const int cidx = wrap(fc - mc + 1 + k, n);
                 const float yx = q.z * cw, yy = q.w * cw;
                 for (int ia = 0; ia < 2 * mr; ++ia) {
@@ -345,21 +351,20 @@ spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n
         float4 *S4 = (float4 *)S;
         for (long long e = tid; e < elems / 2; e += SPREAD_THREADS) S4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 *y = y_base + P.vec_node_off;
-        float cc[NCOEF], rcf[NCOEF];
+        // window coefficients of this lane: row tap k for lanes r = 1 of an
+        // order-2 term (see node_weights), column tap k otherwise
+        float wcf[NCOEF];
         {
-            const float *wsrc = P.windows[T.wc].c[k];
-            const float *rsrc = P.windows[T.wr].c[min(k, 2 * MR - 1)];
+            const bool row = T.order == 2 && (tid & 8);
+            const float *wsrc = row ? P.windows[T.wr].c[min(k, 2 * MR - 1)] : P.windows[T.wc].c[k];
 #pragma unroll
-            for (int i = 0; i < NCOEF; ++i) {
-                cc[i] = __ldg(wsrc + i);
-                rcf[i] = __ldg(rsrc + i);
-            }
+            for (int i = 0; i < NCOEF; ++i) wcf[i] = __ldg(wsrc + i);
         }
         __syncthreads();   // grid zeroed before any addition
-        if (T.sort_slot >= 0 && P.sx)
-            spread_sorted_item<MR>(P, T, y, j0, j1, S, stg_raw, cc, rcf);
+        if (T.sort_slot >= 0 && P.srec)
+            spread_sorted_item<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
         else
-            spread_unsorted_item<MR>(P, T, y, j0, j1, S, stg_raw, cc, rcf);
+            spread_unsorted_item<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
         __syncthreads();
         float4 *dst = (float4 *)(P.partials + (long long)itm.z * P.grid_elems + T.grid_off);
         for (long long e = tid; e < elems / 2; e += SPREAD_THREADS) dst[e] = S4[e];

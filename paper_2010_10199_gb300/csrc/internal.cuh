@@ -70,6 +70,14 @@ struct Term {
     int pad2_;
 };
 
+// A node in the cell order of one term (16 bytes, stored as float4):
+//   x: 2 tau_row - 1 (order 2; 0 for order 1), y: 2 tau_col - 1, the window
+//   polynomial arguments of the node's fractional grid positions;
+//   z (int bits): stored-grid offset of the first tap, i_row * stride + i_col
+//   (order 1: i_col), which identifies the cell;
+//   w (int bits): the node's original index.
+// Built in sort.cu by the same FP32 operations the unsorted kernels apply.
+
 // Device-visible view of a plan (passed by value to kernels).
 struct DevPlan {
     int d;
@@ -93,8 +101,7 @@ struct DevPlan {
     const float2 *grids;      // stored grids of this problem
     float2 *partials;         // adjoint partial grids [spread_chunks][grid_elems]
     int spread_chunks;        // node chunks of the adjoint (one partial grid each)
-    const float2 *sx;         // [slot][M] nodes sorted by grid cell: (row coordinate, column coordinate)
-    const int *sperm;         // [slot][M] original index of each sorted node
+    const float4 *srec;       // [slot][M] nodes sorted by grid cell, see SortedNode
     long long vec_node_off;   // offset of this problem's nodes in batched node vectors
     long long vec_coef_off;   // offset of this problem's coefficients in batched coefficient vectors
 };
@@ -158,8 +165,7 @@ struct Plan {
     int4 *h_items;
     int n_items;
     int *counter;           // work-queue counter of the spread
-    float2 *sx;             // cell-sorted node copies (null: none), n_sorted slots of M
-    int *sperm;
+    float4 *srec;           // cell-sorted node records (null: none), n_sorted slots of M
     int n_sorted;
     int gather_ctas;
     int *err;

@@ -196,8 +196,7 @@ DevPlan dev_view(const Plan &p) {
     v.grids = (const float2 *)p.grids;
     v.partials = (float2 *)p.partials;
     v.spread_chunks = p.spread_K;
-    v.sx = p.sx;
-    v.sperm = p.sperm;
+    v.srec = p.srec;
     v.vec_node_off = 0;
     v.vec_coef_off = 0;
     return v;
@@ -208,7 +207,7 @@ static void free_plan(Plan &p) {
     if (p.solver && p.solver_free) p.solver_free(p.solver);
     p.solver = nullptr;
     void *bufs[] = {p.x, p.terms, p.windows, p.deconv, p.deconvd, p.empty_off, p.grids, p.partials,
-                    p.err, p.scratch, p.act, p.act_newgroup, p.items, p.counter, p.sx, p.sperm};
+                    p.err, p.scratch, p.act, p.act_newgroup, p.items, p.counter, p.srec};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete[] p.h_terms;
@@ -496,20 +495,16 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         int ns = 0;
         for (int s = 0; s < p.n_terms; ++s) ns += p.h_terms[s].order <= 2;
         size_t free_b = 0, total_b = 0;
-        const size_t need = (size_t)ns * (size_t)M * (sizeof(float2) + sizeof(int));
+        const size_t need = (size_t)ns * (size_t)M * sizeof(float4);
         if (ns > 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need <= free_b / 2) {
-            if (cudaMalloc(&p.sx, (size_t)ns * M * sizeof(float2)) == cudaSuccess &&
-                cudaMalloc(&p.sperm, (size_t)ns * M * sizeof(int)) == cudaSuccess) {
+            if (cudaMalloc(&p.srec, need) == cudaSuccess) {
                 int slot = 0;
                 for (int s = 0; s < p.n_terms; ++s)
                     if (p.h_terms[s].order <= 2) p.h_terms[s].sort_slot = slot++;
                 p.n_sorted = ns;
             } else {
                 cudaGetLastError();
-                if (p.sx) cudaFree(p.sx);
-                if (p.sperm) cudaFree(p.sperm);
-                p.sx = nullptr;
-                p.sperm = nullptr;
+                p.srec = nullptr;
             }
         }
     }

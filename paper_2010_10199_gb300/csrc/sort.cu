@@ -6,7 +6,8 @@
 // footprint, so with the nodes of a term in cell order the spread sums a
 // cell's contributions in registers and adds them to the grid once per cell.
 // This file builds that order: a counting sort of the node indices by cell,
-// one term per blockIdx.y, and a copy of the term's coordinates in that order.
+// one term per blockIdx.y, and per sorted node a 16-byte record with the
+// window arguments, the grid offset of its cell and its original index.
 // The order inside a cell is left to the atomics of the scatter; it changes
 // only the rounding order of the sums.
 #include <algorithm>
@@ -84,27 +85,31 @@ __global__ void k_cell_scan(const Term *terms, int *counts, int max_bins) {
     }
 }
 
-// scatter: every node goes to the next free place of its cell
+// scatter: every node goes to the next free place of its cell, as a record
+// (2 tau_row - 1, 2 tau_col - 1, first-tap grid offset, original index)
 __global__ void k_cell_scatter(const Term *terms, const float *x, long long M, int *cursor, int max_bins,
-                               float2 *sx, int *sperm) {
+                               float4 *srec) {
     const Term &T = terms[blockIdx.y];
     if (T.sort_slot < 0) return;
     const float *xr = x + (long long)(T.order == 2 ? T.row0 : T.col) * M;
     const float *xc = x + (long long)T.col * M;
     int *cur = cursor + (long long)T.sort_slot * max_bins;
-    float2 *dx = sx + (long long)T.sort_slot * M;
-    int *dp = sperm + (long long)T.sort_slot * M;
+    float4 *dst = srec + (long long)T.sort_slot * M;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M;
          j += (long long)gridDim.x * blockDim.x) {
-        const float a = xr[j], b = xc[j];
-        const int pos = atomicAdd(&cur[cell_of(T, a, b)], 1);
-        dx[pos] = make_float2(T.order == 2 ? a : 0.f, b);
-        dp[pos] = (int)j;
+        float tc, tr = 0.f;
+        const int fc = grid_pos(xc[j], T.n, tc);
+        int fr = 0;
+        if (T.order == 2) fr = grid_pos(xr[j], T.n, tr);
+        const int pos = atomicAdd(&cur[fr * (T.order == 2 ? T.n : 0) + fc], 1);
+        const int off = fr * T.stride + fc;
+        dst[pos] = make_float4(T.order == 2 ? 2.f * tr - 1.f : 0.f, 2.f * tc - 1.f, __int_as_float(off),
+                               __int_as_float((int)j));
     }
 }
 
 int sort_nodes_by_cell(Plan &p) {
-    if (!p.sx || p.n_sorted == 0 || p.M == 0) return ANOVA_OK;
+    if (!p.srec || p.n_sorted == 0 || p.M == 0) return ANOVA_OK;
     int max_bins = 1;
     for (int s = 0; s < p.n_terms; ++s) {
         const Term &T = p.h_terms[s];
@@ -122,8 +127,7 @@ int sort_nodes_by_cell(Plan &p) {
     if (e == cudaSuccess) {
         k_cell_count<<<grid, 256, hist_bytes, p.stream>>>(p.terms, (const float *)p.x, p.M, counts, max_bins);
         k_cell_scan<<<p.n_terms, 1024, 0, p.stream>>>(p.terms, counts, max_bins);
-        k_cell_scatter<<<grid, 256, 0, p.stream>>>(p.terms, (const float *)p.x, p.M, counts, max_bins, p.sx,
-                                                   p.sperm);
+        k_cell_scatter<<<grid, 256, 0, p.stream>>>(p.terms, (const float *)p.x, p.M, counts, max_bins, p.srec);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);

@@ -33,13 +33,13 @@ def _plan(gft, x, terms, bw, **kw):
     return gft.Plan(to_dev(x, torch.float32), terms, bw, **kw)
 
 
-def _pair_check(gft, x, terms, bw, fhat=None, y=None, tol=TOL, seed=1):
+def _pair_check(gft, x, terms, bw, fhat=None, y=None, tol=TOL, seed=1, **plan_kw):
     xo = f32_nodes(x)
     n = anova.n_coeffs(terms, bw)
     M = x.shape[1]
     fhat = inputs.decaying_coefficients(seed, terms, bw) if fhat is None else fhat
     y = inputs.complex_normal(seed, 4, M) if y is None else y
-    P = _plan(gft, x, terms, bw)
+    P = _plan(gft, x, terms, bw, **plan_kw)
     assert P.n_coeffs == n
     f = host(P.trafo(cplx_dev(fhat)))
     g = host(P.adjoint(cplx_dev(y)))
@@ -61,6 +61,28 @@ def test_ragged_sizes(gft, M):
     x = inputs.uniform_points(7, 5, M)
     terms = anova.term_set(5, 2)
     bw = [0] + [16] * 5 + [8] * 10
+    _pair_check(gft, x, terms, bw)
+
+
+@pytest.mark.parametrize("node_sort", [0, -1])
+@pytest.mark.parametrize("chunks", [0, 1, 3])
+def test_spread_paths_and_chunking(gft, node_sort, chunks):
+    """The adjoint's two spread paths (cell-sorted copies of the nodes, or the
+    original order with per-node atomics) and several node chunks per term."""
+    x = inputs.uniform_points(17, 5, 9001)
+    terms = anova.term_set(5, 2)
+    bw = [0] + [64] * 5 + [32] * 10
+    _pair_check(gft, x, terms, bw, node_sort=node_sort, n_ctas=chunks)
+
+
+def test_clustered_nodes(gft):
+    """Nodes crowded into a few grid cells: long runs of one cell in the
+    sorted spread, and cells with a single node in between."""
+    x = inputs.uniform_points(18, 4, 6000)
+    x[:, :5000] = -0.2 + 1e-3 * x[:, :5000]
+    x[1, 2500:5000] = 0.37
+    terms = anova.term_set(4, 2)
+    bw = [0] + [32] * 4 + [16] * 6
     _pair_check(gft, x, terms, bw)
 
 
