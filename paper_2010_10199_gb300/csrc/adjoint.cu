@@ -90,14 +90,15 @@ __device__ __forceinline__ void node_weights(const float wcf[NCOEF], float vrow,
 }
 
 // Sorted item: the item's nodes in cell order of its term, as records
-// (window arguments, first-tap grid offset, original index).  Blocks of SP_CH
-// records pass through shared memory by cp.async two blocks ahead, the values
-// y[index] one block ahead (their addresses come from the staged records).
-// Each half-warp walks a run of SP_CH / 16 consecutive nodes and sums the
-// contributions of a cell in registers (lane (r, k): column tap k, rows r,
-// r + 2, ..); when the cell changes, or at the end of the run, it adds the
-// sums to the shared grid.  Order 1: the lane groups r = 0, 1 take alternate
-// nodes of the run.
+// (window arguments, first-tap grid offset, original index).  The item's node
+// range is cut into 16 contiguous runs, one per half-warp; block c of the
+// staging holds records c*RUN .. c*RUN+RUN-1 of every run.  Records pass
+// through shared memory by cp.async two blocks ahead, the values y[index] one
+// block ahead (their addresses come from the staged records).  A half-warp
+// sums the contributions of a cell in registers (lane (r, k): column tap k,
+// rows r, r + 2, ..), two nodes per step, and adds the sums to the shared
+// grid when the cell changes and at the end of its run.  Order 1: the lane
+// groups r = 0, 1 take alternate nodes of the run.
 template <int MR>
 __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                    long long j0, long long j1, float2 *S, unsigned char *stg_raw,
@@ -108,22 +109,51 @@ __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term 
     const int r = sub >> 3, k = sub & 7;
     const int hw = (tid >> 5) * 2 + half;
     const int stride = T.stride;
-    const float4 *src = P.srec + (long long)T.sort_slot * P.M;
+    const float4 *src = P.srec + (long long)T.sort_slot * P.M + j0;
     float4 *rbuf = (float4 *)stg_raw;            // [3][SP_CH]
     float2 *ybuf = (float2 *)(rbuf + 3 * SP_CH); // [2][SP_CH]
-    const long long nblk = (j1 - j0 + SP_CH - 1) / SP_CH;
-    auto count = [&](long long c) { return (int)min((long long)SP_CH, j1 - (j0 + c * SP_CH)); };
+    const long long len = j1 - j0;
+    const long long L = (len + 15) / 16;           // run length
+    const long long nblk = (L + RUN - 1) / RUN;
+    // records of run h: [h L, min((h+1) L, len))
+    auto run_len = [&](int h) { return max(0LL, min(L, len - (long long)h * L)); };
     auto stage_a = [&](long long c) {
-        const float4 *g = src + j0 + c * SP_CH;
-        const int cnt = count(c), b = (int)(c % 3) * SP_CH;
-        for (int e = tid; e < cnt; e += SPREAD_THREADS) cp_async16(&rbuf[b + e], g + e);
+        const int b = (int)(c % 3) * SP_CH;
+        for (int e = tid; e < SP_CH; e += SPREAD_THREADS) {
+            const int h = e / RUN, t = e % RUN;
+            const long long q = c * RUN + t;
+            if (q < run_len(h)) cp_async16(&rbuf[b + e], src + (long long)h * L + q);
+        }
     };
     // reads records this thread staged itself (same e), so its own wait suffices
     auto stage_b = [&](long long c) {
-        const int cnt = count(c), b = (int)(c % 3) * SP_CH, yb = (int)(c & 1) * SP_CH;
-        for (int e = tid; e < cnt; e += SPREAD_THREADS)
-            cp_async8(&ybuf[yb + e], y + __float_as_int(rbuf[b + e].w));
+        const int b = (int)(c % 3) * SP_CH, yb = (int)(c & 1) * SP_CH;
+        for (int e = tid; e < SP_CH; e += SPREAD_THREADS) {
+            const int h = e / RUN, t = e % RUN;
+            if (c * RUN + t < run_len(h)) cp_async8(&ybuf[yb + e], y + __float_as_int(rbuf[b + e].w));
+        }
     };
+    const long long my_len = run_len(hw);
+    int cur = -1;   // grid offset of the cell being summed
+    float ax[MR], ay[MR];
+#pragma unroll
+    for (int j = 0; j < MR; ++j) ax[j] = ay[j] = 0.f;
+    auto flush2 = [&]() {
+        float *base = (float *)(S + cur + r * stride + k);
+#pragma unroll
+        for (int j = 0; j < MR; ++j) {
+            red_add(base + 4 * j * stride, ax[j]);
+            red_add(base + 4 * j * stride + 1, ay[j]);
+            ax[j] = ay[j] = 0.f;
+        }
+    };
+    auto flush1 = [&]() {
+        float *base = (float *)(S + cur + k);
+        red_add(base, ax[0]);
+        red_add(base + 1, ay[0]);
+        ax[0] = ay[0] = 0.f;
+    };
+    const int col_src = (half << 4) | k, row_src = (half << 4) | 8 | r;
     if (nblk > 0) stage_a(0);
     cp_async_commit();
     if (nblk > 1) stage_a(1);
@@ -138,80 +168,74 @@ __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term 
         cp_async_commit();
         if (c + 2 < nblk) stage_a(c + 2);
         cp_async_commit();
-        const float4 *rb = rbuf + (int)(c % 3) * SP_CH;
-        const float2 *yb = ybuf + (int)(c & 1) * SP_CH;
-        const int cnt = count(c);
-        const int i0 = hw * RUN;
+        const float4 *rb = rbuf + (int)(c % 3) * SP_CH + hw * RUN;
+        const float2 *yb = ybuf + (int)(c & 1) * SP_CH + hw * RUN;
+        const long long left = my_len - c * RUN;   // records of this run still to come
         if (T.order == 2) {
-            int cur = -1;
-            float ax[MR], ay[MR];
-#pragma unroll
-            for (int j = 0; j < MR; ++j) ax[j] = ay[j] = 0.f;
-            auto flush = [&]() {
-                float *base = (float *)(S + cur + r * stride + k);
+            // both half-warps of a warp run all steps (shuffles); a node past
+            // the run's end computes on record 0, adds zero and keeps the cell
+            for (int t = 0; t < RUN; t += 2) {
+                const bool ok0 = t < left, ok1 = t + 1 < left;
+                const float4 q0 = rb[ok0 ? t : 0], q1 = rb[ok1 ? t + 1 : 0];
+                const float wt0 = horner8(wcf, r ? q0.x : q0.y);
+                const float wt1 = horner8(wcf, r ? q1.x : q1.y);
+                const float cw0 = __shfl_sync(0xffffffffu, wt0, col_src);
+                const float cw1 = __shfl_sync(0xffffffffu, wt1, col_src);
+                float w0[MR], w1[MR];
 #pragma unroll
                 for (int j = 0; j < MR; ++j) {
-                    red_add(base + 4 * j * stride, ax[j]);
-                    red_add(base + 4 * j * stride + 1, ay[j]);
-                    ax[j] = ay[j] = 0.f;
+                    w0[j] = __shfl_sync(0xffffffffu, wt0, row_src + 2 * j);
+                    w1[j] = __shfl_sync(0xffffffffu, wt1, row_src + 2 * j);
                 }
-            };
-            // both half-warps of a warp run RUN steps (shuffles); steps past
-            // the block end compute on record 0 and add nothing
-#pragma unroll 2
-            for (int t = 0; t < RUN; ++t) {
-                const int i = i0 + t;
-                const bool ok = i < cnt;
-                const float4 q = rb[ok ? i : 0];
-                float cw, w[MR];
-                node_weights<MR>(wcf, q.x, q.y, half, r, k, cw, w);
-                if (ok) {
-                    const int off = __float_as_int(q.z);
-                    if (off != cur) {
-                        if (cur >= 0) flush();
-                        cur = off;
-                    }
-                    const float2 yv = yb[i];
-                    const float yx = yv.x * cw, yy = yv.y * cw;
+                const float2 y0 = ok0 ? yb[t] : make_float2(0.f, 0.f);
+                const float2 y1 = ok1 ? yb[t + 1] : make_float2(0.f, 0.f);
+                const int off0 = ok0 ? __float_as_int(q0.z) : cur;
+                const int off1 = ok1 ? __float_as_int(q1.z) : off0;
+                if (off0 != cur) {
+                    if (cur >= 0) flush2();
+                    cur = off0;
+                }
+                const float y0x = y0.x * cw0, y0y = y0.y * cw0;
 #pragma unroll
-                    for (int j = 0; j < MR; ++j) {
-                        ax[j] = fmaf(yx, w[j], ax[j]);
-                        ay[j] = fmaf(yy, w[j], ay[j]);
-                    }
+                for (int j = 0; j < MR; ++j) {
+                    ax[j] = fmaf(y0x, w0[j], ax[j]);
+                    ay[j] = fmaf(y0y, w0[j], ay[j]);
+                }
+                if (off1 != cur) {
+                    flush2();
+                    cur = off1;
+                }
+                const float y1x = y1.x * cw1, y1y = y1.y * cw1;
+#pragma unroll
+                for (int j = 0; j < MR; ++j) {
+                    ax[j] = fmaf(y1x, w1[j], ax[j]);
+                    ay[j] = fmaf(y1y, w1[j], ay[j]);
                 }
             }
-            if (cur >= 0) flush();
         } else {
-            int cur = -1;
-            float ax = 0.f, ay = 0.f;
             for (int t = r; t < RUN; t += 2) {
-                const int i = i0 + t;
-                if (i >= cnt) break;
-                const float4 q = rb[i];
+                if (t >= left) break;
+                const float4 q = rb[t];
                 const int off = __float_as_int(q.z);
                 if (off != cur) {
-                    if (cur >= 0) {
-                        float *base = (float *)(S + cur + k);
-                        red_add(base, ax);
-                        red_add(base + 1, ay);
-                        ax = ay = 0.f;
-                    }
+                    if (cur >= 0) flush1();
                     cur = off;
                 }
                 const float cw = horner8(wcf, q.y);
-                const float2 yv = yb[i];
-                ax = fmaf(yv.x, cw, ax);
-                ay = fmaf(yv.y, cw, ay);
-            }
-            if (cur >= 0) {
-                float *base = (float *)(S + cur + k);
-                red_add(base, ax);
-                red_add(base + 1, ay);
+                const float2 yv = yb[t];
+                ax[0] = fmaf(yv.x, cw, ax[0]);
+                ay[0] = fmaf(yv.y, cw, ay[0]);
             }
         }
         __syncthreads();
     }
     cp_async_wait0();
+    if (cur >= 0) {
+        if (T.order == 2)
+            flush2();
+        else
+            flush1();
+    }
 }
 
 // Unsorted item (order 3, or a plan without sorted copies): the item's nodes
