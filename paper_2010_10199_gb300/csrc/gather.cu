@@ -3,15 +3,20 @@
 //
 // Point-major and persistent: a CTA owns a tile of 128 nodes whose coordinates
 // it stages in shared memory, and walks the term schedule; each term's stored
-// grid arrives in shared memory by a bulk async copy (double-buffered,
-// mbarrier-tracked).  A half-warp owns 8 nodes and evaluates one node at a
+// grid arrives in shared memory by a bulk async copy into one of two buffers,
+// tracked by an mbarrier.  There is no block-wide barrier per term: every warp
+// counts itself out of a buffer when done with it, and the last warp out
+// issues the copy of the term two steps ahead into it, so warps drift freely
+// within that window.  A half-warp owns 8 nodes and evaluates one node at a
 // time with 16 lanes = 2 grid rows x 8 grid columns, so a warp instruction
 // reads 2 nodes x 2 rows x 8 columns; the row pitch = 8 (mod 16) complex
-// elements puts the two rows of a node in complementary bank halves.
-// Order-2 terms reuse the row weights of their first coordinate across the
-// row group (all terms sharing that coordinate), so per node and term a lane
-// evaluates one window polynomial.  Lanes accumulate over all terms in
-// registers; a transposed reduce-scatter per tile finishes each node.
+// elements puts the two rows of a node in complementary bank halves.  The
+// window polynomials are evaluated once per (node, tap): order-2 terms share
+// the row weights of their first coordinate across the row group (lane (r, k)
+// evaluates rows r, r+2, .. of node k and shuffles hand them round), and the
+// column weights of two nodes come from the two lane groups r = 0, 1.  Lanes
+// accumulate over all terms in registers; a transposed reduce-scatter per tile
+// finishes each node.
 #include <algorithm>
 #include <cstring>
 
@@ -21,6 +26,7 @@
 namespace agft {
 
 constexpr int G2_THREADS = 256;
+constexpr int G2_WARPS = G2_THREADS / 32;
 constexpr int G2_PTS = 8;                              // nodes per half-warp
 constexpr int G2_TILE = (G2_THREADS / 16) * G2_PTS;    // 128 nodes per CTA tile
 
@@ -38,6 +44,38 @@ __device__ __forceinline__ const DevPlan &tile_plan(const DevPlan &single, const
 
 __device__ __forceinline__ int tile_terms(const DevPlan &D) { return (D.skip && *D.skip) ? 0 : D.n_act; }
 
+// this CTA's first tile at or after t (stride gridDim.x) with terms to run
+__device__ __forceinline__ int next_busy_tile(const DevPlan &single, const BatchArgs &B, int t, int n_tiles) {
+    int lt;
+    while (t < n_tiles && tile_terms(tile_plan(single, B, t, lt)) == 0) t += gridDim.x;
+    return t;
+}
+
+// Moves (t, s) = (tile, term of that tile) `steps` terms ahead in this CTA's
+// stream; t >= n_tiles when the stream ends first.
+__device__ __forceinline__ void stream_ahead(const DevPlan &single, const BatchArgs &B, int n_tiles, int &t, int &s,
+                                             int steps) {
+    s += steps;
+    while (t < n_tiles) {
+        int lt;
+        const int nt = tile_terms(tile_plan(single, B, t, lt));
+        if (s < nt) return;
+        s -= nt;
+        t = next_busy_tile(single, B, t + gridDim.x, n_tiles);
+    }
+}
+
+// One thread: copy the stored grid of term s of tile t into buffer buf.
+__device__ __forceinline__ void issue_grid(const DevPlan &single, const BatchArgs &B, int t, int s, int buf,
+                                           float2 *sm2, int gb_el, uint64_t *bars) {
+    int lt;
+    const DevPlan &D = tile_plan(single, B, t, lt);
+    const ActRec &R = D.act_rec[s];
+    fence_proxy_async();
+    mbar_expect_tx(&bars[buf], (uint32_t)R.grid_bytes);
+    bulk_g2s(sm2 + (buf ? gb_el : 0), D.grids + R.grid_off, (uint32_t)R.grid_bytes, &bars[buf]);
+}
+
 template <int MR, int PITCH>
 __global__ void __launch_bounds__(G2_THREADS, 2)
 gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, float2 *__restrict__ f_base,
@@ -45,48 +83,40 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
     extern __shared__ __align__(128) float2 sm2[];
     const int gb_el = (int)(max_grid_bytes / 8);
     float *xs = (float *)(sm2 + 2 * gb_el);                     // [d][G2_TILE]
-    uint64_t *bars = (uint64_t *)(xs + dmax * G2_TILE);
+    uint64_t *bars = (uint64_t *)(xs + dmax * G2_TILE);         // full barriers of the two buffers
+    unsigned int *outs = (unsigned int *)(bars + 2);            // warps done with each buffer (running count)
     (void)pitch_rt;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
+    const int half = lane >> 4;
     const int sub = lane & 15;
     const int r = sub >> 3, k = sub & 7;
-    const int hw = (tid >> 5) * 2 + (lane >> 4);
+    const int hw = (tid >> 5) * 2 + half;
     const int pbase = hw * G2_PTS;
 
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
+        outs[0] = outs[1] = 0;
         fence_barrier_init();
     }
     __syncthreads();
 
-    // first item of this CTA: its first tile whose problem has terms to run
-    int tile = blockIdx.x;
-    {
-        int lt;
-        while (tile < n_tiles && tile_terms(tile_plan(single, B, tile, lt)) == 0) tile += gridDim.x;
-    }
+    int tile = next_busy_tile(single, B, blockIdx.x, n_tiles);
     if (tile < n_tiles && tid == 0) {
-        int lt;
-        const DevPlan &D0 = tile_plan(single, B, tile, lt);
-        const Term &T0 = D0.terms[D0.act[0]];
-        mbar_expect_tx(&bars[0], (uint32_t)T0.grid_bytes);
-        bulk_g2s(sm2, D0.grids + T0.grid_off, (uint32_t)T0.grid_bytes, &bars[0]);
+        int t1 = tile, s1 = 0;
+        issue_grid(single, B, t1, s1, 0, sm2, gb_el, bars);
+        stream_ahead(single, B, n_tiles, t1, s1, 1);
+        if (t1 < n_tiles) issue_grid(single, B, t1, s1, 1, sm2, gb_el, bars);
     }
 
     long long it = 0;
-    for (; tile < n_tiles;) {
+    while (tile < n_tiles) {
         int lt;
         const DevPlan &D = tile_plan(single, B, tile, lt);
         const int nt = tile_terms(D);
-        // the next tile of this CTA with terms to run (for the prefetch chain)
-        int next_tile = tile + gridDim.x;
-        {
-            int l2;
-            while (next_tile < n_tiles && tile_terms(tile_plan(single, B, next_tile, l2)) == 0) next_tile += gridDim.x;
-        }
+        const int next_tile = next_busy_tile(single, B, tile + gridDim.x, n_tiles);
         const long long M = D.M;
         const int d = D.d;
         const float *__restrict__ X = D.x;
@@ -119,89 +149,89 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
             for (int j = 0; j < MR; ++j) rw[i][j] = 0.f;
         }
         int cur_wc = -1;
+        ActRec R = D.act_rec[0];
         for (int s = 0; s < nt; ++s, ++it) {
+            ActRec Rn = R;
+            if (s + 1 < nt) Rn = D.act_rec[s + 1];   // prefetch the next term's record
             const int b = (int)(it & 1);
             const uint32_t parity = (uint32_t)((it >> 1) & 1);
-            if (tid == 0) {
-                const Term *Tn = nullptr;
-                const float2 *gn = nullptr;
-                if (s + 1 < nt) {
-                    Tn = &D.terms[D.act[s + 1]];
-                    gn = D.grids;
-                } else if (next_tile < n_tiles) {
-                    int l2;
-                    const DevPlan &Dn = tile_plan(single, B, next_tile, l2);
-                    Tn = &Dn.terms[Dn.act[0]];
-                    gn = Dn.grids;
-                }
-                if (Tn) {
-                    fence_proxy_async();
-                    mbar_expect_tx(&bars[b ^ 1], (uint32_t)Tn->grid_bytes);
-                    bulk_g2s(sm2 + (b ? 0 : gb_el), gn + Tn->grid_off, (uint32_t)Tn->grid_bytes, &bars[b ^ 1]);
-                }
-            }
-            const Term &T = D.terms[D.act[s]];
-            const int order = T.order, n = T.n;
-            const int pitch = PITCH ? PITCH : T.stride;   // order-2 row pitch of this problem
+            const int order = R.order, n = R.n;
+            const int pitch = PITCH ? PITCH : R.stride;   // order-2 row pitch of this problem
             const float nf = (float)n, hn = 0.5f * (float)n, nm1 = (float)(n - 1);
-            if (T.wc != cur_wc) {
-                const float *wsrc = D.windows[T.wc].c[k];
+            if (R.wc != cur_wc) {
+                const float *wsrc = D.windows[R.wc].c[k];
 #pragma unroll
                 for (int i = 0; i < NCOEF; ++i) cc[i] = __ldg(wsrc + i);
-                cur_wc = T.wc;
+                cur_wc = R.wc;
             }
-            if (order == 2 && D.act_newgroup[s]) {
-                float rc[MR][NCOEF];
+            if (order == 2 && R.newgroup) {
+                // lane (r, k): rows r, r+2, .. of node k; then every lane
+                // fetches its rows for all 8 nodes of its half-warp
+                float myrw[MR];
+                {
+                    const float t = fmaf(xs[R.row0 * G2_TILE + pbase + k], nf, hn);
+                    const float fl = fminf(floorf(t), nm1);
+                    const float v = fmaf(2.f, t - fl, -1.f);
 #pragma unroll
-                for (int j = 0; j < MR; ++j)
-#pragma unroll
-                    for (int i = 0; i < NCOEF; ++i) rc[j][i] = __ldg(&D.windows[T.wr].c[r + 2 * j][i]);
-                const float *xr = xs + T.row0 * G2_TILE + pbase;
+                    for (int j = 0; j < MR; ++j) myrw[j] = horner8(D.windows[R.wr].c[r + 2 * j], v);
+                }
+                const float *xr = xs + R.row0 * G2_TILE + pbase;
 #pragma unroll
                 for (int i = 0; i < G2_PTS; ++i) {
                     const float t = fmaf(xr[i], nf, hn);
                     const float fl = fminf(floorf(t), nm1);
-                    const float v = fmaf(2.f, t - fl, -1.f);
-#pragma unroll
-                    for (int j = 0; j < MR; ++j) rw[i][j] = horner8(rc[j], v);
                     rbase[i] = ((int)fl + r) * pitch + k;   // stored row fl + r (row halo MR - 1)
+#pragma unroll
+                    for (int j = 0; j < MR; ++j)
+                        rw[i][j] = __shfl_sync(0xffffffffu, myrw[j], (half << 4) | (r << 3) | i);
                 }
             }
             mbar_wait(&bars[b], parity, D.err, 1);
             const int boff = b ? gb_el : 0;
-            const float *xc = xs + T.col * G2_TILE + pbase;
+            const float *xc = xs + R.col * G2_TILE + pbase;
             if (order == 2) {
 #pragma unroll
-                for (int i = 0; i < G2_PTS; ++i) {
-                    const float t = fmaf(xc[i], nf, hn);
-                    const float fl = fminf(floorf(t), nm1);
-                    const float cw = horner8(cc, fmaf(2.f, t - fl, -1.f));
-                    const int idx = boff + rbase[i] + (int)fl;
-                    float sx = 0.f, sy = 0.f;
+                for (int i = 0; i < G2_PTS; i += 2) {
+                    const float t0 = fmaf(xc[i], nf, hn), t1 = fmaf(xc[i + 1], nf, hn);
+                    const float fl0 = fminf(floorf(t0), nm1), fl1 = fminf(floorf(t1), nm1);
+                    const float wt = horner8(cc, r ? fmaf(2.f, t1 - fl1, -1.f) : fmaf(2.f, t0 - fl0, -1.f));
+                    const float cw0 = __shfl_sync(0xffffffffu, wt, (half << 4) | k);
+                    const float cw1 = __shfl_sync(0xffffffffu, wt, (half << 4) | 8 | k);
+                    const int idx0 = boff + rbase[i] + (int)fl0;
+                    const int idx1 = boff + rbase[i + 1] + (int)fl1;
+                    float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f;
 #pragma unroll
                     for (int j = 0; j < MR; ++j) {
-                        const float2 g = sm2[idx + 2 * j * pitch];
-                        sx = fmaf(rw[i][j], g.x, sx);
-                        sy = fmaf(rw[i][j], g.y, sy);
+                        const float2 g0 = sm2[idx0 + 2 * j * pitch];
+                        const float2 g1 = sm2[idx1 + 2 * j * pitch];
+                        sx0 = fmaf(rw[i][j], g0.x, sx0);
+                        sy0 = fmaf(rw[i][j], g0.y, sy0);
+                        sx1 = fmaf(rw[i + 1][j], g1.x, sx1);
+                        sy1 = fmaf(rw[i + 1][j], g1.y, sy1);
                     }
-                    ax[i] = fmaf(cw, sx, ax[i]);
-                    ay[i] = fmaf(cw, sy, ay[i]);
+                    ax[i] = fmaf(cw0, sx0, ax[i]);
+                    ay[i] = fmaf(cw0, sy0, ay[i]);
+                    ax[i + 1] = fmaf(cw1, sx1, ax[i + 1]);
+                    ay[i + 1] = fmaf(cw1, sy1, ay[i + 1]);
                 }
             } else if (order == 1) {
-                if (r == 0) {
+                // lane group r takes nodes i + r of each pair
 #pragma unroll
-                    for (int i = 0; i < G2_PTS; ++i) {
-                        const float t = fmaf(xc[i], nf, hn);
-                        const float fl = fminf(floorf(t), nm1);
-                        const float cw = horner8(cc, fmaf(2.f, t - fl, -1.f));
-                        const float2 g = sm2[boff + (int)fl + k];
-                        ax[i] = fmaf(cw, g.x, ax[i]);
-                        ay[i] = fmaf(cw, g.y, ay[i]);
-                    }
+                for (int i = 0; i < G2_PTS; i += 2) {
+                    const float t = fmaf(xc[i + r], nf, hn);
+                    const float fl = fminf(floorf(t), nm1);
+                    const float cw = horner8(cc, fmaf(2.f, t - fl, -1.f));
+                    const float2 g = sm2[boff + (int)fl + k];
+                    const float vx = cw * g.x, vy = cw * g.y;
+                    ax[i] += r ? 0.f : vx;
+                    ay[i] += r ? 0.f : vy;
+                    ax[i + 1] += r ? vx : 0.f;
+                    ay[i + 1] += r ? vy : 0.f;
                 }
             } else {
                 // order 3: rows (first, second) wrap modulo n; row weights evaluated directly
-                const Window &W = D.windows[T.wr];
+                const Term &T = D.terms[R.term];
+                const Window &W = D.windows[R.wr];
                 const int mr = T.mr, mc = T.mc, stride = T.stride;
                 const float *xa_p = xs + T.row0 * G2_TILE + pbase;
                 const float *xb_p = xs + T.row1 * G2_TILE + pbase;
@@ -231,7 +261,20 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
                     ay[i] = fmaf(cw, sy, ay[i]);
                 }
             }
-            __syncthreads();
+            // done with buffer b: the last warp out refills it with the term
+            // two steps ahead in this CTA's stream
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                const unsigned int prev = atomicAdd(&outs[b], 1u);
+                if ((prev + 1) % G2_WARPS == 0) {
+                    __threadfence_block();
+                    int t2 = tile, s2 = s;
+                    stream_ahead(single, B, n_tiles, t2, s2, 2);
+                    if (t2 < n_tiles) issue_grid(single, B, t2, s2, b, sm2, gb_el, bars);
+                }
+            }
+            R = Rn;
         }
         // reduce over the 16 lanes of each half-warp: first the two row halves
         // (lane ^ 8), then a transposed reduce-scatter over the 8 nodes
@@ -255,6 +298,7 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
         }
         const long long pp = p0 + pbase + (sub & 7);
         if (sub < 8 && pp < M) f[pp] = make_float2(ax[0] + c0.x, ay[0] + c0.y);
+        __syncthreads();   // every warp is done with xs before the next tile stages it
         tile = next_tile;
     }
 }
@@ -282,7 +326,7 @@ static void launch_mr(cudaStream_t st, const DevPlan &v, const BatchArgs &B, con
 
 int gather_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, const float2 *fhat, float2 *f,
                   int n_tiles, int mr, int pitch, long long max_grid_bytes, int dmax, int sm_count) {
-    const size_t smem = (size_t)max_grid_bytes * 2 + (size_t)dmax * G2_TILE * 4 + 64;
+    const size_t smem = (size_t)max_grid_bytes * 2 + (size_t)dmax * G2_TILE * 4 + 64;   // + barriers, counters
     if (smem > (size_t)MAX_SMEM) return ANOVA_ERR_UNSUPPORTED;
     if (n_tiles <= 0) return ANOVA_OK;
     const int per_sm = smem * 2 <= (size_t)MAX_SMEM ? 2 : 1;

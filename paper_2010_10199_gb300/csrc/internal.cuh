@@ -70,6 +70,32 @@ struct Term {
     int pad2_;
 };
 
+// What the forward gather needs of an active term, in one 48-byte record
+// (prefetched by every warp one term ahead).
+struct ActRec {
+    int order, newgroup;   // newgroup: 1 if the row weights must be recomputed
+    int wc, wr;            // window ids (column axis, row axes)
+    int col, row0, n, stride;
+    long long grid_off;
+    int grid_bytes, term;  // term: index into the term table
+};
+
+inline ActRec make_act_rec(const Term &T, int term, int newgroup) {
+    ActRec a;
+    a.order = T.order;
+    a.newgroup = newgroup;
+    a.wc = T.wc;
+    a.wr = T.wr;
+    a.col = T.col;
+    a.row0 = T.row0;
+    a.n = T.n;
+    a.stride = T.stride;
+    a.grid_off = T.grid_off;
+    a.grid_bytes = (int)T.grid_bytes;
+    a.term = term;
+    return a;
+}
+
 // A node in the cell order of one term (16 bytes, stored as float4):
 //   x: 2 tau_row - 1 (order 2; 0 for order 1), y: 2 tau_col - 1, the window
 //   polynomial arguments of the node's fractional grid positions;
@@ -95,7 +121,7 @@ struct DevPlan {
     long long max_grid_bytes;
     int *err;                 // device error word (bounded waits)
     const int *act;           // active schedule: indices into terms, n_act entries
-    const unsigned char *act_newgroup;  // per active entry: recompute row weights
+    const ActRec *act_rec;    // per active entry: the gather's view of the term
     int n_act;
     const int *skip;          // if non-null and nonzero, kernels return at once
     const float2 *grids;      // stored grids of this problem
@@ -154,7 +180,7 @@ struct Plan {
     int pitch2;             // row pitch shared by all order-2 grids
     // active term list (all scheduled terms unless a group mask restricts it)
     int *act;
-    unsigned char *act_newgroup;
+    ActRec *act_rec;
     int n_act;
     int *h_act;
     const int *skip;        // device flag read by every transform kernel (or null)

@@ -37,7 +37,7 @@ static long long s_empty[NOALLOC_MAX_TERMS];
 static int s_order[NOALLOC_MAX_TERMS];
 static int s_sched[NOALLOC_MAX_TERMS];
 static int s_act[NOALLOC_MAX_TERMS];
-static unsigned char s_newgroup[NOALLOC_MAX_TERMS];
+static ActRec s_rec[NOALLOC_MAX_TERMS];
 static std::mutex s_lock;
 static void *s_dev_ptr[NOALLOC_MAX_DEVICES];
 
@@ -199,7 +199,7 @@ extern "C" int grouped_trafo_noalloc(int d, int64_t M, const float *x_dev, int n
             if (P.order == 2 && P.row0 == T.row0 && P.wr == T.wr && P.n == T.n) T.new_rowgroup = 0;
         }
         s_act[s] = s;
-        s_newgroup[s] = (unsigned char)T.new_rowgroup;
+        s_rec[s] = make_act_rec(T, s, T.new_rowgroup);
     }
 
     // carve the scratch array; reject what does not fit
@@ -209,7 +209,7 @@ extern "C" int grouped_trafo_noalloc(int d, int64_t M, const float *x_dev, int n
     size_t o_empty = align256(o_dec + sizeof(float) * std::max(1, n_dec));
     size_t o_act = align256(o_empty + sizeof(long long) * std::max(1, n_empty));
     size_t o_ng = align256(o_act + sizeof(int) * std::max(1, n_sched));
-    size_t o_err = align256(o_ng + std::max(1, n_sched));
+    size_t o_err = align256(o_ng + sizeof(ActRec) * std::max(1, n_sched));
     size_t o_x = align256(o_err + 16);
     size_t o_grid = align256(o_x + sizeof(float) * (size_t)d * (size_t)M);
     size_t total = o_grid + (size_t)goff * 8;
@@ -226,7 +226,7 @@ extern "C" int grouped_trafo_noalloc(int d, int64_t M, const float *x_dev, int n
     if (e == cudaSuccess && n_sched)
         e = cudaMemcpyAsync(base + o_act, s_act, sizeof(int) * n_sched, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && n_sched)
-        e = cudaMemcpyAsync(base + o_ng, s_newgroup, n_sched, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(base + o_ng, s_rec, sizeof(ActRec) * n_sched, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_err, 0, 16, st);
     if (e != cudaSuccess) return cuda_status(e);
     const long long total_x = (long long)d * M;
@@ -259,7 +259,7 @@ extern "C" int grouped_trafo_noalloc(int d, int64_t M, const float *x_dev, int n
     p.pitch2 = pitch2;
     p.err = (int *)(base + o_err);
     p.act = (int *)(base + o_act);
-    p.act_newgroup = base + o_ng;
+    p.act_rec = (ActRec *)(base + o_ng);
     p.n_act = n_sched;
     p.h_act = s_act;
     cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, dev);

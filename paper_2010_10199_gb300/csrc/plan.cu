@@ -146,18 +146,18 @@ __global__ void wrap_nodes_f64(const double *in, double *out, long long total) {
 // `user_mask` (all when null), with the row-group flags recomputed for that
 // list.  Uploaded on the plan's stream.
 int set_active_terms(Plan &p, const unsigned char *user_mask) {
-    static thread_local std::vector<unsigned char> flags;
-    flags.assign(std::max(1, p.n_terms), 0);
+    static thread_local std::vector<ActRec> recs;
+    recs.clear();
     int n = 0;
     for (int s = 0; s < p.n_terms; ++s) {
         const Term &T = p.h_terms[s];
         if (user_mask && !user_mask[T.user_index]) continue;
-        unsigned char ng = 1;
+        int ng = 1;
         if (T.order == 2 && n > 0) {
             const Term &P = p.h_terms[p.h_act[n - 1]];
             if (P.order == 2 && P.row0 == T.row0 && P.wr == T.wr && P.n == T.n) ng = 0;
         }
-        flags[n] = ng;
+        recs.push_back(make_act_rec(T, s, ng));
         p.h_act[n++] = s;
     }
     p.n_act = n;
@@ -166,10 +166,11 @@ int set_active_terms(Plan &p, const unsigned char *user_mask) {
     p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count);
     if (p.h_items) p.n_items = append_spread_items(p, 0, p.spread_K, p.h_items);
     cudaError_t e = cudaMemcpyAsync(p.act, p.h_act, sizeof(int) * n, cudaMemcpyHostToDevice, p.stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p.act_newgroup, flags.data(), n, cudaMemcpyHostToDevice, p.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p.act_rec, recs.data(), sizeof(ActRec) * n, cudaMemcpyHostToDevice, p.stream);
     if (e == cudaSuccess && p.n_items)
         e = cudaMemcpyAsync(p.items, p.h_items, sizeof(int4) * p.n_items, cudaMemcpyHostToDevice, p.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);   // flags is reused by the next call
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);   // recs is reused by the next call
     return cuda_status(e);
 }
 
@@ -190,7 +191,7 @@ DevPlan dev_view(const Plan &p) {
     v.max_grid_bytes = p.max_grid_bytes;
     v.err = p.err;
     v.act = p.act;
-    v.act_newgroup = p.act_newgroup;
+    v.act_rec = p.act_rec;
     v.n_act = p.n_act;
     v.skip = p.skip;
     v.grids = (const float2 *)p.grids;
@@ -207,7 +208,7 @@ static void free_plan(Plan &p) {
     if (p.solver && p.solver_free) p.solver_free(p.solver);
     p.solver = nullptr;
     void *bufs[] = {p.x, p.terms, p.windows, p.deconv, p.deconvd, p.empty_off, p.grids, p.partials,
-                    p.err, p.scratch, p.act, p.act_newgroup, p.items, p.counter, p.srec};
+                    p.err, p.scratch, p.act, p.act_rec, p.items, p.counter, p.srec};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete[] p.h_terms;
@@ -471,7 +472,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     chk(cudaMalloc(&p.grids, (size_t)std::max<long long>(1, p.grid_elems) * 8));
     chk(cudaMalloc(&p.err, sizeof(int) * 4));
     chk(cudaMalloc(&p.act, sizeof(int) * std::max(1, p.n_terms)));
-    chk(cudaMalloc(&p.act_newgroup, std::max(1, p.n_terms)));
+    chk(cudaMalloc(&p.act_rec, sizeof(ActRec) * std::max(1, p.n_terms)));
     p.h_act = new int[std::max(1, p.n_terms)];
     // adjoint partial grids: one per node chunk of a term (work items of the
     // spread are (term, chunk) pairs), bounded to 8 GB
