@@ -224,4 +224,88 @@ __device__ int smem_fft(C *a, C *b, int n, int nlines, int lstride, int estride,
     return which;
 }
 
+// Unnormalised FFT with sign `sign` along every axis of an n^s array held in
+// shared memory (a; b is scratch of the same size), s = 1..3: all lines of an
+// axis at once, line bases (l / inner) * inner * n + l % inner for the axis
+// whose element stride is `inner`.  All threads of the block call it; returns
+// the buffer that holds the result.
+template <typename C, typename R>
+__device__ C *grid_fft(C *a, C *b, int n, int s, int sign) {
+    using O = CplxOps<C, R>;
+    int fe = n;
+    for (int j = 1; j < s; ++j) fe *= n;
+    C *cur = a, *oth = b;
+    int inner = 1;
+    int rad[24];
+    const int ns = fft_radices(n, rad);
+    for (int ax = s - 1; ax >= 0; --ax) {
+        const int nlines = fe / n;
+        C *src = cur, *dst = oth;
+        int which = 0, Ns = 1;
+        for (int st = 0; st < ns; ++st) {
+            const int Rr = rad[st];
+            const int nb = n / Rr;
+            for (int w = threadIdx.x; w < nlines * nb; w += blockDim.x) {
+                const int l = w / nb, j = w - l * nb;
+                const int base = (l / inner) * inner * n + (l % inner);
+                const C *in = src + base;
+                C *out = dst + base;
+                C v[5];
+                const int jm = j % Ns;
+                for (int r = 0; r < Rr; ++r) {
+                    C x = in[(j + r * nb) * inner];
+                    if (r && jm) {
+                        R sn, cs;
+                        O::sincospi_((R)(2 * sign * r * jm) / (R)(Ns * Rr), &sn, &cs);
+                        x = cmul(x, O::mk(cs, sn));
+                    }
+                    v[r] = x;
+                }
+                C V[5];
+                if (Rr == 2) {
+                    V[0] = O::mk(v[0].x + v[1].x, v[0].y + v[1].y);
+                    V[1] = O::mk(v[0].x - v[1].x, v[0].y - v[1].y);
+                } else if (Rr == 4) {
+                    const C s0 = O::mk(v[0].x + v[2].x, v[0].y + v[2].y);
+                    const C d0 = O::mk(v[0].x - v[2].x, v[0].y - v[2].y);
+                    const C s1 = O::mk(v[1].x + v[3].x, v[1].y + v[3].y);
+                    const C d1 = O::mk(v[1].x - v[3].x, v[1].y - v[3].y);
+                    const C jd1 = sign > 0 ? O::mk(-d1.y, d1.x) : O::mk(d1.y, -d1.x);   // sign i d1
+                    V[0] = O::mk(s0.x + s1.x, s0.y + s1.y);
+                    V[2] = O::mk(s0.x - s1.x, s0.y - s1.y);
+                    V[1] = O::mk(d0.x + jd1.x, d0.y + jd1.y);
+                    V[3] = O::mk(d0.x - jd1.x, d0.y - jd1.y);
+                } else {
+                    for (int q = 0; q < Rr; ++q) {
+                        C acc = v[0];
+                        for (int r = 1; r < Rr; ++r) {
+                            R sn, cs;
+                            O::sincospi_((R)(2 * sign * ((r * q) % Rr)) / (R)Rr, &sn, &cs);
+                            const C t = cmul(v[r], O::mk(cs, sn));
+                            acc.x += t.x;
+                            acc.y += t.y;
+                        }
+                        V[q] = acc;
+                    }
+                }
+                const int idxD = (j / Ns) * Ns * Rr + jm;
+                for (int r = 0; r < Rr; ++r) out[(idxD + r * Ns) * inner] = V[r];
+            }
+            __syncthreads();
+            C *t = src;
+            src = dst;
+            dst = t;
+            which ^= 1;
+            Ns *= Rr;
+        }
+        if (which) {
+            C *t = cur;
+            cur = oth;
+            oth = t;
+        }
+        inner *= n;
+    }
+    return cur;
+}
+
 }  // namespace agft

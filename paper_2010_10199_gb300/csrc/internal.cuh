@@ -67,6 +67,8 @@ struct Term {
     long long coef_len;
     int dc_off, dr_off;   // offsets of the column / row deconvolution factors
     int user_index;
+    int slot_c;           // FP64 plans: window-table slots of the column and row coordinates
+    int slot_r0, slot_r1;
     int pad2_;
 };
 
@@ -193,6 +195,13 @@ struct Plan {
     int *counter;           // work-queue counter of the spread
     float4 *srec;           // cell-sorted node records (null: none), n_sorted slots of M
     int n_sorted;
+    // FP64 plans: window weights per (window, coordinate) slot and node, the
+    // precomputed form of psi (taps 0..2m-1, zero padded to 8), and the first
+    // tap's grid index floor(n x + n/2) in [0, n)
+    double *wt64;           // [n_slots][M][8]
+    int *wb64;              // [n_slots][M]
+    int4 *slots64;          // per slot: (window id, coordinate, n, m)
+    int n_slots64;
     int gather_ctas;
     int *err;
     void *scratch;          // reduction scratch
@@ -229,6 +238,10 @@ int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArg
 size_t spread_smem_bytes(long long max_grid_bytes);
 // Sorts the nodes by grid cell for every term with sort_slot >= 0 (sort.cu).
 int sort_nodes_by_cell(Plan &p);
+// FP64 path (f64.cu): window tables, forward and adjoint transforms.
+int build_window_tables_f64(Plan &p);
+int launch_trafo_f64(Plan &p, const double2 *fhat, double2 *f);
+int launch_adjoint_f64(Plan &p, const double2 *y, double2 *fhat);
 int spread_ctas_per_sm(long long max_grid_bytes);
 // Node chunks per term for a spread over n_act_total active terms (all
 // problems of a launch) on sm_count SMs: about three items per resident CTA,

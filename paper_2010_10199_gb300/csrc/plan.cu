@@ -208,7 +208,7 @@ static void free_plan(Plan &p) {
     if (p.solver && p.solver_free) p.solver_free(p.solver);
     p.solver = nullptr;
     void *bufs[] = {p.x, p.terms, p.windows, p.deconv, p.deconvd, p.empty_off, p.grids, p.partials,
-                    p.err, p.scratch, p.act, p.act_rec, p.items, p.counter, p.srec};
+                    p.err, p.scratch, p.act, p.act_rec, p.items, p.counter, p.srec, p.wt64, p.wb64, p.slots64};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete[] p.h_terms;
@@ -256,7 +256,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
     if (o.precision < ANOVA_PREC_F32 || o.precision > ANOVA_PREC_F64) return ANOVA_ERR_INVALID;
-    if (o.precision != ANOVA_PREC_F32) return ANOVA_ERR_UNSUPPORTED;   // 16-bit and FP64 grids: later
+    if (o.precision != ANOVA_PREC_F32 && o.precision != ANOVA_PREC_F64) return ANOVA_ERR_UNSUPPORTED;   // 16-bit grids
     if (o.eps <= 0) o.eps = 1e-5;
     if (o.sigma <= 0) o.sigma = 2.0;
     if (o.sigma < 1.5 || o.sigma > 8) return ANOVA_ERR_INVALID;
@@ -404,12 +404,14 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         T.grid_off = goff;
         long long elems = (long long)T.erows * T.stride;
         elems = (elems + 1) & ~1LL;   // 16-byte multiple
-        T.grid_bytes = elems * 8;
+        const bool f64 = p.precision == ANOVA_PREC_F64;
+        T.grid_bytes = elems * (f64 ? 16 : 8);
         goff += elems;
         maxbytes = std::max(maxbytes, T.grid_bytes);
         long long fe = 1;
         for (int j = 0; j < T.order; ++j) fe *= T.n;
-        if (fe * 16 > 200 * 1024 || T.grid_bytes > 100 * 1024) status = ANOVA_ERR_UNSUPPORTED;
+        // shared-memory limits of the FFT passes (two copies) and of the spread (one grid)
+        if (fe * (f64 ? 32 : 16) > 200 * 1024 || T.grid_bytes > (f64 ? 200 : 100) * 1024) status = ANOVA_ERR_UNSUPPORTED;
         max_fft = (int)std::max<long long>(max_fft, fe);
         T.coef_off = p.h_user_off[i];
         T.coef_len = p.h_user_len[i];
@@ -453,6 +455,23 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     p.max_grid_bytes = maxbytes;
     p.max_fft_elems = max_fft;
     p.n_windows = (int)wins.size();
+    // FP64 plans: one window table per (window, coordinate) pair in use
+    std::vector<int4> slots64;
+    if (p.precision == ANOVA_PREC_F64) {
+        auto slot_of = [&](int w, int c, int n, int m) {
+            for (size_t i = 0; i < slots64.size(); ++i)
+                if (slots64[i].x == w && slots64[i].y == c) return (int)i;
+            slots64.push_back(make_int4(w, c, n, m));
+            return (int)slots64.size() - 1;
+        };
+        for (int s = 0; s < p.n_terms; ++s) {
+            Term &T = p.h_terms[s];
+            T.slot_c = slot_of(T.wc, T.col, T.n, T.mc);
+            T.slot_r0 = T.order >= 2 ? slot_of(T.wr, T.row0, T.n, T.mr) : -1;
+            T.slot_r1 = T.order == 3 ? slot_of(T.wr, T.row1, T.n, T.mr) : -1;
+        }
+        p.n_slots64 = (int)slots64.size();
+    }
     for (int i = 0; i < n_terms; ++i) {
         (void)i;
     }
@@ -469,7 +488,8 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     chk(cudaMalloc(&p.deconv, sizeof(float) * std::max<size_t>(1, dec.size())));
     chk(cudaMalloc(&p.deconvd, sizeof(double) * std::max<size_t>(1, decd.size())));
     chk(cudaMalloc(&p.empty_off, sizeof(long long) * std::max<size_t>(1, empties.size())));
-    chk(cudaMalloc(&p.grids, (size_t)std::max<long long>(1, p.grid_elems) * 8));
+    const size_t esize = p.precision == ANOVA_PREC_F64 ? 16 : 8;   // bytes per complex grid element
+    chk(cudaMalloc(&p.grids, (size_t)std::max<long long>(1, p.grid_elems) * esize));
     chk(cudaMalloc(&p.err, sizeof(int) * 4));
     chk(cudaMalloc(&p.act, sizeof(int) * std::max(1, p.n_terms)));
     chk(cudaMalloc(&p.act_rec, sizeof(ActRec) * std::max(1, p.n_terms)));
@@ -484,12 +504,20 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     p.gather_ctas = (int)std::min<long long>((long long)p.sm_count,
                                              std::max<long long>(1, (M + GATHER_TILE - 1) / GATHER_TILE));
     if (e == cudaSuccess && p.n_terms > 0)
-        chk(cudaMalloc(&p.partials, (size_t)kmax * (size_t)p.grid_elems * 8));
+        chk(cudaMalloc(&p.partials, (size_t)kmax * (size_t)p.grid_elems * esize));
     chk(cudaMalloc(&p.items, sizeof(int4) * (size_t)std::max(1, p.n_terms) * kmax));
     chk(cudaMalloc(&p.counter, sizeof(int)));
     p.h_items = new int4[(size_t)std::max(1, p.n_terms) * kmax];
     p.scratch_bytes = 1 << 20;
     chk(cudaMalloc(&p.scratch, p.scratch_bytes));
+    if (p.n_slots64 > 0 && M > 0) {
+        chk(cudaMalloc(&p.slots64, sizeof(int4) * p.n_slots64));
+        chk(cudaMalloc(&p.wt64, sizeof(double) * 8 * (size_t)p.n_slots64 * M));
+        chk(cudaMalloc(&p.wb64, sizeof(int) * (size_t)p.n_slots64 * M));
+        if (e == cudaSuccess)
+            chk(cudaMemcpyAsync(p.slots64, slots64.data(), sizeof(int4) * p.n_slots64, cudaMemcpyHostToDevice,
+                                p.stream));
+    }
     // cell-sorted node copies for the adjoint (terms of order <= 2), if they
     // fit in half the free device memory
     if (e == cudaSuccess && o.node_sort >= 0 && M > 0 && p.precision == ANOVA_PREC_F32) {
@@ -538,6 +566,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         chk(cudaGetLastError());
     }
     if (e == cudaSuccess) chk(cuda_err_of(sort_nodes_by_cell(p)));
+    if (e == cudaSuccess && p.precision == ANOVA_PREC_F64) chk(cuda_err_of(build_window_tables_f64(p)));
     if (e == cudaSuccess) chk(cuda_err_of(set_active_terms(p, nullptr)));
     chk(cudaStreamSynchronize(p.stream));
     // wins vector is copied; keep host term table
@@ -581,6 +610,7 @@ int grouped_trafo(anova_plan_t plan, const void *fhat_dev, void *f_dev) {
     if (p.n_coeffs > 0 && !fhat_dev) return ANOVA_ERR_INVALID;
     if (p.M == 0) return ANOVA_OK;
     cudaGetLastError();
+    if (p.precision == ANOVA_PREC_F64) return launch_trafo_f64(p, (const double2 *)fhat_dev, (double2 *)f_dev);
     return launch_trafo_f32(p, (const float2 *)fhat_dev, (float2 *)f_dev);
 }
 
@@ -590,6 +620,7 @@ int grouped_adjoint(anova_plan_t plan, const void *y_dev, void *fhat_dev) {
     if (!fhat_dev) return ANOVA_ERR_INVALID;
     if (p.M > 0 && !y_dev) return ANOVA_ERR_INVALID;
     cudaGetLastError();
+    if (p.precision == ANOVA_PREC_F64) return launch_adjoint_f64(p, (const double2 *)y_dev, (double2 *)fhat_dev);
     return launch_adjoint_f32(p, (const float2 *)y_dev, (float2 *)fhat_dev);
 }
 

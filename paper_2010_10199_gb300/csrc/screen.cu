@@ -24,7 +24,7 @@
 #include <cstring>
 #include <vector>
 
-#include "solvers.cuh"
+#include "solver_kernels.cuh"
 
 namespace agft {
 
@@ -111,10 +111,11 @@ struct ScreenWork {
 static int full_gradient(Plan &p, SolverWork *W, const float2 *y, const float2 *f, float2 *q) {
     int rc = set_active_terms(p, nullptr);
     if (rc) return rc;
-    rc = launch_trafo_f32(p, f, W->tM);
+    float2 *tM = (float2 *)W->tM;
+    rc = launch_trafo_f32(p, f, tM);
     if (rc) return rc;
-    k_residual<<<RED_BLOCKS, RED_THREADS, 0, p.stream>>>(W->st, W->tM, y, p.M, nullptr);
-    return launch_adjoint_f32(p, W->tM, q);
+    k_residual<<<RED_BLOCKS, RED_THREADS, 0, p.stream>>>(W->st, tM, y, p.M, nullptr);
+    return launch_adjoint_f32(p, tM, q);
 }
 
 static int features_host(Plan &p, SolverWork *W, ScreenWork &S, const float2 *f, std::vector<double> &pairs) {
@@ -143,7 +144,7 @@ int anova_screen_features(anova_plan_t plan, const void *y_dev, const double *w_
     StreamScope scope(p, W);
     const int G = p.n_user_terms;
     const long long n = p.n_coeffs;
-    k_weights<<<304, 256, 0, p.stream>>>(w_dev, W->ws, W->wd, n, 1);
+    k_weights<<<304, 256, 0, p.stream>>>(w_dev, (float *)W->ws, W->wd, n, 1);
     SolverState z;
     std::memset(&z, 0, sizeof(z));
     cudaMemcpyAsync(W->st, &z, sizeof(z), cudaMemcpyHostToDevice, p.stream);
@@ -195,7 +196,7 @@ int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, c
     auto t0 = std::chrono::steady_clock::now();
     {
         StreamScope scope(p, W);
-        k_weights<<<304, 256, 0, p.stream>>>(w_dev, W->ws, W->wd, n, 1);
+        k_weights<<<304, 256, 0, p.stream>>>(w_dev, (float *)W->ws, W->wd, n, 1);
         cudaMemcpyAsync(S.order, p.h_user_order, sizeof(int) * G, cudaMemcpyHostToDevice, p.stream);
         k_zero<<<304, 256, 0, p.stream>>>(S.fprev, n);
         SolverState z;

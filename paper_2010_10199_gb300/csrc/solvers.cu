@@ -21,7 +21,7 @@
 #include <cstring>
 #include <vector>
 
-#include "solvers.cuh"
+#include "solver_kernels.cuh"
 
 namespace agft {
 
@@ -53,54 +53,6 @@ __global__ void finish_sums(SolverState *st, const double *part, int nslots) {
     }
 }
 
-#define SKIP_IF_DONE \
-    if (st->done) return;
-
-// out = (scale ? scale[i] : 1) * in, |out|^2 partial into slot 0
-__global__ void k_scale_copy(const SolverState *st, float2 *out, const float2 *in, const float *scale, long long n,
-                             double *part) {
-    __shared__ double sh[32];
-    SKIP_IF_DONE
-    double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float2 v = in[i];
-        if (scale) {
-            float s = scale[i];
-            v.x *= s;
-            v.y *= s;
-        }
-        out[i] = v;
-        acc += (double)v.x * v.x + (double)v.y * v.y;
-    }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
-}
-
-// out = a - coef * out (coef = st->red-derived scalar selected by `which`), partial |out|^2
-// which: 0 -> alpha, 1 -> beta
-__global__ void k_sub_scaled(const SolverState *st, float2 *out, const float2 *a, const float *scale, int which,
-                             long long n, double *part) {
-    __shared__ double sh[32];
-    SKIP_IF_DONE
-    const float c = (float)(which == 0 ? st->alpha : st->beta);
-    double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float2 av = a[i];
-        if (scale) {
-            float s = scale[i];
-            av.x *= s;
-            av.y *= s;
-        }
-        float2 o = out[i];
-        o.x = av.x - c * o.x;
-        o.y = av.y - c * o.y;
-        out[i] = o;
-        acc += (double)o.x * o.x + (double)o.y * o.y;
-    }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
 // out *= 1/norm where norm = sqrt(st->red[0]); writes the norm to alpha (which 0) or beta (1)
 __global__ void k_set_norm(SolverState *st, int which) {
     if (st->done) return;
@@ -111,268 +63,11 @@ __global__ void k_set_norm(SolverState *st, int which) {
         st->beta = nv;
 }
 
-__global__ void k_normalize(const SolverState *st, float2 *v, long long n, int which) {
-    SKIP_IF_DONE
-    const double nv = which == 0 ? st->alpha : st->beta;
-    const float inv = nv > 0 ? (float)(1.0 / nv) : 0.f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float2 a = v[i];
-        a.x *= inv;
-        a.y *= inv;
-        v[i] = a;
-    }
-}
-
 __global__ void k_lsqr_init(SolverState *st) { lsqr_init_dev(st); }
 
 __global__ void k_lsqr_scalars(SolverState *st) { lsqr_scalars_dev(st); }
 
-// x += phi/rho w ; w = v - theta/rho w ; partial |x|^2
-__global__ void k_lsqr_update(const SolverState *st, float2 *x, float2 *w, const float2 *v, long long n,
-                              double *part) {
-    __shared__ double sh[32];
-    SKIP_IF_DONE
-    const float a = (float)st->phi_rho, b = (float)st->theta_rho;
-    double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float2 wi = w[i], xi = x[i], vi = v[i];
-        xi.x += a * wi.x;
-        xi.y += a * wi.y;
-        wi.x = vi.x - b * wi.x;
-        wi.y = vi.y - b * wi.y;
-        x[i] = xi;
-        w[i] = wi;
-        acc += (double)xi.x * xi.x + (double)xi.y * xi.y;
-    }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
 __global__ void k_lsqr_test(SolverState *st) { lsqr_test_dev(st); }
-
-__global__ void k_weights(const double *w, float *ws, double *wd, long long n, int mode) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double om = w ? w[i] : 1.0;
-        wd[i] = om;
-        ws[i] = mode == 0 ? (float)(1.0 / sqrt(om)) : (float)om;
-    }
-}
-
-__global__ void k_zero(float2 *v, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        v[i] = make_float2(0.f, 0.f);
-}
-
-// zero the coefficient blocks of masked groups (the adjoint skips inactive terms)
-__global__ void k_mask_groups(float2 *v, const long long *goff, const long long *glen, const unsigned char *gmask) {
-    const int u = blockIdx.x;
-    if (gmask[u]) return;
-    const long long o = goff[u], m = glen[u];
-    for (long long i = threadIdx.x; i < m; i += blockDim.x) v[o + i] = make_float2(0.f, 0.f);
-}
-
-__global__ void k_diff(float2 *out, const float2 *a, const float2 *b, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float2 u = a[i], v = b[i];
-        out[i] = make_float2(u.x - v.x, u.y - v.y);
-    }
-}
-
-__global__ void k_mul(float2 *out, const float2 *in, const float *scale, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float2 v = in[i];
-        float s = scale[i];
-        out[i] = make_float2(v.x * s, v.y * s);
-    }
-}
-
-// ---------------------------------------------------------------- FISTA --
-
-// r = F h - y (in place on r), partial |r|^2 into part slot 0
-__global__ void k_residual(const SolverState *st, float2 *r, const float2 *y, long long n, double *part) {
-    __shared__ double sh[32];
-    SKIP_IF_DONE
-    double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float2 a = r[i], b = y[i];
-        a.x -= b.x;
-        a.y -= b.y;
-        r[i] = a;
-        acc += (double)a.x * a.x + (double)a.y * a.y;
-    }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
-}
-
-// t(xi) = sum_k omega_k |z_k|^2 / (1/xi + omega_k)^2 over a group (block reduction)
-__device__ double group_t(const float2 *h, const float2 *g, float invL, const double *wd, long long o, long long m,
-                          double xi, double *sh, bool use_s) {
-    double acc = 0.0;
-    for (long long i = threadIdx.x; i < m; i += blockDim.x) {
-        float2 hv = h[o + i], gv = g[o + i];
-        double zx = (double)hv.x - (double)gv.x * invL, zy = (double)hv.y - (double)gv.y * invL;
-        double om = wd[o + i];
-        double den = use_s ? (xi + om) : (1.0 / xi + om);
-        acc += om * (zx * zx + zy * zy) / (den * den);
-    }
-    double s = block_sum(acc, sh);
-    __shared__ double bc;
-    if (threadIdx.x == 0) bc = s;
-    __syncthreads();
-    double r = bc;
-    __syncthreads();
-    return r;
-}
-
-// Prox p_L of eq. (projection), one block per group: f_new = prox(h - g / L).
-// Zero when sqrt(sum |z|^2 / omega) <= lam / L (Lemma (iii)); otherwise
-// z / (1 + xi omega) with t(xi) = (lam/L)^2 (Theorem "projection"): for
-// omega = 1 in closed form, else bisection on [0,1] in xi or in s = 1/xi and
-// Newton steps (Remark after the Theorem).  Masked groups are zero.
-__global__ void k_prox(const SolverState *st, float2 *fnew, const float2 *h, const float2 *g, const double *wd,
-                       const long long *goff, const long long *glen, const unsigned char *gmask, int unit_w) {
-    __shared__ double sh[32];
-    __shared__ double s_scale, s_xi;
-    __shared__ int s_mode;
-    if (st->done) return;
-    const int u = blockIdx.x;
-    const long long o = goff[u], m = glen[u];
-    const double L = st->L, thr = st->lam / L;
-    const float invL = (float)(1.0 / L);
-    if (gmask && !gmask[u]) {
-        for (long long i = threadIdx.x; i < m; i += blockDim.x) fnew[o + i] = make_float2(0.f, 0.f);
-        return;
-    }
-    // zero test
-    double acc = 0.0;
-    for (long long i = threadIdx.x; i < m; i += blockDim.x) {
-        float2 hv = h[o + i], gv = g[o + i];
-        double zx = (double)hv.x - (double)gv.x * invL, zy = (double)hv.y - (double)gv.y * invL;
-        acc += (zx * zx + zy * zy) / wd[o + i];
-    }
-    double z2w = block_sum(acc, sh);
-    if (threadIdx.x == 0) {
-        double zn = sqrt(z2w);
-        if (zn <= thr) {
-            s_mode = 0;
-        } else if (unit_w) {
-            s_mode = 1;
-            s_scale = 1.0 - thr / zn;
-        } else {
-            s_mode = 2;
-        }
-    }
-    __syncthreads();
-    if (s_mode == 0) {
-        for (long long i = threadIdx.x; i < m; i += blockDim.x) fnew[o + i] = make_float2(0.f, 0.f);
-        return;
-    }
-    if (s_mode == 1) {
-        const double sc = s_scale;
-        for (long long i = threadIdx.x; i < m; i += blockDim.x) {
-            float2 hv = h[o + i], gv = g[o + i];
-            double zx = (double)hv.x - (double)gv.x * invL, zy = (double)hv.y - (double)gv.y * invL;
-            fnew[o + i] = make_float2((float)(sc * zx), (float)(sc * zy));
-        }
-        return;
-    }
-    // general weights: root of t(xi) = thr^2
-    const double lam2 = thr * thr;
-    const double t1 = group_t(h, g, invL, wd, o, m, 1.0, sh, false);
-    double xi;
-    if (t1 >= lam2) {
-        double lo = 0.0, hi = 1.0;
-        for (int it = 0; it < 40; ++it) {
-            double mid = 0.5 * (lo + hi);
-            double tv = mid > 0 ? group_t(h, g, invL, wd, o, m, mid, sh, false) : 0.0;
-            if (tv < lam2) lo = mid; else hi = mid;
-        }
-        xi = 0.5 * (lo + hi);
-        for (int it = 0; it < 30; ++it) {
-            // d/dxi of omega |z|^2 (1/xi + omega)^-2 = 2 omega |z|^2 (1/xi + omega)^-3 / xi^2
-            double f = group_t(h, g, invL, wd, o, m, xi, sh, false) - lam2;
-            double acc2 = 0.0;
-            for (long long i = threadIdx.x; i < m; i += blockDim.x) {
-                float2 hv = h[o + i], gv = g[o + i];
-                double zx = (double)hv.x - (double)gv.x * invL, zy = (double)hv.y - (double)gv.y * invL;
-                double om = wd[o + i], den = 1.0 / xi + om;
-                acc2 += 2.0 * om * (zx * zx + zy * zy) / (den * den * den);
-            }
-            double fp = block_sum(acc2, sh);
-            if (threadIdx.x == 0) s_xi = fp;
-            __syncthreads();
-            fp = s_xi / (xi * xi);
-            __syncthreads();
-            double nx = fmin(fmax(xi - f / fp, 0.5 * xi), 2.0 * xi);
-            if (fabs(nx - xi) <= 1e-15 * xi) {
-                xi = nx;
-                break;
-            }
-            xi = nx;
-        }
-    } else {
-        double lo = 0.0, hi = 1.0;   // g(s) = t(1/s) decreasing
-        for (int it = 0; it < 40; ++it) {
-            double mid = 0.5 * (lo + hi);
-            double gv = group_t(h, g, invL, wd, o, m, mid, sh, true);
-            if (gv > lam2) lo = mid; else hi = mid;
-        }
-        double s = 0.5 * (lo + hi);
-        for (int it = 0; it < 30; ++it) {
-            double f = group_t(h, g, invL, wd, o, m, s, sh, true) - lam2;
-            double acc2 = 0.0;
-            for (long long i = threadIdx.x; i < m; i += blockDim.x) {
-                float2 hv = h[o + i], gv = g[o + i];
-                double zx = (double)hv.x - (double)gv.x * invL, zy = (double)hv.y - (double)gv.y * invL;
-                double om = wd[o + i], den = s + om;
-                acc2 += -2.0 * om * (zx * zx + zy * zy) / (den * den * den);
-            }
-            double fp = block_sum(acc2, sh);
-            if (threadIdx.x == 0) s_xi = fp;
-            __syncthreads();
-            fp = s_xi;
-            __syncthreads();
-            double ns = s - f / fp;
-            ns = s > 0 ? fmin(fmax(ns, 0.5 * s), 2.0 * s) : fmax(ns, 0.0);
-            if (fabs(ns - s) <= 1e-15 * fmax(s, 1e-300)) {
-                s = ns;
-                break;
-            }
-            s = ns;
-        }
-        xi = s > 0 ? 1.0 / s : INFINITY;
-    }
-    for (long long i = threadIdx.x; i < m; i += blockDim.x) {
-        float2 hv = h[o + i], gv = g[o + i];
-        double zx = (double)hv.x - (double)gv.x * invL, zy = (double)hv.y - (double)gv.y * invL;
-        double sc = isfinite(xi) ? 1.0 / (1.0 + xi * wd[o + i]) : 0.0;
-        fnew[o + i] = make_float2((float)(sc * zx), (float)(sc * zy));
-    }
-}
-
-// momentum: t_next = (1 + sqrt(1 + 4 t^2))/2, h = f_new + (t - 1)/t_next (f_new - f);
-// f_prev <- f, f <- f_new ; partials: |f_new - f|^2 (slot 0), |f_new|^2 (slot 1)
-__global__ void k_momentum(const SolverState *st, float2 *h, float2 *f, float2 *fp, const float2 *fnew, long long n,
-                           double *part) {
-    __shared__ double sh[32];
-    SKIP_IF_DONE
-    const double t = st->t, tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-    const float beta = (float)((t - 1.0) / tn);
-    double a0 = 0.0, a1 = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float2 fo = f[i], fnv = fnew[i];
-        float dx = fnv.x - fo.x, dy = fnv.y - fo.y;
-        h[i] = make_float2(fnv.x + beta * dx, fnv.y + beta * dy);
-        fp[i] = fo;
-        f[i] = fnv;
-        a0 += (double)dx * dx + (double)dy * dy;
-        a1 += (double)fnv.x * fnv.x + (double)fnv.y * fnv.y;
-    }
-    double s0 = block_sum(a0, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s0;
-    double s1 = block_sum(a1, sh);
-    if (threadIdx.x == 0) part[RED_BLOCKS + blockIdx.x] = s1;
-}
 
 __global__ void k_fista_step(SolverState *st) {
     if (st->done) return;
@@ -392,77 +87,6 @@ __global__ void k_fista_step(SolverState *st) {
     }
 }
 
-// backtracking quantities: slot 0 |F f - y|^2 is finished separately; here
-// cross = Re<f - h, g> (slot 2) and |f - h|^2 (slot 3)
-__global__ void k_bt_terms(const SolverState *st, const float2 *fnew, const float2 *h, const float2 *g, long long n,
-                           double *part) {
-    __shared__ double sh[32];
-    double a2 = 0.0, a3 = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float2 a = fnew[i], b = h[i], c = g[i];
-        double dx = (double)a.x - b.x, dy = (double)a.y - b.y;
-        a2 += dx * c.x + dy * c.y;
-        a3 += dx * dx + dy * dy;
-    }
-    double s2 = block_sum(a2, sh);
-    if (threadIdx.x == 0) part[2 * RED_BLOCKS + blockIdx.x] = s2;
-    double s3 = block_sum(a3, sh);
-    if (threadIdx.x == 0) part[3 * RED_BLOCKS + blockIdx.x] = s3;
-}
-
-// per-group norms: out[u] = sqrt(sum_k weight_k |v_k|^2) with weight omega (mode 0),
-// 1/omega (mode 1) or 1 (mode 2)
-__global__ void k_group_norms(const float2 *v, const double *wd, const long long *goff, const long long *glen,
-                              double *out, int mode) {
-    __shared__ double sh[32];
-    const int u = blockIdx.x;
-    const long long o = goff[u], m = glen[u];
-    double acc = 0.0;
-    for (long long i = threadIdx.x; i < m; i += blockDim.x) {
-        float2 a = v[o + i];
-        double q = (double)a.x * a.x + (double)a.y * a.y;
-        double om = wd ? wd[o + i] : 1.0;
-        acc += mode == 0 ? q * om : (mode == 1 ? q / om : q);
-    }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) out[u] = sqrt(s);
-}
-
-// KKT residual per group, given q = F^H (F f - y) = -F^H r with r = y - F f:
-// inactive (f_u = 0) groups (Lemma (iii)): (||W^{-1/2} q_u|| - lam) / lam;
-// active groups (stationarity in the proof of Lemma (ii)):
-// ||r-part - lam W f_u / ||f_u||_W|| / lam = ||-q_u - lam W f_u / ||f_u||_W|| / lam
-__global__ void k_kkt(const float2 *g, const float2 *f, const double *wd, const long long *goff, const long long *glen,
-                      double lam, double *viol) {
-    __shared__ double sh[32];
-    __shared__ double s_fn;
-    const int u = blockIdx.x;
-    const long long o = goff[u], m = glen[u];
-    double acc = 0.0;
-    for (long long i = threadIdx.x; i < m; i += blockDim.x) {
-        float2 a = f[o + i];
-        acc += ((double)a.x * a.x + (double)a.y * a.y) * wd[o + i];
-    }
-    double fn = block_sum(acc, sh);
-    if (threadIdx.x == 0) s_fn = sqrt(fn);
-    __syncthreads();
-    fn = s_fn;
-    __syncthreads();
-    double acc2 = 0.0;
-    for (long long i = threadIdx.x; i < m; i += blockDim.x) {
-        float2 gv = g[o + i], fv = f[o + i];
-        double om = wd[o + i];
-        if (fn == 0.0) {
-            acc2 += ((double)gv.x * gv.x + (double)gv.y * gv.y) / om;
-        } else {
-            double rx = -gv.x - lam * om * fv.x / fn, ry = -gv.y - lam * om * fv.y / fn;
-            acc2 += rx * rx + ry * ry;
-        }
-    }
-    double s = block_sum(acc2, sh);
-    if (threadIdx.x == 0) viol[u] = fn == 0.0 ? (sqrt(s) - lam) / lam : sqrt(s) / lam;
-}
-
 // ---------------------------------------------------------------- host ----
 
 static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>(RED_BLOCKS, (n + 255) / 256)); }
@@ -474,7 +98,9 @@ SolverWork *get_work(Plan &p, int &rc) {
     W = new SolverWork();
     W->M = p.M;
     W->n = p.n_coeffs;
-    const size_t bm = sizeof(float2) * std::max<long long>(1, p.M), bn = sizeof(float2) * std::max<long long>(1, p.n_coeffs);
+    const size_t es = p.precision == ANOVA_PREC_F64 ? sizeof(double2) : sizeof(float2);   // complex element
+    const size_t rs = es / 2;                                                                  // real element
+    const size_t bm = es * std::max<long long>(1, p.M), bn = es * std::max<long long>(1, p.n_coeffs);
     cudaError_t e = cudaSuccess;
     auto A = [&](void **ptr, size_t b) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, b);
@@ -490,7 +116,7 @@ SolverWork *get_work(Plan &p, int &rc) {
     A((void **)&W->f, bn);
     A((void **)&W->fp, bn);
     A((void **)&W->g, bn);
-    A((void **)&W->ws, sizeof(float) * std::max<long long>(1, p.n_coeffs));
+    A((void **)&W->ws, rs * std::max<long long>(1, p.n_coeffs));
     A((void **)&W->wd, sizeof(double) * std::max<long long>(1, p.n_coeffs));
     A((void **)&W->part, sizeof(double) * 8 * RED_BLOCKS);
     A((void **)&W->gnorm, sizeof(double) * std::max(1, p.n_user_terms));
@@ -566,12 +192,32 @@ static int run_loop(Plan &p, SolverWork *W, int max_it, F &&step) {
     return ANOVA_OK;
 }
 
-static int lsqr_impl(Plan &p, const float2 *y, const double *w, double lambda, int max_it, double atol, double btol,
-                     float2 *fhat, anova_solve_info *info) {
+// The plan's complex vectors of a solver workspace, typed.
+template <typename C>
+struct Vecs {
+    C *uM, *tM, *rM, *v, *w, *x, *tn, *h, *f, *fp, *g;
+    typename CT<C>::R *ws;
+    explicit Vecs(const SolverWork *W)
+        : uM((C *)W->uM), tM((C *)W->tM), rM((C *)W->rM), v((C *)W->v), w((C *)W->w), x((C *)W->x),
+          tn((C *)W->tn), h((C *)W->h), f((C *)W->f), fp((C *)W->fp), g((C *)W->g),
+          ws((typename CT<C>::R *)W->ws) {}
+};
+
+// the transforms by vector type
+static int trafo_c(Plan &p, const float2 *fhat, float2 *f) { return launch_trafo_f32(p, fhat, f); }
+static int trafo_c(Plan &p, const double2 *fhat, double2 *f) { return launch_trafo_f64(p, fhat, f); }
+static int adjoint_c(Plan &p, const float2 *y, float2 *fhat) { return launch_adjoint_f32(p, y, fhat); }
+static int adjoint_c(Plan &p, const double2 *y, double2 *fhat) { return launch_adjoint_f64(p, y, fhat); }
+
+template <typename C>
+static int lsqr_impl(Plan &p, const C *y, const double *w, double lambda, int max_it, double atol, double btol,
+                     C *fhat, anova_solve_info *info) {
     int rc;
     SolverWork *W = get_work(p, rc);
     if (!W) return rc;
     StreamScope scope(p, W);
+    using R = typename CT<C>::R;
+    const Vecs<C> V(W);
     const long long M = p.M, n = p.n_coeffs;
     const int gM = grid_for(M), gn = grid_for(n);
     cudaStream_t s = p.stream;
@@ -583,44 +229,44 @@ static int lsqr_impl(Plan &p, const float2 *y, const double *w, double lambda, i
     h0.btol = btol;
     h0.max_it = max_it;
     cudaMemcpyAsync(W->st, &h0, sizeof(h0), cudaMemcpyHostToDevice, s);
-    k_weights<<<gn, 256, 0, s>>>(w, W->ws, W->wd, n, 0);
-    const float *ws = w ? W->ws : nullptr;
+    k_weights<<<gn, 256, 0, s>>>(w, V.ws, W->wd, n, 0);
+    const R *ws = w ? V.ws : nullptr;
     int n_tr = 0, n_adj = 0;
     cudaEventRecord(W->e0, s);
     // beta u = y
-    k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->uM, y, nullptr, M, W->part);
+    k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.uM, y, nullptr, M, W->part);
     finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
     k_set_norm<<<1, 1, 0, s>>>(W->st, 1);
-    k_normalize<<<gM, 256, 0, s>>>(W->st, W->uM, M, 1);
+    k_normalize<<<gM, 256, 0, s>>>(W->st, V.uM, M, 1);
     // alpha v = A^H u
-    rc = launch_adjoint_f32(p, (const float2 *)W->uM, W->tn);
+    rc = adjoint_c(p, (const C *)V.uM, V.tn);
     ++n_adj;
     if (rc) return rc;
-    k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->v, W->tn, ws, n, W->part);
+    k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.v, V.tn, ws, n, W->part);
     finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
     k_set_norm<<<1, 1, 0, s>>>(W->st, 0);
-    k_normalize<<<gn, 256, 0, s>>>(W->st, W->v, n, 0);
-    cudaMemcpyAsync(W->w, W->v, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s);
-    k_zero<<<gn, 256, 0, s>>>(W->x, n);
+    k_normalize<<<gn, 256, 0, s>>>(W->st, V.v, n, 0);
+    cudaMemcpyAsync(V.w, V.v, sizeof(C) * n, cudaMemcpyDeviceToDevice, s);
+    k_zero<<<gn, 256, 0, s>>>(V.x, n);
     k_lsqr_init<<<1, 1, 0, s>>>(W->st);
     p.skip = &W->st->done;
     auto step = [&]() -> int {
         // u = A v - alpha u ; beta = |u| ; u /= beta
-        k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->tn, W->v, ws, n, nullptr);
-        int r = launch_trafo_f32(p, (const float2 *)W->tn, W->tM);
+        k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.tn, V.v, ws, n, nullptr);
+        int r = trafo_c(p, (const C *)V.tn, V.tM);
         if (r) return r;
-        k_sub_scaled<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->uM, W->tM, nullptr, 0, M, W->part);
+        k_sub_scaled<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.uM, V.tM, nullptr, 0, M, W->part);
         finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
         k_set_norm<<<1, 1, 0, s>>>(W->st, 1);
-        k_normalize<<<gM, 256, 0, s>>>(W->st, W->uM, M, 1);
+        k_normalize<<<gM, 256, 0, s>>>(W->st, V.uM, M, 1);
         // v = A^H u - beta v ; alpha = |v| (in the scalar kernel) ; v /= alpha
-        r = launch_adjoint_f32(p, (const float2 *)W->uM, W->tn);
+        r = adjoint_c(p, (const C *)V.uM, V.tn);
         if (r) return r;
-        k_sub_scaled<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->v, W->tn, ws, 1, n, W->part);
+        k_sub_scaled<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.v, V.tn, ws, 1, n, W->part);
         finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
         k_lsqr_scalars<<<1, 1, 0, s>>>(W->st);
-        k_normalize<<<gn, 256, 0, s>>>(W->st, W->v, n, 0);
-        k_lsqr_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->x, W->w, W->v, n, W->part);
+        k_normalize<<<gn, 256, 0, s>>>(W->st, V.v, n, 0);
+        k_lsqr_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.x, V.w, V.v, n, W->part);
         finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
         k_lsqr_test<<<1, 1, 0, s>>>(W->st);
         return cuda_status(cudaGetLastError());
@@ -630,9 +276,9 @@ static int lsqr_impl(Plan &p, const float2 *y, const double *w, double lambda, i
     if (rc) return rc;
     // fhat = W^{-1/2} x
     if (ws)
-        k_mul<<<gn, 256, 0, s>>>(fhat, W->x, W->ws, n);
+        k_mul<<<gn, 256, 0, s>>>(fhat, V.x, V.ws, n);
     else
-        cudaMemcpyAsync(fhat, W->x, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(fhat, V.x, sizeof(C) * n, cudaMemcpyDeviceToDevice, s);
     cudaEventRecord(W->e1, s);
     SolverState h;
     cudaError_t e = cudaMemcpyAsync(&h, W->st, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -657,29 +303,34 @@ static int lsqr_impl(Plan &p, const float2 *y, const double *w, double lambda, i
 }
 
 // power iteration for ||F||^2 on the active terms (30 steps, FP64 Rayleigh quotient)
+template <typename C>
 static int power_estimate(Plan &p, SolverWork *W, int iters, bool masked, double *out) {
+    const Vecs<C> V(W);
     cudaStream_t s = p.stream;
     const long long n = p.n_coeffs;
     const int gn = grid_for(n);
-    std::vector<float2> ones(n, make_float2(1.f, 0.f));
-    cudaMemcpyAsync(W->v, ones.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s);
-    if (masked) k_mask_groups<<<p.n_user_terms, 256, 0, s>>>(W->v, W->goff, W->glen, W->gmask);
+    C one;
+    one.x = 1;
+    one.y = 0;
+    std::vector<C> ones(n, one);
+    cudaMemcpyAsync(V.v, ones.data(), sizeof(C) * n, cudaMemcpyHostToDevice, s);
+    if (masked) k_mask_groups<<<p.n_user_terms, 256, 0, s>>>(V.v, W->goff, W->glen, W->gmask);
     SolverState h0;
     std::memset(&h0, 0, sizeof(h0));
     cudaMemcpyAsync(W->st, &h0, sizeof(h0), cudaMemcpyHostToDevice, s);
-    k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->v, W->v, nullptr, n, W->part);
+    k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.v, V.v, nullptr, n, W->part);
     finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
     k_set_norm<<<1, 1, 0, s>>>(W->st, 0);
-    k_normalize<<<gn, 256, 0, s>>>(W->st, W->v, n, 0);
+    k_normalize<<<gn, 256, 0, s>>>(W->st, V.v, n, 0);
     double lam = 0.0, prev = -1.0;
     for (int it = 0; it < iters; ++it) {
-        int rc = launch_trafo_f32(p, (const float2 *)W->v, W->tM);
+        int rc = trafo_c(p, (const C *)V.v, V.tM);
         if (rc) return rc;
-        rc = launch_adjoint_f32(p, (const float2 *)W->tM, W->tn);
+        rc = adjoint_c(p, (const C *)V.tM, V.tn);
         if (rc) return rc;
-        if (masked) k_mask_groups<<<p.n_user_terms, 256, 0, s>>>(W->tn, W->goff, W->glen, W->gmask);
+        if (masked) k_mask_groups<<<p.n_user_terms, 256, 0, s>>>(V.tn, W->goff, W->glen, W->gmask);
         // ||F v||^2 = <v, F^H F v> with |v| = 1
-        k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->tM, W->tM, nullptr, p.M, W->part);
+        k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.tM, V.tM, nullptr, p.M, W->part);
         finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
         SolverState h;
         cudaMemcpyAsync(&h, W->st, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -688,26 +339,29 @@ static int power_estimate(Plan &p, SolverWork *W, int iters, bool masked, double
         lam = h.red[0];
         if (prev > 0 && std::fabs(lam - prev) <= 1e-5 * lam) break;
         prev = lam;
-        k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->v, W->tn, nullptr, n, W->part);
+        k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.v, V.tn, nullptr, n, W->part);
         finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
         k_set_norm<<<1, 1, 0, s>>>(W->st, 0);
-        k_normalize<<<gn, 256, 0, s>>>(W->st, W->v, n, 0);
+        k_normalize<<<gn, 256, 0, s>>>(W->st, V.v, n, 0);
     }
     *out = lam;
     return cuda_status(cudaGetLastError());
 }
 
-int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas, int n_lambda, int max_it,
-               double tol, int step_mode, double L0, double eta, const uint8_t *mask, const float2 *f0,
-               float2 *path, anova_solve_info *info, double *L_out) {
+template <typename C>
+int fista_impl_t(Plan &p, const C *y, const double *w, const double *lambdas, int n_lambda, int max_it,
+               double tol, int step_mode, double L0, double eta, const uint8_t *mask, const C *f0,
+               C *path, anova_solve_info *info, double *L_out) {
     int rc;
     SolverWork *W = get_work(p, rc);
     if (!W) return rc;
     StreamScope scope(p, W);
+    using R = typename CT<C>::R;
+    const Vecs<C> V(W);
     const long long M = p.M, n = p.n_coeffs;
     const int gM = grid_for(M), gn = grid_for(n), G = p.n_user_terms;
     cudaStream_t s = p.stream;
-    k_weights<<<gn, 256, 0, s>>>(w, W->ws, W->wd, n, 1);
+    k_weights<<<gn, 256, 0, s>>>(w, V.ws, W->wd, n, 1);
     std::vector<unsigned char> hm(G, 1);
     if (mask)
         for (int u = 0; u < G; ++u) hm[u] = mask[u] ? 1 : 0;
@@ -717,7 +371,7 @@ int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas,
     double L = L0;
     if (L <= 0) {
         double est = 0.0;
-        rc = power_estimate(p, W, 300, mask != nullptr, &est);
+        rc = power_estimate<C>(p, W, 300, mask != nullptr, &est);
         if (rc) return rc;
         L = 1.05 * est;
         if (!(L > 0)) L = 1.0;
@@ -726,10 +380,10 @@ int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas,
     for (int i = 0; i < n_lambda; ++i) ord[i] = i;
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return lambdas[a] > lambdas[b]; });
     if (f0) {
-        cudaMemcpyAsync(W->f, f0, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s);
-        if (mask) k_mask_groups<<<G, 256, 0, s>>>(W->f, W->goff, W->glen, W->gmask);
+        cudaMemcpyAsync(V.f, f0, sizeof(C) * n, cudaMemcpyDeviceToDevice, s);
+        if (mask) k_mask_groups<<<G, 256, 0, s>>>(V.f, W->goff, W->glen, W->gmask);
     } else {
-        k_zero<<<gn, 256, 0, s>>>(W->f, n);
+        k_zero<<<gn, 256, 0, s>>>(V.f, n);
     }
     for (int li = 0; li < n_lambda; ++li) {
         const int idx = ord[li];
@@ -742,20 +396,20 @@ int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas,
         h0.max_it = max_it;
         h0.eta = eta;
         cudaMemcpyAsync(W->st, &h0, sizeof(h0), cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(W->h, W->f, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(V.h, V.f, sizeof(C) * n, cudaMemcpyDeviceToDevice, s);
         cudaEventRecord(W->e0, s);
         int n_tr = 0, n_adj = 0;
         if (step_mode == 0) {
             p.skip = &W->st->done;
             auto step = [&]() -> int {
-                int r = launch_trafo_f32(p, (const float2 *)W->h, W->rM);
+                int r = trafo_c(p, (const C *)V.h, V.rM);
                 if (r) return r;
-                k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->rM, y, M, nullptr);
-                r = launch_adjoint_f32(p, (const float2 *)W->rM, W->g);
+                k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.rM, y, M, nullptr);
+                r = adjoint_c(p, (const C *)V.rM, V.g);
                 if (r) return r;
-                if (mask) k_mask_groups<<<G, 256, 0, s>>>(W->g, W->goff, W->glen, W->gmask);
-                k_prox<<<G, 256, 0, s>>>(W->st, W->x, W->h, W->g, W->wd, W->goff, W->glen, W->gmask, w ? 0 : 1);
-                k_momentum<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->h, W->f, W->fp, W->x, n, W->part);
+                if (mask) k_mask_groups<<<G, 256, 0, s>>>(V.g, W->goff, W->glen, W->gmask);
+                k_prox<<<G, 256, 0, s>>>(W->st, V.x, V.h, V.g, W->wd, W->goff, W->glen, W->gmask, w ? 0 : 1);
+                k_momentum<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.h, V.f, V.fp, V.x, n, W->part);
                 finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 2);
                 k_fista_step<<<1, 1, 0, s>>>(W->st);
                 return cuda_status(cudaGetLastError());
@@ -767,26 +421,26 @@ int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas,
             // backtracking: host checks the sufficient-decrease condition per trial
             SolverState hs;
             for (int it = 0; it < max_it; ++it) {
-                rc = launch_trafo_f32(p, (const float2 *)W->h, W->rM);
+                rc = trafo_c(p, (const C *)V.h, V.rM);
                 ++n_tr;
                 if (rc) return rc;
-                k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->rM, y, M, nullptr);
-                rc = launch_adjoint_f32(p, (const float2 *)W->rM, W->g);
+                k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.rM, y, M, nullptr);
+                rc = adjoint_c(p, (const C *)V.rM, V.g);
                 ++n_adj;
                 if (rc) return rc;
-                if (mask) k_mask_groups<<<G, 256, 0, s>>>(W->g, W->goff, W->glen, W->gmask);
+                if (mask) k_mask_groups<<<G, 256, 0, s>>>(V.g, W->goff, W->glen, W->gmask);
                 for (int trial = 0; trial < 64; ++trial) {
                     // For the quadratic data term the Algorithm's test
                     //   ||y - F f||^2 - ||y - F h||^2 <= 2 Re<f - h, F^H (F h - y)> + L ||f - h||^2
                     // is exactly ||F d||^2 <= L ||d||^2 with d = f - h; that form has no
                     // cancellation of two nearly equal residual norms.
-                    k_prox<<<G, 256, 0, s>>>(W->st, W->x, W->h, W->g, W->wd, W->goff, W->glen, W->gmask, w ? 0 : 1);
-                    k_diff<<<gn, 256, 0, s>>>(W->tn, W->x, W->h, n);
-                    rc = launch_trafo_f32(p, (const float2 *)W->tn, W->tM);
+                    k_prox<<<G, 256, 0, s>>>(W->st, V.x, V.h, V.g, W->wd, W->goff, W->glen, W->gmask, w ? 0 : 1);
+                    k_diff<<<gn, 256, 0, s>>>(V.tn, V.x, V.h, n);
+                    rc = trafo_c(p, (const C *)V.tn, V.tM);
                     ++n_tr;
                     if (rc) return rc;
-                    k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->tM, W->tM, nullptr, M, W->part);
-                    k_bt_terms<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->x, W->h, W->g, n, W->part);
+                    k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.tM, V.tM, nullptr, M, W->part);
+                    k_bt_terms<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.x, V.h, V.g, n, W->part);
                     finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 4);
                     cudaMemcpyAsync(&hs, W->st, sizeof(hs), cudaMemcpyDeviceToHost, s);
                     cudaError_t e = cudaStreamSynchronize(s);
@@ -795,7 +449,7 @@ int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas,
                     hs.L *= eta;
                     cudaMemcpyAsync(&W->st->L, &hs.L, sizeof(double), cudaMemcpyHostToDevice, s);
                 }
-                k_momentum<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->h, W->f, W->fp, W->x, n, W->part);
+                k_momentum<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.h, V.f, V.fp, V.x, n, W->part);
                 finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 2);
                 k_fista_step<<<1, 1, 0, s>>>(W->st);
                 cudaMemcpyAsync(&hs, W->st, sizeof(hs), cudaMemcpyDeviceToHost, s);
@@ -805,7 +459,7 @@ int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas,
             }
         }
         // store the solution and the objective 1/2 ||y - F f||^2 + lam sum_u ||f_u||_W
-        cudaMemcpyAsync(path + (long long)idx * n, W->f, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(path + (long long)idx * n, V.f, sizeof(C) * n, cudaMemcpyDeviceToDevice, s);
         SolverState hf;
         cudaMemcpyAsync(&hf, W->st, sizeof(hf), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
@@ -816,11 +470,11 @@ int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas,
             SolverState z;
             std::memset(&z, 0, sizeof(z));
             cudaMemcpyAsync(W->st, &z, sizeof(z), cudaMemcpyHostToDevice, s);
-            rc = launch_trafo_f32(p, (const float2 *)W->f, W->tM);
+            rc = trafo_c(p, (const C *)V.f, V.tM);
             if (rc) return rc;
-            k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->tM, y, M, W->part);
+            k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.tM, y, M, W->part);
             finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
-            k_group_norms<<<G, 256, 0, s>>>(W->f, W->wd, W->goff, W->glen, W->gnorm, 0);
+            k_group_norms<<<G, 256, 0, s>>>(V.f, W->wd, W->goff, W->glen, W->gnorm, 0);
             cudaEventRecord(W->e1, s);
             std::vector<double> gn_h(G);
             SolverState hz;
@@ -856,6 +510,55 @@ int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas,
     return set_active_terms(p, nullptr);
 }
 
+int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas, int n_lambda, int max_it,
+               double tol, int step_mode, double L0, double eta, const uint8_t *mask, const float2 *f0,
+               float2 *path, anova_solve_info *info, double *L_out) {
+    return fista_impl_t<float2>(p, y, w, lambdas, n_lambda, max_it, tol, step_mode, L0, eta, mask, f0, path, info,
+                                L_out);
+}
+
+}  // namespace agft
+
+namespace agft {
+
+// KKT residuals of a group-lasso solution (see k_kkt) into viol_out (host).
+template <typename C>
+static int kkt_impl(Plan &p, const C *y, const double *w_dev, const C *fhat, double lambda, double rtol,
+                    double *viol_out, int *n_viol) {
+    int rc;
+    SolverWork *W = get_work(p, rc);
+    if (!W) return rc;
+    StreamScope scope(p, W);
+    const Vecs<C> V(W);
+    cudaStream_t s = p.stream;
+    const long long n = p.n_coeffs, M = p.M;
+    const int G = p.n_user_terms;
+    k_weights<<<grid_for(n), 256, 0, s>>>(w_dev, V.ws, W->wd, n, 1);
+    SolverState z;
+    std::memset(&z, 0, sizeof(z));
+    cudaMemcpyAsync(W->st, &z, sizeof(z), cudaMemcpyHostToDevice, s);
+    rc = set_active_terms(p, nullptr);
+    if (rc) return rc;
+    rc = trafo_c(p, fhat, V.tM);
+    if (rc) return rc;
+    // F f - y, then q = F^H (F f - y)
+    k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.tM, y, M, nullptr);
+    rc = adjoint_c(p, (const C *)V.tM, V.g);
+    if (rc) return rc;
+    k_kkt<<<G, 256, 0, s>>>(V.g, fhat, W->wd, W->goff, W->glen, lambda, W->gnorm);
+    std::vector<double> v(G);
+    cudaMemcpyAsync(v.data(), W->gnorm, sizeof(double) * G, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    int cnt = 0;
+    for (int u = 0; u < G; ++u) {
+        if (viol_out) viol_out[u] = v[u];
+        cnt += v[u] > rtol;
+    }
+    if (n_viol) *n_viol = cnt;
+    return ANOVA_OK;
+}
+
 }  // namespace agft
 
 using namespace agft;
@@ -868,13 +571,16 @@ int lsqr_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, double
     cudaGetLastError();   // do not report an earlier, unrelated error
     Plan &p = plan->p;
     if (p.M > 0 && !y_dev) return ANOVA_ERR_INVALID;
-    if (p.precision != ANOVA_PREC_F32) return ANOVA_ERR_UNSUPPORTED;
+    const bool f64 = p.precision == ANOVA_PREC_F64;
     if (p.M == 0) {
-        cudaMemsetAsync(fhat_dev, 0, sizeof(float2) * p.n_coeffs, p.stream);
+        cudaMemsetAsync(fhat_dev, 0, (f64 ? sizeof(double2) : sizeof(float2)) * p.n_coeffs, p.stream);
         if (info) std::memset(info, 0, sizeof(*info));
         return cuda_status(cudaStreamSynchronize(p.stream));
     }
-    return lsqr_impl(p, (const float2 *)y_dev, w_dev, lambda, max_it, atol, btol, (float2 *)fhat_dev, info);
+    if (f64)
+        return lsqr_impl<double2>(p, (const double2 *)y_dev, w_dev, lambda, max_it, atol, btol, (double2 *)fhat_dev,
+                                  info);
+    return lsqr_impl<float2>(p, (const float2 *)y_dev, w_dev, lambda, max_it, atol, btol, (float2 *)fhat_dev, info);
 }
 
 int fista_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, const double *lambdas, int n_lambda,
@@ -888,11 +594,14 @@ int fista_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, const
         if (!(lambdas[i] >= 0)) return ANOVA_ERR_INVALID;
     Plan &p = plan->p;
     if (p.M > 0 && !y_dev) return ANOVA_ERR_INVALID;
-    if (p.precision != ANOVA_PREC_F32) return ANOVA_ERR_UNSUPPORTED;
     if (p.M == 0) return ANOVA_ERR_INVALID;
-    return fista_impl(p, (const float2 *)y_dev, w_dev, lambdas, n_lambda, max_it, tol, step_mode, L0, eta,
-                      group_mask, warm_start ? (const float2 *)fhat_path_dev : nullptr, (float2 *)fhat_path_dev,
-                      info, nullptr);
+    if (p.precision == ANOVA_PREC_F64)
+        return fista_impl_t<double2>(p, (const double2 *)y_dev, w_dev, lambdas, n_lambda, max_it, tol, step_mode, L0,
+                                     eta, group_mask, warm_start ? (const double2 *)fhat_path_dev : nullptr,
+                                     (double2 *)fhat_path_dev, info, nullptr);
+    return fista_impl_t<float2>(p, (const float2 *)y_dev, w_dev, lambdas, n_lambda, max_it, tol, step_mode, L0, eta,
+                                group_mask, warm_start ? (const float2 *)fhat_path_dev : nullptr,
+                                (float2 *)fhat_path_dev, info, nullptr);
 }
 
 // KKT check of a group-lasso solution: viol_out[u] for every user term (host
@@ -900,40 +609,13 @@ int fista_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, const
 int anova_kkt_check(anova_plan_t plan, const void *y_dev, const double *w_dev, const void *fhat_dev, double lambda,
                     double rtol, double *viol_out, int *n_viol) {
     if (!plan || !fhat_dev || !(lambda > 0)) return ANOVA_ERR_INVALID;
+    cudaGetLastError();
     Plan &p = plan->p;
     if (p.M > 0 && !y_dev) return ANOVA_ERR_INVALID;
-    if (p.precision != ANOVA_PREC_F32) return ANOVA_ERR_UNSUPPORTED;
-    int rc;
-    SolverWork *W = get_work(p, rc);
-    if (!W) return rc;
-    StreamScope scope(p, W);
-    cudaStream_t s = p.stream;
-    const long long n = p.n_coeffs, M = p.M;
-    const int G = p.n_user_terms;
-    k_weights<<<grid_for(n), 256, 0, s>>>(w_dev, W->ws, W->wd, n, 1);
-    SolverState z;
-    std::memset(&z, 0, sizeof(z));
-    cudaMemcpyAsync(W->st, &z, sizeof(z), cudaMemcpyHostToDevice, s);
-    rc = set_active_terms(p, nullptr);
-    if (rc) return rc;
-    rc = launch_trafo_f32(p, (const float2 *)fhat_dev, W->tM);
-    if (rc) return rc;
-    // F f - y, then q = F^H (F f - y)
-    k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, W->tM, (const float2 *)y_dev, M, nullptr);
-    rc = launch_adjoint_f32(p, (const float2 *)W->tM, W->g);
-    if (rc) return rc;
-    k_kkt<<<G, 256, 0, s>>>(W->g, (const float2 *)fhat_dev, W->wd, W->goff, W->glen, lambda, W->gnorm);
-    std::vector<double> v(G);
-    cudaMemcpyAsync(v.data(), W->gnorm, sizeof(double) * G, cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(e);
-    int cnt = 0;
-    for (int u = 0; u < G; ++u) {
-        if (viol_out) viol_out[u] = v[u];
-        cnt += v[u] > rtol;
-    }
-    if (n_viol) *n_viol = cnt;
-    return ANOVA_OK;
+    if (p.precision == ANOVA_PREC_F64)
+        return kkt_impl<double2>(p, (const double2 *)y_dev, w_dev, (const double2 *)fhat_dev, lambda, rtol, viol_out,
+                                 n_viol);
+    return kkt_impl<float2>(p, (const float2 *)y_dev, w_dev, (const float2 *)fhat_dev, lambda, rtol, viol_out, n_viol);
 }
 
 }  // extern "C"

@@ -23,10 +23,11 @@ struct SolverState {
 
 struct SolverWork {
     long long M = 0, n = 0;
-    float2 *uM = nullptr, *tM = nullptr, *rM = nullptr;                          // node-sized
-    float2 *v = nullptr, *w = nullptr, *x = nullptr, *tn = nullptr, *h = nullptr;  // coefficient-sized
-    float2 *f = nullptr, *fp = nullptr, *g = nullptr;
-    float *ws = nullptr;          // omega^{-1/2} (LSQR) or omega (FISTA) per coefficient
+    // complex vectors in the plan's precision (float2 or double2 elements)
+    void *uM = nullptr, *tM = nullptr, *rM = nullptr;                          // node-sized
+    void *v = nullptr, *w = nullptr, *x = nullptr, *tn = nullptr, *h = nullptr;  // coefficient-sized
+    void *f = nullptr, *fp = nullptr, *g = nullptr;
+    void *ws = nullptr;           // omega^{-1/2} (LSQR) or omega (FISTA) per coefficient, real type of the plan
     double *wd = nullptr;         // omega per coefficient (FP64)
     double *part = nullptr;       // [8][RED_BLOCKS] partial sums
     double *gnorm = nullptr;      // per-group values
@@ -147,9 +148,5 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 SolverWork *get_work(Plan &p, int &rc);
 
 __global__ void finish_sums(SolverState *st, const double *part, int nslots);
-__global__ void k_residual(const SolverState *st, float2 *r, const float2 *y, long long n, double *part);
-__global__ void k_mask_groups(float2 *v, const long long *goff, const long long *glen, const unsigned char *gmask);
-__global__ void k_weights(const double *w, float *ws, double *wd, long long n, int mode);
-__global__ void k_zero(float2 *v, long long n);
 
 }  // namespace agft
