@@ -13,6 +13,12 @@ every timed step, outside the step's events.
 ``--impl reference`` times the FP64 oracle (direct summation on the host
 cores) on a bounded node sample of the same workload and scales to M = 1e6.
 
+``--precision f64`` measures the same pairs on an FP64 plan (the plain FP64
+path).  ``--mode lambda-path`` runs the group-lasso lambda path of the d = 30
+workload three ways -- FP32 with the learned group screen, FP32 on all groups,
+FP64 on all groups -- and prints one JSON line with their times, iteration
+counts and the agreement of the screened FP32 path with the FP64 path.
+
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
 torch.distributed.run, every rank runs an independent replica (the transform
 pair needs no exchange between problems), ``value`` sums over ranks.
@@ -48,6 +54,12 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=20000, help="nodes in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--mode", default="pairs", choices=["pairs", "lambda-path"])
+    ap.add_argument("--lambdas", type=int, default=20, help="lambda-path mode: first K values of the path")
+    ap.add_argument("--max-it", type=int, default=5000, help="lambda-path mode: FISTA iterations per lambda")
+    ap.add_argument("--tol", type=float, default=1e-8, help="lambda-path mode: FISTA relative-change stop")
+    ap.add_argument("--skip-f64", action="store_true", help="lambda-path mode: leave out the FP64 path")
     return ap.parse_args()
 
 
@@ -174,15 +186,19 @@ def run_mine(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     w = inputs.c2_scale(M=args.M)
-    x32 = torch.from_numpy(w["x"].astype(np.float32)).to(dev)
-    P = gft.Plan(x32, w["terms"], w["bandwidths"])
+    f64 = args.precision == "f64"
+    rdt, cdt = (np.float64, np.complex128) if f64 else (np.float32, np.complex64)
+    tcdt = torch.complex128 if f64 else torch.complex64
+    esz = 16 if f64 else 8
+    xd = torch.from_numpy(w["x"].astype(rdt)).to(dev)
+    P = gft.Plan(xd, w["terms"], w["bandwidths"], precision=gft.PREC_F64 if f64 else gft.PREC_F32)
     n = P.n_coeffs
-    fhat_h = torch.from_numpy(w["fhat"].astype(np.complex64)).pin_memory()
-    y_h = torch.from_numpy(w["y"].astype(np.complex64)).pin_memory()
+    fhat_h = torch.from_numpy(w["fhat"].astype(cdt)).pin_memory()
+    y_h = torch.from_numpy(w["y"].astype(cdt)).pin_memory()
     fhat = fhat_h.to(dev)
     y = y_h.to(dev)
-    f = torch.empty(args.M, dtype=torch.complex64, device=dev)
-    g = torch.empty(n, dtype=torch.complex64, device=dev)
+    f = torch.empty(args.M, dtype=tcdt, device=dev)
+    g = torch.empty(n, dtype=tcdt, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def pair():
@@ -224,8 +240,8 @@ def run_mine(args, rank, world, local_rank):
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        f_h = torch.empty(args.M, dtype=torch.complex64).pin_memory()
-        g_h = torch.empty(n, dtype=torch.complex64).pin_memory()
+        f_h = torch.empty(args.M, dtype=tcdt).pin_memory()
+        g_h = torch.empty(n, dtype=tcdt).pin_memory()
         ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for k in range(args.steps + 1):
             if k > 0:
@@ -244,7 +260,7 @@ def run_mine(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
         e2e = {"value": args.steps * world / float(te.item()), "unit": UNIT,
-               "h2d_bytes_per_step": 8 * (n + args.M), "d2h_bytes_per_step": 8 * (n + args.M)}
+               "h2d_bytes_per_step": esz * (n + args.M), "d2h_bytes_per_step": esz * (n + args.M)}
 
     # roofline of the dominant kernel (algorithmic bytes per launch / live event time)
     peaks, peak_kind = measured_peaks()
@@ -253,14 +269,17 @@ def run_mine(args, rank, world, local_rank):
     M, d = args.M, 20
     n_terms2, n_terms1 = 190, 20
     grid_bytes = 8 * (n_terms2 * 69 * 72 + n_terms1 * 136)
+    rs = 8 if f64 else 4
+    grid_bytes = grid_bytes * esz // 8
+    sfx = "_f64" if f64 else "_f32"
     if gms / max(gl, 1) >= sms / max(sl, 1):
-        kname, kms, klaunch = "gather_f32", gms / max(gl, 1), gl
-        # nodes read (4 B per coordinate), f written, grids and coefficients read once
-        alg_bytes = 4 * d * M + 8 * M + grid_bytes + 8 * n
+        kname, kms, klaunch = ("gather_f64" if f64 else "gather2_f32"), gms / max(gl, 1), gl
+        # nodes read (one real per coordinate), f written, grids and coefficients read once
+        alg_bytes = rs * d * M + esz * M + grid_bytes + esz * n
     else:
-        kname, kms, klaunch = "spread_f32", sms / max(sl, 1), sl
+        kname, kms, klaunch = "spread" + sfx, sms / max(sl, 1), sl
         # nodes and y read, one grid written
-        alg_bytes = 4 * d * M + 8 * M + grid_bytes
+        alg_bytes = rs * d * M + esz * M + grid_bytes
     achieved = alg_bytes / (kms / 1e3) / 1e9
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic.json")
@@ -298,8 +317,10 @@ def run_mine(args, rank, world, local_rank):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64)",
-                "config": {"workload": WORKLOAD, "M": args.M, "precision": "fp32 grids and accumulation",
+                "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+                "data": "synthetic (seeded SplitMix64)",
+                "config": {"workload": WORKLOAD, "M": args.M,
+                           "precision": "fp64 throughout" if f64 else "fp32 grids and accumulation",
                            "window": "Kaiser-Bessel, sigma=2, 6 row x 8 column taps",
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
@@ -308,6 +329,117 @@ def run_mine(args, rank, world, local_rank):
                 "wall_s": wall}
         print(json.dumps(line), flush=True)
     P.close()
+
+
+# ----------------------------------------------------------- lambda path ---
+
+def run_lambda_path(args, local_rank):
+    """Group-lasso lambda path of the d = 30 workload: FP32 with the learned
+    screen vs FP32 on all groups vs FP64 on all groups (the plain path).
+
+    The workload's lambda values are read for the node-averaged data term
+    (1 / (2M)) ||y - F f||^2; the paper's functional has 1/2 ||y - F f||^2, so
+    the path runs with M times the listed values.  The screen is trained on the
+    paths of three problems of the same family at M / 8 nodes (seeds 101..103);
+    that training time is reported apart from the path times."""
+    import numpy as np
+    import torch
+
+    from paper_2010_10199_gb300 import build as cuda_build
+    from paper_2010_10199_gb300 import gft, inputs
+
+    cuda_build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    M = args.M
+    K = max(1, min(20, args.lambdas))
+    w = inputs.c4_fista(M=M)
+    terms, bw = w["terms"], w["bandwidths"]
+    lams = [float(M * v) for v in w["lambdas"][:K]]
+
+    def sync_time(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    # the screen: trained on the project's own paths of smaller problems
+    def train():
+        Xs, ys = [], []
+        for seed in (101, 102, 103):
+            mt = max(1000, M // 8)
+            wt = inputs.c4_fista(seed=seed, M=mt)
+            Pt = gft.Plan(torch.from_numpy(wt["x"].astype(np.float32)).to(dev), terms, bw)
+            yt = torch.from_numpy(wt["y"].astype(np.complex64)).to(dev)
+            lt = [float(mt * v) for v in wt["lambdas"][:K]]
+            path, _, _ = Pt.fista(yt, lt, max_it=args.max_it, tol=1e-6)
+            X, lab = gft.screening_training_set(Pt, yt, lt, path)
+            Xs.append(X)
+            ys.append(lab)
+            Pt.close()
+        X = torch.cat(Xs).contiguous()
+        lab = torch.cat(ys).contiguous()
+        pos = float(lab.mean())
+        net = gft.Mlp(gft.mlp_init_params(21))
+        net.train(X, lab, batch=256, epochs=150, lr=2e-3, pos_weight=max(1.0, (1 - pos) / max(pos, 1e-3)))
+        return net
+
+    net, t_train = sync_time(train)
+
+    x32 = torch.from_numpy(w["x"].astype(np.float32)).to(dev)
+    y32 = torch.from_numpy(w["y"].astype(np.complex64)).to(dev)
+    P32 = gft.Plan(x32, terms, bw)
+    (scr, sinfo, stats), t_scr = sync_time(
+        lambda: gft.fista_screened_path(P32, net, y32, lams, max_it=args.max_it, tol=args.tol, threshold=0.5))
+    (full32, finfo, rc32), t_full32 = sync_time(lambda: P32.fista(y32, lams, max_it=args.max_it, tol=args.tol))
+
+    blocks = [P32.term_offset(u) for u in range(len(terms))]
+
+    def groups(path):
+        out = []
+        for i in range(path.shape[0]):
+            act = [bool(torch.linalg.vector_norm(path[i, o:o + ln].to(torch.complex128)) > 0) for o, ln in blocks]
+            out.append(np.array(act))
+        return out
+
+    def rel(a, b):
+        a = a.to(torch.complex128)
+        b = b.to(torch.complex128)
+        return float(torch.linalg.vector_norm(a - b) / max(float(torch.linalg.vector_norm(b)), 1e-300))
+
+    g_scr, g_full32 = groups(scr), groups(full32)
+    res = {"fp32_screened_s": t_scr, "fp32_full_s": t_full32, "screen_training_s": t_train,
+           "fp32_screened_iterations": int(sum(i["iterations"] for i in sinfo)),
+           "fp32_full_iterations": int(sum(i["iterations"] for i in finfo)),
+           "screen_term_iterations": stats.get("term_iterations") if isinstance(stats, dict) else None,
+           "active_groups": [int(a.sum()) for a in g_full32],
+           "screened_vs_fp32_full": {"max_rel_l2": max(rel(scr[i], full32[i]) for i in range(K)),
+                                     "active_sets_equal": all(np.array_equal(a, b) for a, b in zip(g_scr, g_full32))}}
+    P32.close()
+    value = None
+    if not args.skip_f64:
+        x64 = torch.from_numpy(w["x"]).to(dev)
+        y64 = torch.from_numpy(w["y"]).to(dev)
+        P64 = gft.Plan(x64, terms, bw, precision=gft.PREC_F64)
+        (p64, i64, rc64), t64 = sync_time(lambda: P64.fista(y64, lams, max_it=args.max_it, tol=args.tol))
+        g64 = groups(p64)
+        res.update({"fp64_full_s": t64, "fp64_full_iterations": int(sum(i["iterations"] for i in i64)),
+                    "screened_vs_fp64_full": {"max_rel_l2": max(rel(scr[i], p64[i]) for i in range(K)),
+                                              "active_sets_equal": all(np.array_equal(a, b)
+                                                                       for a, b in zip(g_scr, g64))}})
+        value = t64 / t_scr
+        P64.close()
+    line = {"metric": "FISTA lambda-path time: plain FP64 full-group path / FP32 screened path",
+            "value": value, "unit": "x", "higher_is_better": True, "n_gpus": 1,
+            "dtype": "f32 (screened) vs f64 (plain)", "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": f"d=30, |u|<=2 (466 terms), N=32 (1D) / 16x16 (2D), M={M} uniform nodes, "
+                                   f"5 active pairs + 3 singletons, noise 0.05",
+                       "lambdas": f"first {K} of 20 geometric 1e-1..1e-5, times M",
+                       "fista": f"constant step L = 1.05 x power estimate, tol {args.tol}, max_it {args.max_it}, "
+                                f"warm-started path"},
+            "results": res}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -324,6 +456,9 @@ def main():
             torch.distributed.init_process_group("gloo")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.mode == "lambda-path":
+        if rank == 0:
+            run_lambda_path(args, local_rank)
     else:
         run_mine(args, rank, world, local_rank)
     if world > 1:

@@ -5,7 +5,9 @@
 // reference form of the method on the GPU: the window is evaluated directly
 // (sinh and sqrt in FP64) once per plan into per-node tables, the way NFFT
 // libraries precompute psi, and the kernels are straightforward: one thread
-// per node for the gather, FP64 shared-memory atomics for the spread.
+// per node for the gather; for the spread, nodes in cell order (the plan's
+// sorted records) summed per cell in registers, FP64 shared-memory atomics
+// once per cell.
 //
 // Window tables: one slot per (window, coordinate) pair that some term uses;
 // for node j, slot q holds the weights psi(tau + m - 1 - t) / psi(0) of taps
@@ -227,10 +229,109 @@ int launch_trafo_f64(Plan &p, const double2 *fhat, double2 *f) {
 
 // ------------------------------------------------------------ adjoint ----
 
-// Work item (problem 0, active term, node chunk z, chunks K): the nodes
-// [M z / K, M (z+1) / K) add y_j times their window into a shared-memory copy
-// of the term's stored grid with FP64 atomics (half-warp per node, lane (r, k):
-// column tap k, rows r, r+2, ..); the copy goes to partial grid z.
+// Sorted item (order <= 2, plan with cell-sorted records): the item's nodes in
+// the term's cell order, cut into 16 contiguous runs, one per half-warp.  Lane
+// (r, k) keeps the sums of column tap k and rows r, r+2, .. of the current
+// cell in registers and adds them to the shared grid when the cell changes
+// (FP64 atomics, once per cell instead of once per node).  Four nodes are
+// loaded ahead of their use.  Order 1: the lane groups r = 0, 1 take
+// alternate nodes.
+__device__ __forceinline__ void spread_sorted_item_f64(const DevPlan &P, const Term &T, const double2 *__restrict__ y,
+                                                       long long j0, long long j1, double2 *S, const double *wt) {
+    const int tid = threadIdx.x;
+    const int sub = tid & 15, hw = tid >> 4;
+    const int r = sub >> 3, k = sub & 7;
+    const long long M = P.M;
+    const int stride = T.stride, mc = T.mc, mr = T.mr;
+    const float4 *rec = P.srec + (long long)T.sort_slot * M;
+    const long long len = j1 - j0, L = (len + 15) / 16;
+    const long long a = j0 + min((long long)hw * L, len), b = j0 + min((long long)(hw + 1) * L, len);
+    const double *wcol = wt + (long long)T.slot_c * M * 8;
+    const bool kc = k < 2 * mc;
+    int cur = -1;
+    if (T.order == 2) {
+        const double *wrow = wt + (long long)T.slot_r0 * M * 8;
+        double ax[4] = {0.0, 0.0, 0.0, 0.0}, ay[4] = {0.0, 0.0, 0.0, 0.0};
+        auto flush = [&]() {
+            if (kc) {
+                double2 *base = S + cur + r * stride + k;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (r + 2 * q < 2 * mr) {
+                        atomicAdd(&base[2 * q * stride].x, ax[q]);
+                        atomicAdd(&base[2 * q * stride].y, ay[q]);
+                    }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ax[q] = ay[q] = 0.0;
+        };
+        for (long long p0 = a; p0 < b; p0 += 4) {
+            int off[4], jj[4];
+            double wc[4], wr[4][4];
+            double2 yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = p0 + u < b;
+                const float4 q = __ldg(rec + (ok ? p0 + u : a));
+                off[u] = ok ? __float_as_int(q.z) : -2;
+                jj[u] = __float_as_int(q.w);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long j = jj[u];
+                yv[u] = __ldg(y + j);
+                wc[u] = kc ? __ldg(wcol + j * 8 + k) : 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) wr[u][q] = r + 2 * q < 2 * mr ? __ldg(wrow + j * 8 + r + 2 * q) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (off[u] == -2) break;
+                if (off[u] != cur) {
+                    if (cur >= 0) flush();
+                    cur = off[u];
+                }
+                const double yx = yv[u].x * wc[u], yy = yv[u].y * wc[u];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    ax[q] = fma(yx, wr[u][q], ax[q]);
+                    ay[q] = fma(yy, wr[u][q], ay[q]);
+                }
+            }
+        }
+        if (cur >= 0) flush();
+    } else {
+        double ax = 0.0, ay = 0.0;
+        for (long long p = a + r; p < b; p += 2) {
+            const float4 q = __ldg(rec + p);
+            const int off = __float_as_int(q.z);
+            const long long j = __float_as_int(q.w);
+            if (off != cur) {
+                if (cur >= 0 && kc) {
+                    atomicAdd(&S[cur + k].x, ax);
+                    atomicAdd(&S[cur + k].y, ay);
+                }
+                ax = ay = 0.0;
+                cur = off;
+            }
+            const double w = kc ? __ldg(wcol + j * 8 + k) : 0.0;
+            const double2 v = __ldg(y + j);
+            ax = fma(v.x, w, ax);
+            ay = fma(v.y, w, ay);
+        }
+        if (cur >= 0 && kc) {
+            atomicAdd(&S[cur + k].x, ax);
+            atomicAdd(&S[cur + k].y, ay);
+        }
+    }
+}
+
+// Work item (problem 0, active term, node chunk z, chunks K): the item's
+// nodes add y_j times their window into a shared-memory copy of the term's
+// stored grid, which then goes to partial grid z.  Terms with cell-sorted
+// records take the sorted path above; the others (order 3, or no records)
+// add every tap with FP64 atomics (half-warp per node, lane (r, k): column tap
+// k, rows r, r+2, ..), nodes in their original order.
 __global__ void __launch_bounds__(256) spread_f64(DevPlan P, const int4 *items, const double2 *__restrict__ y,
                                                   int n_items, int *counter, long long max_grid_bytes,
                                                   const double *wt, const int *wb) {
@@ -255,39 +356,43 @@ __global__ void __launch_bounds__(256) spread_f64(DevPlan P, const int4 *items, 
         for (long long e = tid; e < elems; e += 256) S[e] = make_double2(0.0, 0.0);
         __syncthreads();
         const int stride = T.stride, n = T.n, mc = T.mc, mr = T.mr;
-        for (long long j = j0 + hw; j < j1; j += 16) {
-            const double2 yv = __ldg(y + j);
-            const double wck = k < 2 * mc ? __ldg(wt + ((long long)T.slot_c * M + j) * 8 + k) : 0.0;
-            const int fc = __ldg(wb + (long long)T.slot_c * M + j);
-            const double yx = yv.x * wck, yy = yv.y * wck;
-            if (T.order == 1) {
-                if (r == 0 && k < 2 * mc) {
-                    atomicAdd(&S[fc + k].x, yx);
-                    atomicAdd(&S[fc + k].y, yy);
-                }
-            } else if (T.order == 2) {
-                const long long ro = (long long)T.slot_r0 * M + j;
-                const int fr = __ldg(wb + ro);
-                if (k < 2 * mc)
-                    for (int i = r; i < 2 * mr; i += 2) {
-                        const double w = __ldg(wt + ro * 8 + i);
-                        double2 *c = S + (fr + i) * stride + fc + k;
-                        atomicAdd(&c->x, yx * w);
-                        atomicAdd(&c->y, yy * w);
+        if (T.sort_slot >= 0 && P.srec && T.order <= 2) {
+            spread_sorted_item_f64(P, T, y, j0, j1, S, wt);
+        } else {
+            for (long long j = j0 + hw; j < j1; j += 16) {
+                const double2 yv = __ldg(y + j);
+                const double wck = k < 2 * mc ? __ldg(wt + ((long long)T.slot_c * M + j) * 8 + k) : 0.0;
+                const int fc = __ldg(wb + (long long)T.slot_c * M + j);
+                const double yx = yv.x * wck, yy = yv.y * wck;
+                if (T.order == 1) {
+                    if (r == 0 && k < 2 * mc) {
+                        atomicAdd(&S[fc + k].x, yx);
+                        atomicAdd(&S[fc + k].y, yy);
                     }
-            } else if (k < 2 * mc) {
-                const long long ra0 = (long long)T.slot_r0 * M + j, rb0 = (long long)T.slot_r1 * M + j;
-                const int fa = __ldg(wb + ra0), fb = __ldg(wb + rb0);
-                const int col = wrap(fc - mc + 1 + k, n);
-                for (int ia = 0; ia < 2 * mr; ++ia) {
-                    const double wa = __ldg(wt + ra0 * 8 + ia);
-                    const int ra = wrap(fa - mr + 1 + ia, n);
-                    for (int ib = r; ib < 2 * mr; ib += 2) {
-                        const double w = wa * __ldg(wt + rb0 * 8 + ib);
-                        const int rb = wrap(fb - mr + 1 + ib, n);
-                        double2 *c = S + (ra * n + rb) * stride + col;
-                        atomicAdd(&c->x, yx * w);
-                        atomicAdd(&c->y, yy * w);
+                } else if (T.order == 2) {
+                    const long long ro = (long long)T.slot_r0 * M + j;
+                    const int fr = __ldg(wb + ro);
+                    if (k < 2 * mc)
+                        for (int i = r; i < 2 * mr; i += 2) {
+                            const double w = __ldg(wt + ro * 8 + i);
+                            double2 *c = S + (fr + i) * stride + fc + k;
+                            atomicAdd(&c->x, yx * w);
+                            atomicAdd(&c->y, yy * w);
+                        }
+                } else if (k < 2 * mc) {
+                    const long long ra0 = (long long)T.slot_r0 * M + j, rb0 = (long long)T.slot_r1 * M + j;
+                    const int fa = __ldg(wb + ra0), fb = __ldg(wb + rb0);
+                    const int col = wrap(fc - mc + 1 + k, n);
+                    for (int ia = 0; ia < 2 * mr; ++ia) {
+                        const double wa = __ldg(wt + ra0 * 8 + ia);
+                        const int ra = wrap(fa - mr + 1 + ia, n);
+                        for (int ib = r; ib < 2 * mr; ib += 2) {
+                            const double w = wa * __ldg(wt + rb0 * 8 + ib);
+                            const int rb = wrap(fb - mr + 1 + ib, n);
+                            double2 *c = S + (ra * n + rb) * stride + col;
+                            atomicAdd(&c->x, yx * w);
+                            atomicAdd(&c->y, yy * w);
+                        }
                     }
                 }
             }

@@ -520,7 +520,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     }
     // cell-sorted node copies for the adjoint (terms of order <= 2), if they
     // fit in half the free device memory
-    if (e == cudaSuccess && o.node_sort >= 0 && M > 0 && p.precision == ANOVA_PREC_F32) {
+    if (e == cudaSuccess && o.node_sort >= 0 && M > 0) {
         int ns = 0;
         for (int s = 0; s < p.n_terms; ++s) ns += p.h_terms[s].order <= 2;
         size_t free_b = 0, total_b = 0;
@@ -565,8 +565,8 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
             wrap_nodes_f32<<<blocks, 256, 0, p.stream>>>((const float *)x_dev, (float *)p.x, total);
         chk(cudaGetLastError());
     }
-    if (e == cudaSuccess) chk(cuda_err_of(sort_nodes_by_cell(p)));
     if (e == cudaSuccess && p.precision == ANOVA_PREC_F64) chk(cuda_err_of(build_window_tables_f64(p)));
+    if (e == cudaSuccess) chk(cuda_err_of(sort_nodes_by_cell(p)));
     if (e == cudaSuccess) chk(cuda_err_of(set_active_terms(p, nullptr)));
     chk(cudaStreamSynchronize(p.stream));
     // wins vector is copied; keep host term table

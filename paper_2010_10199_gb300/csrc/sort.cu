@@ -9,7 +9,8 @@
 // one term per blockIdx.y, and per sorted node a 16-byte record with the
 // window arguments, the grid offset of its cell and its original index.
 // The order inside a cell is left to the atomics of the scatter; it changes
-// only the rounding order of the sums.
+// only the rounding order of the sums.  FP64 plans sort by the bases of their
+// window tables (records carry only the cell offset and the node index).
 #include <algorithm>
 
 #include "device.cuh"
@@ -108,6 +109,50 @@ __global__ void k_cell_scatter(const Term *terms, const float *x, long long M, i
     }
 }
 
+// FP64 plans: the cell of a node is that of its window-table bases (the
+// spread adds at exactly those bases); records (0, 0, offset, index)
+__device__ __forceinline__ int cell_of64(const Term &T, const int *wb, long long M, long long j, int &off) {
+    const int fc = wb[(long long)T.slot_c * M + j];
+    if (T.order != 2) {
+        off = fc;
+        return fc;
+    }
+    const int fr = wb[(long long)T.slot_r0 * M + j];
+    off = fr * T.stride + fc;
+    return fr * T.n + fc;
+}
+
+__global__ void k_cell_count64(const Term *terms, const int *wb, long long M, int *counts, int max_bins) {
+    extern __shared__ int hist[];
+    const Term &T = terms[blockIdx.y];
+    if (T.sort_slot < 0) return;
+    const int nb = cell_bins(T);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M; j += (long long)gridDim.x * blockDim.x) {
+        int off;
+        atomicAdd(&hist[cell_of64(T, wb, M, j, off)], 1);
+    }
+    __syncthreads();
+    int *cnt = counts + (long long)T.sort_slot * max_bins;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (hist[b]) atomicAdd(&cnt[b], hist[b]);
+}
+
+__global__ void k_cell_scatter64(const Term *terms, const int *wb, long long M, int *cursor, int max_bins,
+                                 float4 *srec) {
+    const Term &T = terms[blockIdx.y];
+    if (T.sort_slot < 0) return;
+    int *cur = cursor + (long long)T.sort_slot * max_bins;
+    float4 *dst = srec + (long long)T.sort_slot * M;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M;
+         j += (long long)gridDim.x * blockDim.x) {
+        int off;
+        const int pos = atomicAdd(&cur[cell_of64(T, wb, M, j, off)], 1);
+        dst[pos] = make_float4(0.f, 0.f, __int_as_float(off), __int_as_float((int)j));
+    }
+}
+
 int sort_nodes_by_cell(Plan &p) {
     if (!p.srec || p.n_sorted == 0 || p.M == 0) return ANOVA_OK;
     int max_bins = 1;
@@ -119,15 +164,24 @@ int sort_nodes_by_cell(Plan &p) {
     cudaError_t e = cudaMalloc(&counts, sizeof(int) * (size_t)p.n_sorted * max_bins);
     if (e != cudaSuccess) return cuda_status(e);
     const size_t hist_bytes = sizeof(int) * (size_t)max_bins;
-    if (hist_bytes > 48 * 1024) e = cudaFuncSetAttribute(k_cell_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         (int)hist_bytes);
+    const bool f64 = p.precision == ANOVA_PREC_F64;
+    if (hist_bytes > 48 * 1024)
+        e = cudaFuncSetAttribute(f64 ? (const void *)k_cell_count64 : (const void *)k_cell_count,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes);
     const int bx = (int)std::max<long long>(1, std::min<long long>(64, (p.M + 4095) / 4096));
     const dim3 grid(bx, p.n_terms);
     if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)p.n_sorted * max_bins, p.stream);
     if (e == cudaSuccess) {
-        k_cell_count<<<grid, 256, hist_bytes, p.stream>>>(p.terms, (const float *)p.x, p.M, counts, max_bins);
+        if (f64)
+            k_cell_count64<<<grid, 256, hist_bytes, p.stream>>>(p.terms, p.wb64, p.M, counts, max_bins);
+        else
+            k_cell_count<<<grid, 256, hist_bytes, p.stream>>>(p.terms, (const float *)p.x, p.M, counts, max_bins);
         k_cell_scan<<<p.n_terms, 1024, 0, p.stream>>>(p.terms, counts, max_bins);
-        k_cell_scatter<<<grid, 256, 0, p.stream>>>(p.terms, (const float *)p.x, p.M, counts, max_bins, p.srec);
+        if (f64)
+            k_cell_scatter64<<<grid, 256, 0, p.stream>>>(p.terms, p.wb64, p.M, counts, max_bins, p.srec);
+        else
+            k_cell_scatter<<<grid, 256, 0, p.stream>>>(p.terms, (const float *)p.x, p.M, counts, max_bins,
+                                                       p.srec);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
