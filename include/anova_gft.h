@@ -82,7 +82,7 @@ typedef struct {
     int n_ctas;         /* adjoint: most node chunks (partial grids) per term, <= 64 (0: auto) */
     int node_sort;      /* adjoint: 0 = keep a copy of the nodes sorted by grid cell for every
                            term of order <= 2 when it fits in half the free device memory
-                           (12 bytes per node and term); -1 = never */
+                           (16 bytes per node and term); -1 = never */
 } anova_plan_options;
 
 /*
@@ -99,7 +99,11 @@ typedef struct {
  *   opts       : host, may be NULL for defaults (FP32, eps 1e-5)
  *   stream     : cudaStream_t used by every later call on this plan (NULL = legacy default)
  * Errors: ANOVA_ERR_INVALID for bad sizes/terms, ANOVA_ERR_UNSUPPORTED for
- * |u| > 3 or a grid that does not fit the kernels, ANOVA_ERR_NOMEM.
+ * |u| > 3 or a grid that does not fit the kernels (two copies of the
+ * n_u^{|u|} FFT array in shared memory: 200 KB, i.e. 3-D terms up to n = 23
+ * in FP32 and n = 18 in FP64; one stored grid of at most 100 KB, FP64 200 KB),
+ * ANOVA_ERR_NOMEM.  FP64 plans also precompute window tables of
+ * 68 bytes per node for every (window, coordinate) pair in use.
  * Synchronises the stream before returning.
  */
 int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, int n_terms,
@@ -303,6 +307,41 @@ int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, c
 int anova_profile_enable(anova_plan_t plan, int on);
 int anova_profile_read(anova_plan_t plan, double *ms, int64_t *launches, const char **names, int max_stages,
                        int *n_stages, int reset);
+
+/*
+ * anova_plan_autotune -- choose plan options for one node set and term list
+ * by measurement (the NFFT's error falls as the window widens and the
+ * oversampling grows, Sec. 3 after eq. (somafm); its cost rises with both).
+ * A reference plan (sigma 2.5, 8 x 8 taps) transforms two fixed pseudo-random
+ * vectors; every candidate plan transforms the same vectors, its estimated
+ * error is max(rel. l2 distance of F fhat, of F^H y) to the reference, and its
+ * time is the mean of `reps` timed pairs after one warm-up pair on `stream`.
+ * Candidates: sigma in {1.75, 2, 2.5} x row half-width in {3, 4}; then, around
+ * the fastest one within eps_target, node chunks per term (n_ctas) in
+ * {4, 16, 64} and the original node order (node_sort = -1).
+ *   opts       : in: base options (precision must be ANOVA_PREC_F32);
+ *                out: the fastest candidate with est_error <= eps_target
+ *   d .. bandwidth : as for anova_plan_create
+ *   trials     : host array [max_trials] receiving every candidate tried
+ *                (ms_pair and est_error are INFINITY for one that could not
+ *                be built), in order; *n_trials gets the count (may be NULL)
+ * Errors: ANOVA_ERR_INVALID, ANOVA_ERR_UNSUPPORTED (not FP32, or no candidate
+ * met eps_target), errors of anova_plan_create.  Creates and destroys plans
+ * (device allocations); synchronises the stream.  The paper has no tuner.
+ */
+typedef struct {
+    double sigma;
+    int window_m_row;
+    int n_ctas;
+    int node_sort;
+    double ms_pair;    /* mean time of one forward + adjoint pair */
+    double est_error;  /* estimated relative l2 error against the reference plan */
+    int chosen;        /* 1 for the candidate written to opts */
+} anova_tune_trial;
+
+int anova_plan_autotune(anova_plan_options *opts, int d, int64_t M, const void *x_dev, int n_terms,
+                        const int32_t *term_dims, const int32_t *bandwidth, double eps_target, int reps,
+                        anova_tune_trial *trials, int max_trials, int *n_trials, void *stream);
 
 /*
  * grouped_trafo_noalloc -- f = F(X, I_N(U)) fhat without a plan and without

@@ -349,7 +349,7 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
 // the original order) into a shared-memory copy of the term's stored grid
 // (halos included) and writes it to partial grid z of its problem.  CTAs take
 // items from a global counter.
-template <int MR>
+template <int MR, typename G>
 __global__ void __launch_bounds__(SPREAD_THREADS, 3)
 spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n_items, int *counter,
            long long max_grid_bytes) {
@@ -371,7 +371,7 @@ spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n
         const Term &T = P.terms[P.act[itm.y]];
         const long long M = P.M;
         const long long j0 = M * itm.z / itm.w, j1 = M * (itm.z + 1) / itm.w;
-        const long long elems = T.grid_bytes / 8;
+        const long long elems = T.grid_bytes / (long long)sizeof(G);   // shared copy is FP32 complex
         float4 *S4 = (float4 *)S;
         for (long long e = tid; e < elems / 2; e += SPREAD_THREADS) S4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 *y = y_base + P.vec_node_off;
@@ -390,39 +390,64 @@ spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n
         else
             spread_unsorted_item<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
         __syncthreads();
-        float4 *dst = (float4 *)(P.partials + (long long)itm.z * P.grid_elems + T.grid_off);
-        for (long long e = tid; e < elems / 2; e += SPREAD_THREADS) dst[e] = S4[e];
+        if constexpr (std::is_same<G, float2>::value) {
+            float4 *dst = (float4 *)(P.partials + (long long)itm.z * P.grid_elems + T.grid_off);
+            for (long long e = tid; e < elems / 2; e += SPREAD_THREADS) dst[e] = S4[e];
+        } else {
+            G *dst = (G *)P.partials + (long long)itm.z * P.grid_elems + T.grid_off;
+            for (long long e = tid; e < elems; e += SPREAD_THREADS) dst[e] = GridEl<G>::store(S[e].x, S[e].y);
+        }
         __syncthreads();
     }
 }
 
+template <typename G>
 __global__ void reduce_partials_f32(DevPlan single, BatchArgs B) {
     const DevPlan &P = B.plans ? B.plans[blockIdx.y] : single;
     if (P.skip && *P.skip) return;
-    const float4 *__restrict__ partials = (const float4 *)P.partials;
-    float4 *__restrict__ out = (float4 *)P.grids;
-    const long long n4 = P.grid_elems / 2, pstride4 = n4;
     const int nparts = P.spread_chunks;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int c = 0; c < nparts; ++c) {
-            float4 v = __ldg(partials + (long long)c * pstride4 + i);
-            a.x += v.x;
-            a.y += v.y;
-            a.z += v.z;
-            a.w += v.w;
+    if constexpr (std::is_same<G, float2>::value) {
+        const float4 *__restrict__ partials = (const float4 *)P.partials;
+        float4 *__restrict__ out = (float4 *)P.grids;
+        const long long n4 = P.grid_elems / 2, pstride4 = n4;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+             i += (long long)gridDim.x * blockDim.x) {
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < nparts; ++c) {
+                float4 v = __ldg(partials + (long long)c * pstride4 + i);
+                a.x += v.x;
+                a.y += v.y;
+                a.z += v.z;
+                a.w += v.w;
+            }
+            out[i] = a;
         }
-        out[i] = a;
+    } else {
+        // 16-bit partials and grid: widen, sum in FP32, round once
+        const G *__restrict__ partials = (const G *)P.partials;
+        G *__restrict__ out = (G *)P.grids;
+        const long long ne = P.grid_elems;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ne;
+             i += (long long)gridDim.x * blockDim.x) {
+            float ax = 0.f, ay = 0.f;
+            for (int c = 0; c < nparts; ++c) {
+                const float2 v = GridEl<G>::load(partials[(long long)c * ne + i]);
+                ax += v.x;
+                ay += v.y;
+            }
+            out[i] = GridEl<G>::store(ax, ay);
+        }
     }
 }
 
+template <typename G>
 __global__ void adjoint_post_f32(DevPlan single, BatchArgs B, float2 *__restrict__ fhat_base) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int pb = B.plans ? B.blk_prob[blockIdx.x] : 0;
     const DevPlan &P = B.plans ? B.plans[pb] : single;
     const int sblk = B.plans ? (int)blockIdx.x - B.blk0[pb] : (int)blockIdx.x;
     if (P.skip && *P.skip) return;
-    const float2 *__restrict__ grids = P.grids;
+    const G *__restrict__ grids = (const G *)P.grids;
     float2 *__restrict__ fhat = fhat_base + P.vec_coef_off;
     const Term T = P.terms[P.act[sblk]];
     const int n = T.n, s = T.order, N = T.N;
@@ -430,7 +455,7 @@ __global__ void adjoint_post_f32(DevPlan single, BatchArgs B, float2 *__restrict
     for (int j = 1; j < s; ++j) fe *= n;
     float2 *a = (float2 *)smem_raw;
     float2 *b = a + fe;
-    const float2 *g = grids + T.grid_off;
+    const G *g = grids + T.grid_off;
     // fold the stored (halo) grid onto the periodic grid
     for (int e = threadIdx.x; e < fe; e += blockDim.x) {
         float2 v = make_float2(0.f, 0.f);
@@ -444,14 +469,14 @@ __global__ void adjoint_post_f32(DevPlan single, BatchArgs B, float2 *__restrict
                 for (int dc = -1; dc <= 1; ++dc) {
                     int ec = qc + T.hc + dc * n;
                     if (ec < 0 || ec >= ecw) continue;
-                    float2 u = g[(long long)er * T.stride + ec];
+                    const float2 u = GridEl<G>::load(g[(long long)er * T.stride + ec]);
                     v.x += u.x;
                     v.y += u.y;
                 }
             }
         } else {
             int row = e / n, c = e % n;
-            v = g[(long long)row * T.stride + c];
+            v = GridEl<G>::load(g[(long long)row * T.stride + c]);
         }
         a[e] = v;
     }
@@ -589,21 +614,49 @@ __global__ void sum_y_stage2(DevPlan single, BatchArgs B, const double2 *part_ba
     for (int e = 0; e < n_empty; ++e) fhat[eoff[e]] = make_float2((float)sx, (float)sy);
 }
 
+template <typename G>
 static void adjoint_attrs() {
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(adjoint_post_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(spread_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        cudaFuncSetAttribute(spread_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(adjoint_post_f32<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(spread_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         attr_done = true;
     }
+}
+
+// spread + reduce + post for grids stored as G; sgrid = bytes of the largest
+// grid in FP32 (the spread's shared-memory copy)
+template <typename G>
+static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P,
+                            const float2 *y, float2 *fhat, int n_items, int *counter, int n_blocks, int mr,
+                            long long sgrid, int max_fft_elems, int sm_count, long long max_grid_elems) {
+    adjoint_attrs<G>();
+    const size_t ssm = spread_smem_bytes(sgrid);
+    const int ctas = std::max(1, std::min(n_items, spread_ctas_per_sm(sgrid) * sm_count));
+    if (prof) stage_begin(*prof, ST_SPREAD);
+    cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (mr <= 3)
+        spread_f32<3, G><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items, counter, sgrid);
+    else
+        spread_f32<4, G><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items, counter, sgrid);
+    if (prof) stage_end(*prof, ST_SPREAD);
+    const long long n4 = max_grid_elems / 2;
+    const int rb = (int)std::max<long long>(1, std::min<long long>(sm_count * 8LL / std::max(1, P) + 1, (n4 + 255) / 256));
+    if (prof) stage_begin(*prof, ST_REDUCE);
+    reduce_partials_f32<G><<<dim3(rb, P), 256, 0, st>>>(v, B);
+    if (prof) stage_end(*prof, ST_REDUCE);
+    const size_t post_smem = (size_t)max_fft_elems * 2 * sizeof(float2);
+    if (prof) stage_begin(*prof, ST_POST);
+    adjoint_post_f32<G><<<n_blocks, 256, post_smem, st>>>(v, B, fhat);
+    if (prof) stage_end(*prof, ST_POST);
 }
 
 // The adjoint kernels for one problem (B.plans == null) or a batch of P problems.
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
                    float2 *fhat, int n_items, int *counter, int n_blocks, int mr, long long max_grid_bytes,
-                   int max_fft_elems, int sm_count, long long max_grid_elems, bool any_empty, double2 *scratch) {
-    adjoint_attrs();
+                   int max_fft_elems, int sm_count, long long max_grid_elems, bool any_empty, double2 *scratch,
+                   int prec) {
     if (any_empty) {
         const int nb = 256;
         if (prof) stage_begin(*prof, ST_SUMY);
@@ -612,24 +665,15 @@ int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArg
         if (prof) stage_end(*prof, ST_SUMY);
     }
     if (n_blocks == 0) return cuda_status(cudaGetLastError());
-    const size_t ssm = spread_smem_bytes(max_grid_bytes);
-    const int ctas = std::max(1, std::min(n_items, spread_ctas_per_sm(max_grid_bytes) * sm_count));
-    if (prof) stage_begin(*prof, ST_SPREAD);
-    cudaMemsetAsync(counter, 0, sizeof(int), st);
-    if (mr <= 3)
-        spread_f32<3><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items, counter, max_grid_bytes);
+    if (prec == ANOVA_PREC_F16)
+        adjoint_kernels<__half2>(prof, st, v, B, P, y, fhat, n_items, counter, n_blocks, mr, 2 * max_grid_bytes,
+                                 max_fft_elems, sm_count, max_grid_elems);
+    else if (prec == ANOVA_PREC_BF16)
+        adjoint_kernels<__nv_bfloat162>(prof, st, v, B, P, y, fhat, n_items, counter, n_blocks, mr,
+                                        2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems);
     else
-        spread_f32<4><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items, counter, max_grid_bytes);
-    if (prof) stage_end(*prof, ST_SPREAD);
-    const long long n4 = max_grid_elems / 2;
-    const int rb = (int)std::max<long long>(1, std::min<long long>(sm_count * 8LL / std::max(1, P) + 1, (n4 + 255) / 256));
-    if (prof) stage_begin(*prof, ST_REDUCE);
-    reduce_partials_f32<<<dim3(rb, P), 256, 0, st>>>(v, B);
-    if (prof) stage_end(*prof, ST_REDUCE);
-    const size_t post_smem = (size_t)max_fft_elems * 2 * sizeof(float2);
-    if (prof) stage_begin(*prof, ST_POST);
-    adjoint_post_f32<<<n_blocks, 256, post_smem, st>>>(v, B, fhat);
-    if (prof) stage_end(*prof, ST_POST);
+        adjoint_kernels<float2>(prof, st, v, B, P, y, fhat, n_items, counter, n_blocks, mr, max_grid_bytes,
+                                max_fft_elems, sm_count, max_grid_elems);
     return cuda_status(cudaGetLastError());
 }
 
@@ -645,7 +689,8 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s) mr = p.h_terms[s].mr > 0 ? p.h_terms[s].mr : mr;
     return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.n_items, p.counter, p.n_act, mr, p.max_grid_bytes,
-                          p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0, (double2 *)p.scratch);
+                          p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0, (double2 *)p.scratch,
+                          p.precision);
 }
 
 }  // namespace agft

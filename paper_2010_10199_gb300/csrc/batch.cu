@@ -22,7 +22,7 @@
 namespace agft {
 
 int gather_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, const float2 *fhat, float2 *f, int n_tiles,
-                  int mr, int pitch, long long max_grid_bytes, int dmax, int sm_count);
+                  int mr, int pitch, long long max_grid_bytes, int dmax, int sm_count, int prec);
 __global__ void trafo_pre_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base);
 
 constexpr int BRB = 32;   // partial sums per problem segment
@@ -83,12 +83,13 @@ static int batch_trafo(Batch &b, cudaStream_t st, const float2 *fhat, float2 *f)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
     return gather_launch(st, b.views[0], b.args, fhat, f, b.n_tiles, b.mr, b.pitch, b.max_grid_bytes, b.dmax,
-                         b.sm_count);
+                         b.sm_count, ANOVA_PREC_F32);
 }
 
 static int batch_adjoint(Batch &b, cudaStream_t st, const float2 *y, float2 *fhat) {
     return adjoint_launch(nullptr, st, b.views[0], b.args, b.P, y, fhat, b.n_items, b.counter, b.n_blocks, b.mr,
-                          b.max_grid_bytes, b.max_fft, b.sm_count, b.max_grid_elems, b.any_empty, b.scratch);
+                          b.max_grid_bytes, b.max_fft, b.sm_count, b.max_grid_elems, b.any_empty, b.scratch,
+                          ANOVA_PREC_F32);
 }
 
 // ----------------------------------------------------- segmented kernels --

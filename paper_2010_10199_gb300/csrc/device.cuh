@@ -2,9 +2,37 @@
 // waits, and the shared-memory mixed-radix FFT used for the oversampled grids.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace agft {
+
+// ---------------------------------------------------------- grid elements --
+
+// Storage type of an FP32-computing plan's grids: complex FP32 (float2) or a
+// pair of 16-bit floats (FP16 or BF16); values are widened to FP32 on load and
+// rounded to nearest on store, every sum stays in FP32.
+template <typename G>
+struct GridEl;
+template <>
+struct GridEl<float2> {
+    static __device__ __forceinline__ float2 load(float2 v) { return v; }
+    static __device__ __forceinline__ float2 store(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct GridEl<__half2> {
+    static __device__ __forceinline__ float2 load(__half2 v) { return __half22float2(v); }
+    static __device__ __forceinline__ __half2 store(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <>
+struct GridEl<__nv_bfloat162> {
+    static __device__ __forceinline__ float2 load(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ __nv_bfloat162 store(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
 
 // ---------------------------------------------------------------- windows --
 

@@ -29,6 +29,7 @@ constexpr int G2_THREADS = 256;
 constexpr int G2_WARPS = G2_THREADS / 32;
 constexpr int G2_PTS = 8;                              // nodes per half-warp
 constexpr int G2_TILE = (G2_THREADS / 16) * G2_PTS;    // 128 nodes per CTA tile
+static_assert(G2_PTS == 8, "coordinate loads read a half-warp's nodes as two float4");
 
 // Problem of a tile and the number of its terms still to run (0 when the
 // problem's skip flag is set).
@@ -66,22 +67,24 @@ __device__ __forceinline__ void stream_ahead(const DevPlan &single, const BatchA
 }
 
 // One thread: copy the stored grid of term s of tile t into buffer buf.
+template <typename G>
 __device__ __forceinline__ void issue_grid(const DevPlan &single, const BatchArgs &B, int t, int s, int buf,
-                                           float2 *sm2, int gb_el, uint64_t *bars) {
+                                           G *sm2, int gb_el, uint64_t *bars) {
     int lt;
     const DevPlan &D = tile_plan(single, B, t, lt);
     const ActRec &R = D.act_rec[s];
     fence_proxy_async();
     mbar_expect_tx(&bars[buf], (uint32_t)R.grid_bytes);
-    bulk_g2s(sm2 + (buf ? gb_el : 0), D.grids + R.grid_off, (uint32_t)R.grid_bytes, &bars[buf]);
+    bulk_g2s(sm2 + (buf ? gb_el : 0), (const G *)D.grids + R.grid_off, (uint32_t)R.grid_bytes, &bars[buf]);
 }
 
-template <int MR, int PITCH>
+template <int MR, int PITCH, typename G>
 __global__ void __launch_bounds__(G2_THREADS, 2)
 gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, float2 *__restrict__ f_base,
             int n_tiles, int pitch_rt, long long max_grid_bytes, int dmax) {
-    extern __shared__ __align__(128) float2 sm2[];
-    const int gb_el = (int)(max_grid_bytes / 8);
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    G *sm2 = (G *)sm_raw;   // two grid buffers, grid elements of the plan's storage type
+    const int gb_el = (int)(max_grid_bytes / sizeof(G));
     float *xs = (float *)(sm2 + 2 * gb_el);                     // [d][G2_TILE]
     uint64_t *bars = (uint64_t *)(xs + dmax * G2_TILE);         // full barriers of the two buffers
     unsigned int *outs = (unsigned int *)(bars + 2);            // warps done with each buffer (running count)
@@ -190,9 +193,16 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
             const int boff = b ? gb_el : 0;
             const float *xc = xs + R.col * G2_TILE + pbase;
             if (order == 2) {
+                // the half-warp's 8 coordinates in two 16-byte loads (broadcast to its lanes)
+                float xcv[G2_PTS];
+                {
+                    const float4 c0 = *(const float4 *)xc, c1 = *(const float4 *)(xc + 4);
+                    xcv[0] = c0.x, xcv[1] = c0.y, xcv[2] = c0.z, xcv[3] = c0.w;
+                    xcv[4] = c1.x, xcv[5] = c1.y, xcv[6] = c1.z, xcv[7] = c1.w;
+                }
 #pragma unroll
                 for (int i = 0; i < G2_PTS; i += 2) {
-                    const float t0 = fmaf(xc[i], nf, hn), t1 = fmaf(xc[i + 1], nf, hn);
+                    const float t0 = fmaf(xcv[i], nf, hn), t1 = fmaf(xcv[i + 1], nf, hn);
                     const float fl0 = fminf(floorf(t0), nm1), fl1 = fminf(floorf(t1), nm1);
                     const float wt = horner8(cc, r ? fmaf(2.f, t1 - fl1, -1.f) : fmaf(2.f, t0 - fl0, -1.f));
                     const float cw0 = __shfl_sync(0xffffffffu, wt, (half << 4) | k);
@@ -202,8 +212,8 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
                     float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f;
 #pragma unroll
                     for (int j = 0; j < MR; ++j) {
-                        const float2 g0 = sm2[idx0 + 2 * j * pitch];
-                        const float2 g1 = sm2[idx1 + 2 * j * pitch];
+                        const float2 g0 = GridEl<G>::load(sm2[idx0 + 2 * j * pitch]);
+                        const float2 g1 = GridEl<G>::load(sm2[idx1 + 2 * j * pitch]);
                         sx0 = fmaf(rw[i][j], g0.x, sx0);
                         sy0 = fmaf(rw[i][j], g0.y, sy0);
                         sx1 = fmaf(rw[i + 1][j], g1.x, sx1);
@@ -221,7 +231,7 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
                     const float t = fmaf(xc[i + r], nf, hn);
                     const float fl = fminf(floorf(t), nm1);
                     const float cw = horner8(cc, fmaf(2.f, t - fl, -1.f));
-                    const float2 g = sm2[boff + (int)fl + k];
+                    const float2 g = GridEl<G>::load(sm2[boff + (int)fl + k]);
                     const float vx = cw * g.x, vy = cw * g.y;
                     ax[i] += r ? 0.f : vx;
                     ay[i] += r ? 0.f : vy;
@@ -235,7 +245,7 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
                 const int mr = T.mr, mc = T.mc, stride = T.stride;
                 const float *xa_p = xs + T.row0 * G2_TILE + pbase;
                 const float *xb_p = xs + T.row1 * G2_TILE + pbase;
-                const float2 *G = sm2 + boff;
+                const G *Gs = sm2 + boff;
 #pragma unroll
                 for (int i = 0; i < G2_PTS; ++i) {
                     float ta, tb, tc;
@@ -251,7 +261,7 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
                         for (int jb = r; jb < 2 * mr; jb += 2) {
                             const float wb = kb_direct(tb + (float)(mr - 1 - jb), mr, W.b, W.inv_psi0);
                             const int rb = wrap(fb - mr + 1 + jb, n);
-                            const float2 v = G[(ra * n + rb) * stride + cidx];
+                            const float2 v = GridEl<G>::load(Gs[(ra * n + rb) * stride + cidx]);
                             const float w = wa * wb;
                             sx = fmaf(w, v.x, sx);
                             sy = fmaf(w, v.y, sy);
@@ -303,38 +313,46 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
     }
 }
 
-template <int MR, int PITCH>
+template <int MR, int PITCH, typename G>
 static void launch_one(cudaStream_t st, const DevPlan &v, const BatchArgs &B, const float2 *fhat, float2 *f,
                        int n_tiles, size_t smem, int ctas, int pitch, long long max_grid_bytes, int dmax) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(gather2_f32<MR, PITCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(gather2_f32<MR, PITCH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         attr = true;
     }
-    gather2_f32<MR, PITCH><<<ctas, G2_THREADS, smem, st>>>(v, B, fhat, f, n_tiles, pitch, max_grid_bytes, dmax);
+    gather2_f32<MR, PITCH, G><<<ctas, G2_THREADS, smem, st>>>(v, B, fhat, f, n_tiles, pitch, max_grid_bytes, dmax);
 }
 
 template <int MR>
 static void launch_mr(cudaStream_t st, const DevPlan &v, const BatchArgs &B, const float2 *fhat, float2 *f,
-                      int n_tiles, size_t smem, int ctas, int pitch, long long max_grid_bytes, int dmax) {
+                      int n_tiles, size_t smem, int ctas, int pitch, long long max_grid_bytes, int dmax, int prec) {
+    if (prec == ANOVA_PREC_F16) {
+        launch_one<MR, 0, __half2>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax);
+        return;
+    }
+    if (prec == ANOVA_PREC_BF16) {
+        launch_one<MR, 0, __nv_bfloat162>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax);
+        return;
+    }
     switch (pitch) {
-        case 40: launch_one<MR, 40>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax); break;
-        case 72: launch_one<MR, 72>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax); break;
-        default: launch_one<MR, 0>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax); break;
+        case 40: launch_one<MR, 40, float2>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax); break;
+        case 72: launch_one<MR, 72, float2>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax); break;
+        default: launch_one<MR, 0, float2>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax); break;
     }
 }
 
 int gather_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, const float2 *fhat, float2 *f,
-                  int n_tiles, int mr, int pitch, long long max_grid_bytes, int dmax, int sm_count) {
+                  int n_tiles, int mr, int pitch, long long max_grid_bytes, int dmax, int sm_count, int prec) {
     const size_t smem = (size_t)max_grid_bytes * 2 + (size_t)dmax * G2_TILE * 4 + 64;   // + barriers, counters
     if (smem > (size_t)MAX_SMEM) return ANOVA_ERR_UNSUPPORTED;
     if (n_tiles <= 0) return ANOVA_OK;
     const int per_sm = smem * 2 <= (size_t)MAX_SMEM ? 2 : 1;
     const int ctas = std::max(1, std::min(n_tiles, per_sm * sm_count));
     if (mr <= 3)
-        launch_mr<3>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax);
+        launch_mr<3>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax, prec);
     else
-        launch_mr<4>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax);
+        launch_mr<4>(st, v, B, fhat, f, n_tiles, smem, ctas, pitch, max_grid_bytes, dmax, prec);
     return cuda_status(cudaGetLastError());
 }
 
@@ -346,7 +364,8 @@ int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f) {
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s)
         if (p.h_terms[s].mr > 0) mr = p.h_terms[s].mr;
-    return gather_launch(p.stream, v, B, fhat, f, n_tiles, mr, p.pitch2, p.max_grid_bytes, p.d, p.sm_count);
+    return gather_launch(p.stream, v, B, fhat, f, n_tiles, mr, p.pitch2, p.max_grid_bytes, p.d, p.sm_count,
+                         p.precision);
 }
 
 }  // namespace agft

@@ -234,7 +234,8 @@ int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
                    float2 *fhat, int n_items, int *counter, int n_blocks, int mr, long long max_grid_bytes,
-                   int max_fft_elems, int sm_count, long long max_grid_elems, bool any_empty, double2 *scratch);
+                   int max_fft_elems, int sm_count, long long max_grid_elems, bool any_empty, double2 *scratch,
+                   int prec);
 size_t spread_smem_bytes(long long max_grid_bytes);
 // Sorts the nodes by grid cell for every term with sort_slot >= 0 (sort.cu).
 int sort_nodes_by_cell(Plan &p);

@@ -256,7 +256,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
     if (o.precision < ANOVA_PREC_F32 || o.precision > ANOVA_PREC_F64) return ANOVA_ERR_INVALID;
-    if (o.precision != ANOVA_PREC_F32 && o.precision != ANOVA_PREC_F64) return ANOVA_ERR_UNSUPPORTED;   // 16-bit grids
+
     if (o.eps <= 0) o.eps = 1e-5;
     if (o.sigma <= 0) o.sigma = 2.0;
     if (o.sigma < 1.5 || o.sigma > 8) return ANOVA_ERR_INVALID;
@@ -403,9 +403,10 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         T.wr = T.order > 1 ? get_window(T.mr, T.n, T.N) : T.wc;
         T.grid_off = goff;
         long long elems = (long long)T.erows * T.stride;
-        elems = (elems + 1) & ~1LL;   // 16-byte multiple
         const bool f64 = p.precision == ANOVA_PREC_F64;
-        T.grid_bytes = elems * (f64 ? 16 : 8);
+        const bool h16 = p.precision == ANOVA_PREC_F16 || p.precision == ANOVA_PREC_BF16;
+        elems = h16 ? (elems + 3) & ~3LL : (elems + 1) & ~1LL;   // 16-byte multiples
+        T.grid_bytes = elems * (f64 ? 16 : h16 ? 4 : 8);
         goff += elems;
         maxbytes = std::max(maxbytes, T.grid_bytes);
         long long fe = 1;
@@ -488,7 +489,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     chk(cudaMalloc(&p.deconv, sizeof(float) * std::max<size_t>(1, dec.size())));
     chk(cudaMalloc(&p.deconvd, sizeof(double) * std::max<size_t>(1, decd.size())));
     chk(cudaMalloc(&p.empty_off, sizeof(long long) * std::max<size_t>(1, empties.size())));
-    const size_t esize = p.precision == ANOVA_PREC_F64 ? 16 : 8;   // bytes per complex grid element
+    const size_t esize = p.precision == ANOVA_PREC_F64 ? 16 : (p.precision == ANOVA_PREC_F32 ? 8 : 4);   // bytes per grid element
     chk(cudaMalloc(&p.grids, (size_t)std::max<long long>(1, p.grid_elems) * esize));
     chk(cudaMalloc(&p.err, sizeof(int) * 4));
     chk(cudaMalloc(&p.act, sizeof(int) * std::max(1, p.n_terms)));

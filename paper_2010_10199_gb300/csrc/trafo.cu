@@ -23,14 +23,17 @@ __device__ __forceinline__ int freq_index(int q, int N) { return q < N / 2 ? q -
 
 // ------------------------------------------------------------ pre-pass ----
 
-__global__ void trafo_pre_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base) {
+// grids stored as G (FP32 complex, or a pair of 16-bit floats rounded from the FP32 FFT)
+template <typename G>
+__device__ __forceinline__ void trafo_pre_body(const DevPlan &single, const BatchArgs &B,
+                                               const float2 *__restrict__ fhat_base) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int pb = B.plans ? B.blk_prob[blockIdx.x] : 0;
     const DevPlan &P = B.plans ? B.plans[pb] : single;
     const int sblk = B.plans ? (int)blockIdx.x - B.blk0[pb] : (int)blockIdx.x;
     if (P.skip && *P.skip) return;
     const float2 *fhat = fhat_base + P.vec_coef_off;
-    float2 *grids = (float2 *)P.grids;
+    G *grids = (G *)P.grids;
     const Term T = P.terms[P.act[sblk]];
     const int n = T.n, s = T.order, N = T.N;
     int fe = n;
@@ -141,7 +144,7 @@ __global__ void trafo_pre_f32(DevPlan single, BatchArgs B, const float2 *__restr
         inner *= n;
     }
     // store with halos
-    float2 *g = grids + T.grid_off;
+    G *g = grids + T.grid_off;
     const int ecols = T.stride;
     const long long total = (long long)T.erows * ecols;
     for (long long e = threadIdx.x; e < total; e += blockDim.x) {
@@ -156,8 +159,18 @@ __global__ void trafo_pre_f32(DevPlan single, BatchArgs B, const float2 *__restr
         } else {
             if (ec < n) v = cur[er * n + ec];
         }
-        g[e] = v;
+        g[e] = GridEl<G>::store(v.x, v.y);
     }
+}
+
+__global__ void trafo_pre_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base) {
+    trafo_pre_body<float2>(single, B, fhat_base);
+}
+__global__ void trafo_pre_f16(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base) {
+    trafo_pre_body<__half2>(single, B, fhat_base);
+}
+__global__ void trafo_pre_bf16(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base) {
+    trafo_pre_body<__nv_bfloat162>(single, B, fhat_base);
 }
 
 // ------------------------------------------------------- empty plan case --
@@ -186,12 +199,15 @@ int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f) {
     static bool attr_done = false;
     if (!attr_done) {
         cudaFuncSetAttribute(trafo_pre_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(trafo_pre_f16, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(trafo_pre_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_done = true;
     }
     stage_begin(p, ST_PRE);
     BatchArgs B;
     std::memset(&B, 0, sizeof(B));
-    trafo_pre_f32<<<p.n_act, 256, pre_smem, p.stream>>>(v, B, fhat);
+    auto pre = p.precision == ANOVA_PREC_F16 ? trafo_pre_f16 : p.precision == ANOVA_PREC_BF16 ? trafo_pre_bf16 : trafo_pre_f32;
+    pre<<<p.n_act, 256, pre_smem, p.stream>>>(v, B, fhat);
     stage_end(p, ST_PRE);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);

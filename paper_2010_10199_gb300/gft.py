@@ -56,6 +56,15 @@ class ScreenStats(ctypes.Structure):
 N_SCREEN_FEATURES = 7
 
 
+class TuneTrial(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("window_m_row", ctypes.c_int), ("n_ctas", ctypes.c_int),
+                ("node_sort", ctypes.c_int), ("ms_pair", ctypes.c_double), ("est_error", ctypes.c_double),
+                ("chosen", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def library_path() -> str:
     return LIB_PATH
 
@@ -120,6 +129,10 @@ def load(path: str | None = None):
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, vp,
                                         ctypes.POINTER(SolveInfo), ctypes.POINTER(ScreenStats)]
     lib.fista_screened_path.restype = ctypes.c_int
+    lib.anova_plan_autotune.argtypes = [ctypes.POINTER(PlanOptions), ctypes.c_int, ctypes.c_int64, vp, ctypes.c_int,
+                                        i32p, i32p, ctypes.c_double, ctypes.c_int, ctypes.POINTER(TuneTrial),
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
+    lib.anova_plan_autotune.restype = ctypes.c_int
     lib.anova_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(i32p), ctypes.POINTER(i32p), ctypes.POINTER(PlanOptions), vp]
@@ -174,6 +187,33 @@ def anova_plan_create(d, M, x_ptr, term_dims, bandwidth, opts: PlanOptions | Non
                                ctypes.byref(opts) if opts is not None else None, ctypes.c_void_p(int(stream) or None))
     _check("anova_plan_create", rc)
     return h
+
+
+def autotune(x, terms, bandwidths, eps: float = 1e-5, reps: int = 3, stream=None):
+    """Plan options chosen by anova_plan_autotune for FP32 node tensor x [d, M];
+    returns (options dict for Plan(...), list of trial dicts)."""
+    import torch
+    x = x.to(torch.float32).contiguous()
+    d, M = int(x.shape[0]), int(x.shape[1])
+    n = len(terms)
+    td = (ctypes.c_int32 * (3 * n))()
+    bw = (ctypes.c_int32 * n)()
+    for i, u in enumerate(terms):
+        u = tuple(int(c) for c in u)
+        for j in range(3):
+            td[3 * i + j] = u[j] if j < len(u) else -1
+        bw[i] = int(bandwidths[i]) if len(u) else 0
+    opts = PlanOptions(precision=PREC_F32, eps=0.0, window_m_col=0, window_m_row=0, sigma=0.0, n_ctas=0,
+                       node_sort=0)
+    trials = (TuneTrial * 32)()
+    nt = ctypes.c_int(0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = load().anova_plan_autotune(ctypes.byref(opts), d, M, ctypes.c_void_p(x.data_ptr()), n, td, bw, float(eps),
+                                    int(reps), trials, 32, ctypes.byref(nt), ctypes.c_void_p(st.cuda_stream or None))
+    _check("anova_plan_autotune", rc)
+    chosen = {"sigma": opts.sigma, "window_m_row": opts.window_m_row, "n_ctas": opts.n_ctas,
+              "node_sort": opts.node_sort}
+    return chosen, [trials[i].as_dict() for i in range(nt.value)]
 
 
 def anova_plan_destroy(h):
