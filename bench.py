@@ -18,6 +18,10 @@ path).  ``--mode lambda-path`` runs the group-lasso lambda path of the d = 30
 workload three ways -- FP32 with the learned group screen, FP32 on all groups,
 FP64 on all groups -- and prints one JSON line with their times, iteration
 counts and the agreement of the screened FP32 path with the FP64 path.
+``--mode batch`` times 64 independent problems of uneven size (transform pairs
+and 30 LSQR iterations) in one launch per kernel against the same problems
+run one plan after the other.  ``--mode lsqr-path`` times the Tikhonov LSQR
+lambda path of the d = 10, |u| <= 3 workload.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
 torch.distributed.run, every rank runs an independent replica (the transform
@@ -50,17 +54,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--M", type=int, default=1_000_000)
+    ap.add_argument("--M", type=int, default=0, help="nodes (0: the mode's workload size)")
     ap.add_argument("--cpu-sample", type=int, default=20000, help="nodes in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--mode", default="pairs", choices=["pairs", "lambda-path"])
+    ap.add_argument("--mode", default="pairs", choices=["pairs", "lambda-path", "batch", "lsqr-path"])
     ap.add_argument("--lambdas", type=int, default=20, help="lambda-path mode: first K values of the path")
     ap.add_argument("--max-it", type=int, default=5000, help="lambda-path mode: FISTA iterations per lambda")
-    ap.add_argument("--tol", type=float, default=1e-8, help="lambda-path mode: FISTA relative-change stop")
+    ap.add_argument("--tol", type=float, default=1e-6, help="lambda-path mode: FISTA relative-change stop")
     ap.add_argument("--skip-f64", action="store_true", help="lambda-path mode: leave out the FP64 path")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.M <= 0:
+        a.M = {"pairs": 1_000_000, "lambda-path": 2_000_000, "lsqr-path": 500_000}.get(a.mode, 1_000_000)
+    if a.mode == "lsqr-path" and a.max_it == 5000:
+        a.max_it = 300
+    return a
 
 
 # ---------------------------------------------------------------- clocks ---
@@ -294,7 +303,8 @@ def run_mine(args, rank, world, local_rank):
     clk_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     smem_peak = 152 * 128 * clk_mhz * 1e6 / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "traffic_gbs": None if traffic is None else traffic / (kms / 1e3) / 1e9, "kernel": kname,
             "kernel_ms": kms, "alg_bytes_per_launch": alg_bytes, "peak_source": peak_kind,
             "onchip": {"bound": "smem", "achieved": smem_bytes / (kms / 1e3) / 1e9, "peak": smem_peak,
                        "unit": "GB/s", "frac": smem_bytes / (kms / 1e3) / 1e9 / smem_peak,
@@ -442,6 +452,110 @@ def run_lambda_path(args, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batch ---
+
+def run_batch(args, local_rank):
+    """64 problems, M log-uniform in [1e4, 2e5], d in 5..15, |u| <= 2: one
+    launch per kernel for all of them vs one plan after the other."""
+    import numpy as np
+    import torch
+
+    from paper_2010_10199_gb300 import build as cuda_build
+    from paper_2010_10199_gb300 import gft, inputs
+
+    cuda_build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    probs = inputs.c5_batched(64)
+    xs = [torch.from_numpy(w["x"].astype(np.float32)).to(dev) for w in probs]
+    B = gft.Batch(xs, [w["terms"] for w in probs], [w["bandwidths"] for w in probs])
+    plans = [gft.Plan(x, w["terms"], w["bandwidths"]) for x, w in zip(xs, probs)]
+    fh = [inputs.decaying_coefficients(7 + i, w["terms"], w["bandwidths"]) for i, w in enumerate(probs)]
+    fh_all = torch.from_numpy(np.concatenate(fh).astype(np.complex64)).to(dev)
+    y_all = torch.from_numpy(np.concatenate([w["y"] for w in probs]).astype(np.complex64)).to(dev)
+    fh_p = [fh_all[B.coef_off[p]:B.coef_off[p + 1]] for p in range(64)]
+    y_p = [y_all[B.node_off[p]:B.node_off[p + 1]] for p in range(64)]
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps / 1e3
+
+    def batched_pair():
+        B.trafo(fh_all)
+        B.adjoint(y_all)
+
+    def sequential_pair():
+        for p in range(64):
+            plans[p].trafo(fh_p[p])
+            plans[p].adjoint(y_p[p])
+
+    t_bp = timed(batched_pair, args.steps)
+    t_sp = timed(sequential_pair, args.steps)
+
+    def batched_lsqr():
+        B.lsqr(y_all, 1e-3, max_it=30)
+
+    def sequential_lsqr():
+        for p in range(64):
+            plans[p].lsqr(y_p[p], 1e-3, max_it=30)
+
+    t_bl = timed(batched_lsqr, max(1, args.steps // 3))
+    t_sl = timed(sequential_lsqr, max(1, args.steps // 3))
+    Ms = [w["M"] for w in probs]
+    line = {"metric": "many problems in one launch: sequential time / batched time", "value": t_sl / t_bl,
+            "unit": "x", "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": f"64 problems, M {min(Ms)}..{max(Ms)} (total {sum(Ms)}), d 5..15, |u|<=2, "
+                                   "N=32 (1D) / 16x16 (2D)", "lsqr": "lambda 1e-3, 30 iterations"},
+            "results": {"batched_pair_s": t_bp, "sequential_pair_s": t_sp, "pair_speedup": t_sp / t_bp,
+                        "batched_lsqr_s": t_bl, "sequential_lsqr_s": t_sl, "lsqr_speedup": t_sl / t_bl}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- lsqr path ---
+
+def run_lsqr_path(args, local_rank):
+    """Tikhonov LSQR over 10 lambda values (1e0 .. 1e-4) on d = 10, |u| <= 3
+    (176 terms, N = 100 / 24x24 / 10x10x10), M = 5e5 Beta(2,2) nodes."""
+    import numpy as np
+    import torch
+
+    from paper_2010_10199_gb300 import build as cuda_build
+    from paper_2010_10199_gb300 import gft, inputs
+
+    cuda_build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = inputs.c3_lsqr(M=args.M)
+    P = gft.Plan(torch.from_numpy(w["x"].astype(np.float32)).to(dev), w["terms"], w["bandwidths"])
+    y = torch.from_numpy(w["y"].astype(np.complex64)).to(dev)
+    P.lsqr(y, float(w["lambdas"][0]), max_it=5)   # warm-up (graph capture, workspaces)
+    per = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for lam in w["lambdas"]:
+        fh, info, rc = P.lsqr(y, float(lam), max_it=args.max_it, atol=1e-6, btol=1e-6)
+        per.append({"lambda": float(lam), "iterations": info["iterations"], "seconds": info["seconds"],
+                    "rnorm": info["rnorm"], "status": rc})
+    torch.cuda.synchronize()
+    total = time.perf_counter() - t0
+    its = sum(q["iterations"] for q in per)
+    line = {"metric": "LSQR lambda-path time (10 lambda values)", "value": total, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32 vectors, f64 scalars",
+            "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": f"d=10, |u|<=3 (176 terms), N=100 / 24x24 / 10x10x10, M={args.M} Beta(2,2) nodes",
+                       "lsqr": f"atol = btol = 1e-6, at most {args.max_it} iterations per lambda, graph-replayed"},
+            "results": {"iterations": its, "ms_per_iteration": 1e3 * total / max(its, 1), "per_lambda": per}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -459,6 +573,12 @@ def main():
     elif args.mode == "lambda-path":
         if rank == 0:
             run_lambda_path(args, local_rank)
+    elif args.mode == "batch":
+        if rank == 0:
+            run_batch(args, local_rank)
+    elif args.mode == "lsqr-path":
+        if rank == 0:
+            run_lsqr_path(args, local_rank)
     else:
         run_mine(args, rank, world, local_rank)
     if world > 1:

@@ -264,7 +264,7 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
         v.vec_node_off = b->node_off[p];
         v.vec_coef_off = b->coef_off[p];
         b->views.push_back(v);
-        const int tiles = (int)((pl.M + 127) / 128);
+        const int tiles = (int)((pl.M + GATHER_TILE - 1) / GATHER_TILE);
         tile0.push_back(b->n_tiles);
         for (int t = 0; t < tiles; ++t) tile_prob.push_back(p);
         b->n_tiles += tiles;

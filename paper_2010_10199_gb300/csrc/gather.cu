@@ -30,6 +30,7 @@ constexpr int G2_WARPS = G2_THREADS / 32;
 constexpr int G2_PTS = 8;                              // nodes per half-warp
 constexpr int G2_TILE = (G2_THREADS / 16) * G2_PTS;    // 128 nodes per CTA tile
 static_assert(G2_PTS == 8, "coordinate loads read a half-warp's nodes as two float4");
+static_assert(G2_TILE == GATHER_TILE, "tile size shared with the batch tables");
 
 // Problem of a tile and the number of its terms still to run (0 when the
 // problem's skip flag is set).

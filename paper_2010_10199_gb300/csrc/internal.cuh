@@ -21,9 +21,7 @@ namespace agft {
 constexpr int MAX_ORDER = 3;
 constexpr int MAXM = 8;          // largest window half-width
 constexpr int NCOEF = 8;         // coefficients of the per-tap polynomial (degree 7)
-constexpr int GATHER_THREADS = 256;
-constexpr int PTS_PER_HALF = 16; // points per half-warp in the gather tile
-constexpr int GATHER_TILE = (GATHER_THREADS / 16) * PTS_PER_HALF;  // 256 points
+constexpr int GATHER_TILE = 128;   // nodes per gather tile (gather.cu)
 constexpr int SPREAD_THREADS = 256;
 constexpr int SPREAD_MAX_CTAS_PER_SM = 4;
 constexpr int SPREAD_MAX_K = 64;     // largest number of node chunks (partial grids) per term
@@ -251,6 +249,7 @@ int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid
 // Appends the spread work items of one problem: active terms of higher order
 // first (they cost more), K chunks each.
 int append_spread_items(const Plan &p, int prob, int K, int4 *out);
+int lipschitz_estimate(Plan &p, double *L);
 int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas, int n_lambda, int max_it,
                double tol, int step_mode, double L0, double eta, const uint8_t *mask, const float2 *f0,
                float2 *path, anova_solve_info *info, double *L_out);

@@ -207,6 +207,10 @@ int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, c
         e = cudaStreamSynchronize(p.stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
+    // a step bound for the whole path: ||F_S||^2 <= ||F||^2 for every group set S
+    double Lpath = 0.0;
+    rc = lipschitz_estimate(p, &Lpath);
+    if (rc) return rc;
     double lam_prev = lambdas[ord[0]];
     std::vector<double> pairs;
     std::vector<float> prob(G);
@@ -242,8 +246,13 @@ int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, c
         anova_solve_info I;
         int rounds = 0, readmitted = 0;
         for (; rounds < 16; ++rounds) {
+            // a small proposal gets its own (smaller, cheap to estimate) step bound;
+            // a large one the path's bound, which costs no extra transforms
+            int prop_terms = 0;
+            for (int u = 0; u < G; ++u) prop_terms += mask[u] && p.h_user_order[u] > 0;
+            const double L0 = 4 * prop_terms <= p.n_terms ? 0.0 : Lpath;
             double L = 0.0;
-            rc = fista_impl(p, y, w_dev, &lam, 1, max_it, tol, 0, 0.0, 2.0, mask.data(), S.fprev,
+            rc = fista_impl(p, y, w_dev, &lam, 1, max_it, tol, 0, L0, 2.0, mask.data(), S.fprev,
                             path + (long long)idx * n, &I, &L);
             if (rc) return rc;
             int act_terms = 0;

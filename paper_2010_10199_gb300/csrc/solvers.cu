@@ -510,6 +510,24 @@ int fista_impl_t(Plan &p, const C *y, const double *w, const double *lambdas, in
     return set_active_terms(p, nullptr);
 }
 
+// 1.05 x the power-iteration estimate of ||F||^2 over all terms (FP32 plans):
+// a valid FISTA step bound for the full problem and for every group-masked one
+int lipschitz_estimate(Plan &p, double *L) {
+    int rc;
+    SolverWork *W = get_work(p, rc);
+    if (!W) return rc;
+    rc = set_active_terms(p, nullptr);
+    if (rc) return rc;
+    double est = 0.0;
+    {
+        StreamScope scope(p, W);
+        rc = power_estimate<float2>(p, W, 300, false, &est);
+    }
+    if (rc) return rc;
+    *L = est > 0 ? 1.05 * est : 1.0;
+    return cuda_status(cudaStreamSynchronize(p.stream));
+}
+
 int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas, int n_lambda, int max_it,
                double tol, int step_mode, double L0, double eta, const uint8_t *mask, const float2 *f0,
                float2 *path, anova_solve_info *info, double *L_out) {

@@ -5,8 +5,8 @@
 //      n^{|u|} grid (the extension before eq. (somafm)), multiply by the
 //      deconvolution factors, run the oversampled FFT (sign +) in shared
 //      memory and store the grid with its halos.
-//   2. gather: all terms fused, point-major.  A CTA owns a tile of 256 nodes;
-//      each half-warp owns 16 nodes and evaluates them one at a time with its
+//   2. gather: all terms fused, point-major.  A CTA owns a tile of 128 nodes;
+//      each half-warp owns 8 nodes and evaluates them one at a time with its
 //      16 lanes = 2 rows x 8 columns of the window, reading the term's grid from
 //      shared memory (double-buffered bulk async copies from L2).  Lanes keep
 //      per-node partial sums over all terms in registers; one transposed
