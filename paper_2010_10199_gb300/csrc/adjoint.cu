@@ -312,28 +312,46 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
                 red_add(base + 1, q.w * cw);
             }
         } else {
-            const Window &W = P.windows[T.wr];
-            const int mr = T.mr, mc = T.mc;
-            const int hw = warp * 2 + half;
-            for (int i = hw; i < cnt; i += SPREAD_THREADS / 16) {
-                const float4 q = stg[i];
+            // order 3: rows wrap modulo n; row weights from the per-tap
+            // polynomials, lane (0, k) the first row coordinate's tap k, lane
+            // (1, k) the second's, handed round by shuffles (the whole warp
+            // iterates together; a half-warp past the end adds nothing)
+            float rcf[NCOEF];
+            {
+                const float *src = P.windows[T.wr].c[min(k, 2 * MR - 1)];
+#pragma unroll
+                for (int q = 0; q < NCOEF; ++q) rcf[q] = __ldg(src + q);
+            }
+            const int mc = T.mc;
+            for (int i0 = 2 * warp; i0 < cnt; i0 += 2 * NW) {
+                const int i = i0 + half;
+                const bool ok = i < cnt;
+                const int ii = ok ? i : i0;
+                const float4 q = stg[ii];
                 float ta, tb, tc;
                 const int fa = grid_pos(q.x, n, ta);
-                const int fb = grid_pos(__ldg(xr1 + a + i), n, tb);
+                const int fb = grid_pos(__ldg(xr1 + a + ii), n, tb);
                 const int fc = grid_pos(q.y, n, tc);
                 const float cw = horner8(wcf, 2.f * tc - 1.f);
+                const float wrow = horner8(rcf, r ? 2.f * tb - 1.f : 2.f * ta - 1.f);
+                float wa[2 * MR], wb[MR];
+#pragma unroll
+                for (int t = 0; t < 2 * MR; ++t) wa[t] = __shfl_sync(0xffffffffu, wrow, (half << 4) | t);
+#pragma unroll
+                for (int j = 0; j < MR; ++j) wb[j] = __shfl_sync(0xffffffffu, wrow, (half << 4) | 8 | (r + 2 * j));
+                if (!ok) continue;
                 const int cidx = wrap(fc - mc + 1 + k, n);
                 const float yx = q.z * cw, yy = q.w * cw;
-                for (int ia = 0; ia < 2 * mr; ++ia) {
-                    const float wa = kb_direct(ta + (float)(mr - 1 - ia), mr, W.b, W.inv_psi0);
-                    const int ra = wrap(fa - mr + 1 + ia, n);
-                    for (int jb = r; jb < 2 * mr; jb += 2) {
-                        const float wb = kb_direct(tb + (float)(mr - 1 - jb), mr, W.b, W.inv_psi0);
-                        const int rb = wrap(fb - mr + 1 + jb, n);
-                        float *cp = (float *)(S + (ra * n + rb) * stride + cidx);
-                        const float w = wa * wb;
-                        red_add(cp, yx * w);
-                        red_add(cp + 1, yy * w);
+#pragma unroll
+                for (int ia = 0; ia < 2 * MR; ++ia) {
+                    const int row = wrap(fa - MR + 1 + ia, n) * n;
+                    const float ax = yx * wa[ia], ay = yy * wa[ia];
+#pragma unroll
+                    for (int j = 0; j < MR; ++j) {
+                        const int rbj = wrap(fb - MR + 1 + r + 2 * j, n);
+                        float *cp = (float *)(S + (row + rbj) * stride + cidx);
+                        red_add(cp, ax * wb[j]);
+                        red_add(cp + 1, ay * wb[j]);
                     }
                 }
             }

@@ -240,13 +240,22 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
                     ay[i + 1] += r ? vy : 0.f;
                 }
             } else {
-                // order 3: rows (first, second) wrap modulo n; row weights evaluated directly
+                // order 3: rows (first, second) wrap modulo n.  The row weights
+                // come from the per-tap polynomials: lane (0, k) evaluates tap k of
+                // the first row coordinate, lane (1, k) tap k of the second, and
+                // shuffles hand them round (all 2 MR first-row taps, rows r, r+2, ..
+                // of the second).
                 const Term &T = D.terms[R.term];
-                const Window &W = D.windows[R.wr];
-                const int mr = T.mr, mc = T.mc, stride = T.stride;
+                const int stride = T.stride;
                 const float *xa_p = xs + T.row0 * G2_TILE + pbase;
                 const float *xb_p = xs + T.row1 * G2_TILE + pbase;
                 const G *Gs = sm2 + boff;
+                float rcf[NCOEF];
+                {
+                    const float *src = D.windows[R.wr].c[min(k, 2 * MR - 1)];
+#pragma unroll
+                    for (int q = 0; q < NCOEF; ++q) rcf[q] = __ldg(src + q);
+                }
 #pragma unroll
                 for (int i = 0; i < G2_PTS; ++i) {
                     float ta, tb, tc;
@@ -254,19 +263,30 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
                     const int fb = grid_pos(xb_p[i], n, tb);
                     const int fc = grid_pos(xc[i], n, tc);
                     const float cw = horner8(cc, 2.f * tc - 1.f);
-                    const int cidx = wrap(fc - mc + 1 + k, n);
+                    const float wrow = horner8(rcf, r ? 2.f * tb - 1.f : 2.f * ta - 1.f);
+                    float wa[2 * MR], wb[MR];
+                    int rb[MR];
+#pragma unroll
+                    for (int q = 0; q < 2 * MR; ++q) wa[q] = __shfl_sync(0xffffffffu, wrow, (half << 4) | q);
+#pragma unroll
+                    for (int j = 0; j < MR; ++j) {
+                        wb[j] = __shfl_sync(0xffffffffu, wrow, (half << 4) | 8 | (r + 2 * j));
+                        rb[j] = wrap(fb - MR + 1 + r + 2 * j, n);
+                    }
+                    const int cidx = wrap(fc - T.mc + 1 + k, n);
                     float sx = 0.f, sy = 0.f;
-                    for (int ia = 0; ia < 2 * mr; ++ia) {
-                        const float wa = kb_direct(ta + (float)(mr - 1 - ia), mr, W.b, W.inv_psi0);
-                        const int ra = wrap(fa - mr + 1 + ia, n);
-                        for (int jb = r; jb < 2 * mr; jb += 2) {
-                            const float wb = kb_direct(tb + (float)(mr - 1 - jb), mr, W.b, W.inv_psi0);
-                            const int rb = wrap(fb - mr + 1 + jb, n);
-                            const float2 v = GridEl<G>::load(Gs[(ra * n + rb) * stride + cidx]);
-                            const float w = wa * wb;
-                            sx = fmaf(w, v.x, sx);
-                            sy = fmaf(w, v.y, sy);
+#pragma unroll
+                    for (int ia = 0; ia < 2 * MR; ++ia) {
+                        const int row = wrap(fa - MR + 1 + ia, n) * n;
+                        float tx = 0.f, ty = 0.f;
+#pragma unroll
+                        for (int j = 0; j < MR; ++j) {
+                            const float2 v = GridEl<G>::load(Gs[(row + rb[j]) * stride + cidx]);
+                            tx = fmaf(wb[j], v.x, tx);
+                            ty = fmaf(wb[j], v.y, ty);
                         }
+                        sx = fmaf(wa[ia], tx, sx);
+                        sy = fmaf(wa[ia], ty, sy);
                     }
                     ax[i] = fmaf(cw, sx, ax[i]);
                     ay[i] = fmaf(cw, sy, ay[i]);
