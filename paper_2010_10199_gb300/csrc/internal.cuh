@@ -181,6 +181,8 @@ struct Plan {
     // active term list (all scheduled terms unless a group mask restricts it)
     int *act;
     ActRec *act_rec;
+    ActRec *act_rec3;       // the active third-order terms alone (point-major gather of the sorted forward)
+    int n_act3;
     int n_act;
     int *h_act;
     const int *skip;        // device flag read by every transform kernel (or null)
@@ -193,6 +195,8 @@ struct Plan {
     int *counter;           // work-queue counter of the spread
     float4 *srec;           // cell-sorted node records (null: none), n_sorted slots of M
     int n_sorted;
+    unsigned long long *facc;   // sorted forward: fixed-point accumulators [M][2]
+    int *fexp;              // and their exponent
     // FP64 plans: window weights per (window, coordinate) slot and node, the
     // precomputed form of psi (taps 0..2m-1, zero padded to 8), and the first
     // tap's grid index floor(n x + n/2) in [0, n)
@@ -229,6 +233,9 @@ enum { ST_PRE = 0, ST_GATHER = 1, ST_SPREAD = 2, ST_REDUCE = 3, ST_POST = 4, ST_
 // kernels launched by the entry points (trafo.cu / adjoint.cu)
 int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f);
+// Sorted forward (gather_sorted.cu): order-1/2 terms over the cell-sorted
+// records, accumulated into f with atomics; f must hold the other terms' sum.
+int launch_gather_sorted_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
                    float2 *fhat, int n_items, int *counter, int n_blocks, int mr, long long max_grid_bytes,

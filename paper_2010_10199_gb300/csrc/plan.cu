@@ -146,8 +146,9 @@ __global__ void wrap_nodes_f64(const double *in, double *out, long long total) {
 // `user_mask` (all when null), with the row-group flags recomputed for that
 // list.  Uploaded on the plan's stream.
 int set_active_terms(Plan &p, const unsigned char *user_mask) {
-    static thread_local std::vector<ActRec> recs;
+    static thread_local std::vector<ActRec> recs, recs3;
     recs.clear();
+    recs3.clear();
     int n = 0;
     for (int s = 0; s < p.n_terms; ++s) {
         const Term &T = p.h_terms[s];
@@ -158,9 +159,11 @@ int set_active_terms(Plan &p, const unsigned char *user_mask) {
             if (P.order == 2 && P.row0 == T.row0 && P.wr == T.wr && P.n == T.n) ng = 0;
         }
         recs.push_back(make_act_rec(T, s, ng));
+        if (T.order == 3) recs3.push_back(make_act_rec(T, s, 1));
         p.h_act[n++] = s;
     }
     p.n_act = n;
+    p.n_act3 = (int)recs3.size();
     p.n_items = 0;
     if (n == 0) return ANOVA_OK;
     p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count);
@@ -170,6 +173,8 @@ int set_active_terms(Plan &p, const unsigned char *user_mask) {
         e = cudaMemcpyAsync(p.act_rec, recs.data(), sizeof(ActRec) * n, cudaMemcpyHostToDevice, p.stream);
     if (e == cudaSuccess && p.n_items)
         e = cudaMemcpyAsync(p.items, p.h_items, sizeof(int4) * p.n_items, cudaMemcpyHostToDevice, p.stream);
+    if (e == cudaSuccess && p.n_act3 && p.act_rec3)
+        e = cudaMemcpyAsync(p.act_rec3, recs3.data(), sizeof(ActRec) * p.n_act3, cudaMemcpyHostToDevice, p.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);   // recs is reused by the next call
     return cuda_status(e);
 }
@@ -208,7 +213,8 @@ static void free_plan(Plan &p) {
     if (p.solver && p.solver_free) p.solver_free(p.solver);
     p.solver = nullptr;
     void *bufs[] = {p.x, p.terms, p.windows, p.deconv, p.deconvd, p.empty_off, p.grids, p.partials,
-                    p.err, p.scratch, p.act, p.act_rec, p.items, p.counter, p.srec, p.wt64, p.wb64, p.slots64};
+                    p.err, p.scratch, p.act, p.act_rec, p.act_rec3, p.items, p.counter, p.srec, p.wt64, p.wb64, p.slots64,
+                    p.facc, p.fexp};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete[] p.h_terms;
@@ -494,6 +500,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     chk(cudaMalloc(&p.err, sizeof(int) * 4));
     chk(cudaMalloc(&p.act, sizeof(int) * std::max(1, p.n_terms)));
     chk(cudaMalloc(&p.act_rec, sizeof(ActRec) * std::max(1, p.n_terms)));
+    chk(cudaMalloc(&p.act_rec3, sizeof(ActRec) * std::max(1, p.n_terms)));
     p.h_act = new int[std::max(1, p.n_terms)];
     // adjoint partial grids: one per node chunk of a term (work items of the
     // spread are (term, chunk) pairs), bounded to 8 GB
@@ -532,6 +539,14 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
                 for (int s = 0; s < p.n_terms; ++s)
                     if (p.h_terms[s].order <= 2) p.h_terms[s].sort_slot = slot++;
                 p.n_sorted = ns;
+                if (p.precision == ANOVA_PREC_F32) {
+                    if (cudaMalloc(&p.facc, sizeof(unsigned long long) * 2 * (size_t)M) != cudaSuccess ||
+                        cudaMalloc(&p.fexp, sizeof(int) * 4) != cudaSuccess) {
+                        cudaGetLastError();   // the forward falls back to the point-major gather
+                        if (p.facc) cudaFree(p.facc);
+                        p.facc = nullptr;
+                    }
+                }
             } else {
                 cudaGetLastError();
                 p.srec = nullptr;
