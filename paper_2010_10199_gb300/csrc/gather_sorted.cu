@@ -31,11 +31,14 @@ __device__ __forceinline__ void red_add_u64(unsigned long long *addr, long long 
 
 // fixed-point exponent e for the accumulators: 2^e * 2 sum |fhat| <= 2^62
 // (every partial sum of a node's terms is bounded by sum_k |fhat_k| up to the
-// window error), clamped so that 2^e stays a normal float
-__global__ void k_fixed_point_exponent(const float2 *__restrict__ fhat, long long n, int *e_out) {
+// window error), clamped so that 2^e stays a normal float.  Two passes with
+// a fixed block count, so the sum (and e) never depends on timing.
+constexpr int FPE_BLOCKS = 128;
+
+__global__ void k_fixed_point_partial(const float2 *__restrict__ fhat, long long n, double *part) {
     __shared__ double sh[32];
     double a = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float2 v = fhat[i];
         a += fabs((double)v.x) + fabs((double)v.y);
     }
@@ -45,10 +48,17 @@ __global__ void k_fixed_point_exponent(const float2 *__restrict__ fhat, long lon
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-        int e = 100;
-        if (s > 0) e = 61 - (int)ceil(log2(s));
-        *e_out = max(-100, min(100, e));
+        part[blockIdx.x] = s;
     }
+}
+
+__global__ void k_fixed_point_exponent(const double *part, int *e_out) {
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < FPE_BLOCKS; ++b) s += part[b];
+    int e = 100;
+    if (s > 0) e = 61 - (int)ceil(log2(s));
+    *e_out = max(-100, min(100, e));
 }
 
 // f[j] += acc[j] * 2^-e
@@ -176,7 +186,9 @@ gather_sorted_f32(DevPlan P, const int4 *__restrict__ items, unsigned long long 
 
 int launch_gather_sorted_f32(Plan &p, const float2 *fhat, float2 *f) {
     DevPlan v = dev_view(p);
-    k_fixed_point_exponent<<<1, 1024, 0, p.stream>>>(fhat, p.n_coeffs, p.fexp);
+    double *part = (double *)p.scratch;   // FPE_BLOCKS partial sums
+    k_fixed_point_partial<<<FPE_BLOCKS, 256, 0, p.stream>>>(fhat, p.n_coeffs, part);
+    k_fixed_point_exponent<<<1, 32, 0, p.stream>>>(part, p.fexp);
     cudaMemsetAsync(p.facc, 0, sizeof(unsigned long long) * 2 * p.M, p.stream);
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s)
