@@ -302,13 +302,43 @@ static int lsqr_impl(Plan &p, const C *y, const double *w, double lambda, int ma
     return h.stop == 1 ? ANOVA_ERR_BREAKDOWN : ANOVA_OK;
 }
 
-// power iteration for ||F||^2 on the active terms (30 steps, FP64 Rayleigh quotient)
+// largest eigenvalue of the symmetric tridiagonal matrix (diag d, off-diagonal
+// e) by bisection on the Sturm count
+static double tridiag_max_eig(const std::vector<double> &d, const std::vector<double> &e) {
+    const int k = (int)d.size();
+    double lo = 0.0, hi = 0.0;
+    for (int i = 0; i < k; ++i) {
+        const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(e[i]) : 0.0);
+        hi = std::max(hi, d[i] + r);
+    }
+    auto count_below = [&](double x) {   // eigenvalues < x
+        int c = 0;
+        double q = 1.0;
+        for (int i = 0; i < k; ++i) {
+            q = d[i] - x - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
+            if (q == 0.0) q = -1e-300;
+            c += q < 0;
+        }
+        return c;
+    };
+    for (int it = 0; it < 200 && hi - lo > 1e-14 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (count_below(mid) == k) hi = mid; else lo = mid;
+    }
+    return hi;
+}
+
+// ||F||^2 on the active terms (group-masked if asked) from the Golub--Kahan
+// bidiagonalisation F V_k = U_k B_k started at the all-ones vector: the largest
+// Ritz value of B_k^T B_k is a lower bound that converges much faster than the
+// power iteration (Lanczos on F^H F); stop when it changes by < 1e-5 relative
+// or after max_steps steps.  Scalars in FP64.
 template <typename C>
-static int power_estimate(Plan &p, SolverWork *W, int iters, bool masked, double *out) {
+static int lanczos_estimate(Plan &p, SolverWork *W, int max_steps, bool masked, double *out) {
     const Vecs<C> V(W);
     cudaStream_t s = p.stream;
-    const long long n = p.n_coeffs;
-    const int gn = grid_for(n);
+    const long long n = p.n_coeffs, M = p.M;
+    const int gn = grid_for(n), gM = grid_for(M);
     C one;
     one.x = 1;
     one.y = 0;
@@ -318,33 +348,57 @@ static int power_estimate(Plan &p, SolverWork *W, int iters, bool masked, double
     SolverState h0;
     std::memset(&h0, 0, sizeof(h0));
     cudaMemcpyAsync(W->st, &h0, sizeof(h0), cudaMemcpyHostToDevice, s);
+    // v_1 = ones / |ones|  (the norm goes through beta, which is unused otherwise here)
     k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.v, V.v, nullptr, n, W->part);
     finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
+    k_set_norm<<<1, 1, 0, s>>>(W->st, 1);
+    k_normalize<<<gn, 256, 0, s>>>(W->st, V.v, n, 1);
+    // alpha_1 u_1 = F v_1
+    int rc = trafo_c(p, (const C *)V.v, V.uM);
+    if (rc) return rc;
+    k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.uM, V.uM, nullptr, M, W->part);
+    finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
     k_set_norm<<<1, 1, 0, s>>>(W->st, 0);
-    k_normalize<<<gn, 256, 0, s>>>(W->st, V.v, n, 0);
-    double lam = 0.0, prev = -1.0;
-    for (int it = 0; it < iters; ++it) {
-        int rc = trafo_c(p, (const C *)V.v, V.tM);
-        if (rc) return rc;
-        rc = adjoint_c(p, (const C *)V.tM, V.tn);
-        if (rc) return rc;
-        if (masked) k_mask_groups<<<p.n_user_terms, 256, 0, s>>>(V.tn, W->goff, W->glen, W->gmask);
-        // ||F v||^2 = <v, F^H F v> with |v| = 1
-        k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.tM, V.tM, nullptr, p.M, W->part);
-        finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
+    k_normalize<<<gM, 256, 0, s>>>(W->st, V.uM, M, 0);
+    std::vector<double> alpha, beta;
+    double est = 0.0, prev = -1.0;
+    for (int it = 0; it < max_steps; ++it) {
         SolverState h;
         cudaMemcpyAsync(&h, W->st, sizeof(h), cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_status(e);
-        lam = h.red[0];
-        if (prev > 0 && std::fabs(lam - prev) <= 1e-5 * lam) break;
-        prev = lam;
-        k_scale_copy<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.v, V.tn, nullptr, n, W->part);
+        alpha.push_back(h.alpha);
+        if (!(h.alpha > 0)) break;
+        // beta_i v_{i+1} = F^H u_i - alpha_i v_i
+        rc = adjoint_c(p, (const C *)V.uM, V.tn);
+        if (rc) return rc;
+        if (masked) k_mask_groups<<<p.n_user_terms, 256, 0, s>>>(V.tn, W->goff, W->glen, W->gmask);
+        k_sub_scaled<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.v, V.tn, nullptr, 0, n, W->part);
+        finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
+        k_set_norm<<<1, 1, 0, s>>>(W->st, 1);
+        k_normalize<<<gn, 256, 0, s>>>(W->st, V.v, n, 1);
+        // alpha_{i+1} u_{i+1} = F v_{i+1} - beta_i u_i
+        rc = trafo_c(p, (const C *)V.v, V.tM);
+        if (rc) return rc;
+        k_sub_scaled<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.uM, V.tM, nullptr, 1, M, W->part);
         finish_sums<<<1, 256, 0, s>>>(W->st, W->part, 1);
         k_set_norm<<<1, 1, 0, s>>>(W->st, 0);
-        k_normalize<<<gn, 256, 0, s>>>(W->st, V.v, n, 0);
+        k_normalize<<<gM, 256, 0, s>>>(W->st, V.uM, M, 0);
+        cudaMemcpyAsync(&h, W->st, sizeof(h), cudaMemcpyDeviceToHost, s);
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_status(e);
+        beta.push_back(h.beta);
+        // T = B^T B for the k x k upper bidiagonal B (alpha on the diagonal, beta above)
+        const int k = (int)alpha.size();
+        std::vector<double> d(k), off(std::max(0, k - 1));
+        for (int i = 0; i < k; ++i) d[i] = alpha[i] * alpha[i] + (i > 0 ? beta[i - 1] * beta[i - 1] : 0.0);
+        for (int i = 0; i + 1 < k; ++i) off[i] = alpha[i] * beta[i];
+        est = tridiag_max_eig(d, off);
+        if (prev > 0 && std::fabs(est - prev) <= 1e-5 * est) break;
+        prev = est;
+        if (!(h.beta > 0)) break;
     }
-    *out = lam;
+    *out = est;
     return cuda_status(cudaGetLastError());
 }
 
@@ -371,7 +425,7 @@ int fista_impl_t(Plan &p, const C *y, const double *w, const double *lambdas, in
     double L = L0;
     if (L <= 0) {
         double est = 0.0;
-        rc = power_estimate<C>(p, W, 300, mask != nullptr, &est);
+        rc = lanczos_estimate<C>(p, W, 60, mask != nullptr, &est);
         if (rc) return rc;
         L = 1.05 * est;
         if (!(L > 0)) L = 1.0;
@@ -510,7 +564,7 @@ int fista_impl_t(Plan &p, const C *y, const double *w, const double *lambdas, in
     return set_active_terms(p, nullptr);
 }
 
-// 1.05 x the power-iteration estimate of ||F||^2 over all terms (FP32 plans):
+// 1.05 x the Lanczos estimate of ||F||^2 over all terms (FP32 plans):
 // a valid FISTA step bound for the full problem and for every group-masked one
 int lipschitz_estimate(Plan &p, double *L) {
     int rc;
@@ -521,7 +575,7 @@ int lipschitz_estimate(Plan &p, double *L) {
     double est = 0.0;
     {
         StreamScope scope(p, W);
-        rc = power_estimate<float2>(p, W, 300, false, &est);
+        rc = lanczos_estimate<float2>(p, W, 60, false, &est);
     }
     if (rc) return rc;
     *L = est > 0 ? 1.05 * est : 1.0;
