@@ -66,9 +66,9 @@ int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid
     return (int)std::max<long long>(1, K);
 }
 
-int append_spread_items(const Plan &p, int prob, int K, int4 *out) {
+int append_spread_items(const Plan &p, int prob, int K, int4 *out, int sel) {
     int n = 0;
-    for (int order = MAX_ORDER; order >= 1; --order)
+    for (int order = sel == 3 ? 3 : 2; order >= (sel == 3 ? 3 : 1); --order)
         for (int s = 0; s < p.n_act; ++s) {
             if (p.h_terms[p.h_act[s]].order != order) continue;
             for (int z = 0; z < K; ++z) out[n++] = make_int4(prob, s, z, K);
@@ -238,11 +238,138 @@ __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term 
     }
 }
 
+// Sorted third-order item: two records per node (window arguments and
+// original index; the cell's grid indices).  The item's nodes are cut into 8
+// runs, one per warp; blocks of 32 nodes per run are staged like the order-2
+// path (records two blocks ahead, y one block ahead).  A warp takes one node
+// at a time: lane (g, k), g = lane / 8, owns column tap k and the row pairs
+// (ia, ib) with ib in {g, g + 4}, keeps their sums for the current cell in
+// registers and adds them to the shared grid (indices modulo n) when the cell
+// changes and at the end of its run.  Lanes 0..7 evaluate the first row
+// coordinate's taps, lanes 8..15 the second's; shuffles hand them round.
+constexpr int SP3_RUN = 32;                     // nodes per warp and block
+constexpr int SP3_BLK = SP3_RUN * (SPREAD_THREADS / 32);
+static_assert(3 * SP3_BLK * 32 + 2 * SP3_BLK * 8 <= SP_STAGE_BYTES, "third-order staging");
+
+template <int MR>
+__device__ __forceinline__ void spread_sorted_item3(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
+                                                    long long j0, long long j1, float2 *S, unsigned char *stg_raw,
+                                                    const float cc[NCOEF]) {
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 3, k = lane & 7;
+    const int n = T.n, stride = T.stride, mc = T.mc;
+    const float4 *src = P.srec + (long long)T.sort_slot * P.M + 2 * j0;
+    float4 *rbuf = (float4 *)stg_raw;                   // [3][SP3_BLK][2]
+    float2 *ybuf = (float2 *)(rbuf + 3 * 2 * SP3_BLK);  // [2][SP3_BLK]
+    float rcf[NCOEF];
+    {
+        const float *c = P.windows[T.wr].c[min(k, 2 * MR - 1)];
+#pragma unroll
+        for (int q = 0; q < NCOEF; ++q) rcf[q] = __ldg(c + q);
+    }
+    const long long len = j1 - j0;
+    const long long L = (len + 7) / 8;   // run length
+    const long long nblk = (L + SP3_RUN - 1) / SP3_RUN;
+    auto run_len = [&](int h) { return max(0LL, min(L, len - (long long)h * L)); };
+    // thread tid stages node t_s of run h_s in every block
+    const int h_s = tid / SP3_RUN, t_s = tid % SP3_RUN;
+    const long long len_s = run_len(h_s);
+    auto stage_a = [&](long long c) {
+        const long long q = c * SP3_RUN + t_s;
+        if (q < len_s) {
+            float4 *d = rbuf + ((int)(c % 3) * SP3_BLK + tid) * 2;
+            const float4 *gsrc = src + 2 * ((long long)h_s * L + q);
+            cp_async16(d, gsrc);
+            cp_async16(d + 1, gsrc + 1);
+        }
+    };
+    auto stage_b = [&](long long c) {   // reads this thread's own staged record
+        if (c * SP3_RUN + t_s < len_s)
+            cp_async8(&ybuf[(int)(c & 1) * SP3_BLK + tid],
+                      y + __float_as_int(rbuf[((int)(c % 3) * SP3_BLK + tid) * 2].w));
+    };
+    const long long my_len = run_len(warp);
+    const bool ib1_ok = g + 4 < 2 * MR;
+    int cfa = -1, cfb = 0, cfc = 0;
+    float ax[2 * MR][2], ay[2 * MR][2];
+#pragma unroll
+    for (int a = 0; a < 2 * MR; ++a) ax[a][0] = ax[a][1] = ay[a][0] = ay[a][1] = 0.f;
+    auto flush = [&]() {
+        const int col = wrap(cfc - mc + 1 + k, n);
+        const int rb0 = wrap(cfb - MR + 1 + g, n), rb1 = wrap(cfb - MR + 1 + g + 4, n);
+#pragma unroll
+        for (int a = 0; a < 2 * MR; ++a) {
+            const int ra = wrap(cfa - MR + 1 + a, n) * n;
+            if (g < 2 * MR) {
+                float *cp = (float *)(S + (ra + rb0) * stride + col);
+                red_add(cp, ax[a][0]);
+                red_add(cp + 1, ay[a][0]);
+            }
+            if (ib1_ok) {
+                float *cp = (float *)(S + (ra + rb1) * stride + col);
+                red_add(cp, ax[a][1]);
+                red_add(cp + 1, ay[a][1]);
+            }
+            ax[a][0] = ax[a][1] = ay[a][0] = ay[a][1] = 0.f;
+        }
+    };
+    if (nblk > 0) stage_a(0);
+    cp_async_commit();
+    if (nblk > 1) stage_a(1);
+    cp_async_commit();
+    cp_async_wait1();
+    if (nblk > 0) stage_b(0);
+    cp_async_commit();
+    for (long long c = 0; c < nblk; ++c) {
+        cp_async_wait0();
+        __syncthreads();
+        if (c + 1 < nblk) stage_b(c + 1);
+        cp_async_commit();
+        if (c + 2 < nblk) stage_a(c + 2);
+        cp_async_commit();
+        const float4 *rb = rbuf + ((int)(c % 3) * SP3_BLK + warp * SP3_RUN) * 2;
+        const float2 *yb = ybuf + (int)(c & 1) * SP3_BLK + warp * SP3_RUN;
+        const long long left = my_len - c * SP3_RUN;
+        for (int t = 0; t < SP3_RUN; ++t) {
+            if (t >= left) break;   // warp-uniform
+            const float4 q = rb[2 * t], qc = rb[2 * t + 1];
+            const float cw = horner8(cc, q.z);
+            const float wt = horner8(rcf, g == 0 ? q.x : q.y);   // lanes 0..7: first row, 8..15: second
+            float wa[2 * MR];
+#pragma unroll
+            for (int a = 0; a < 2 * MR; ++a) wa[a] = __shfl_sync(0xffffffffu, wt, a);
+            const float wb0 = __shfl_sync(0xffffffffu, wt, 8 + min(g, 2 * MR - 1));
+            const float wb1 = __shfl_sync(0xffffffffu, wt, 8 + min(g + 4, 2 * MR - 1));
+            const int fa = __float_as_int(qc.x), fb = __float_as_int(qc.y), fc = __float_as_int(qc.z);
+            if (fa != cfa || fb != cfb || fc != cfc) {
+                if (cfa >= 0) flush();
+                cfa = fa;
+                cfb = fb;
+                cfc = fc;
+            }
+            const float2 yv = yb[t];
+            const float yx = yv.x * cw, yy = yv.y * cw;
+            const float u0x = yx * wb0, u0y = yy * wb0, u1x = yx * wb1, u1y = yy * wb1;
+#pragma unroll
+            for (int a = 0; a < 2 * MR; ++a) {
+                ax[a][0] = fmaf(u0x, wa[a], ax[a][0]);
+                ay[a][0] = fmaf(u0y, wa[a], ay[a][0]);
+                ax[a][1] = fmaf(u1x, wa[a], ax[a][1]);
+                ay[a][1] = fmaf(u1y, wa[a], ay[a][1]);
+            }
+        }
+        __syncthreads();
+    }
+    cp_async_wait0();
+    if (cfa >= 0) flush();
+}
+
 // Unsorted item (order 3, or a plan without sorted copies): the item's nodes
 // in their original order, staged as float4 (first-row coordinate, last
 // coordinate, y) one block ahead; every node adds its window to the shared
 // grid with shared-memory atomics.
-template <int MR>
+template <int MR, bool O3>
 __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                      long long j0, long long j1, float2 *S, unsigned char *stg_raw,
                                                      const float wcf[NCOEF]) {
@@ -311,7 +438,7 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
                 red_add(base, q.z * cw);
                 red_add(base + 1, q.w * cw);
             }
-        } else {
+        } else if constexpr (O3) {
             // order 3: rows wrap modulo n; row weights from the per-tap
             // polynomials, lane (0, k) the first row coordinate's tap k, lane
             // (1, k) the second's, handed round by shuffles (the whole warp
@@ -367,10 +494,10 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
 // the original order) into a shared-memory copy of the term's stored grid
 // (halos included) and writes it to partial grid z of its problem.  CTAs take
 // items from a global counter.
-template <int MR, typename G>
-__global__ void __launch_bounds__(SPREAD_THREADS, 3)
-spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n_items, int *counter,
-           long long max_grid_bytes) {
+template <int MR, typename G, bool O3>
+__device__ __forceinline__ void spread_items(const DevPlan &single, const BatchArgs &B,
+                                             const float2 *__restrict__ y_base, int item_begin, int item_end,
+                                             int *counter, long long max_grid_bytes) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *S = (float2 *)smem_raw;
     unsigned char *stg_raw = smem_raw + max_grid_bytes;
@@ -378,11 +505,11 @@ spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n
     const int tid = threadIdx.x;
     const int k = tid & 7;
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(counter, 1);
+        if (tid == 0) s_item = item_begin + atomicAdd(counter, 1);
         __syncthreads();
         const int item = s_item;
         __syncthreads();
-        if (item >= n_items) break;
+        if (item >= item_end) break;
         const int4 itm = B.items[item];
         const DevPlan &P = B.plans ? B.plans[itm.x] : single;
         if (P.skip && *P.skip) continue;
@@ -403,10 +530,17 @@ spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n
             for (int i = 0; i < NCOEF; ++i) wcf[i] = __ldg(wsrc + i);
         }
         __syncthreads();   // grid zeroed before any addition
-        if (T.sort_slot >= 0 && P.srec)
-            spread_sorted_item<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
-        else
-            spread_unsorted_item<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
+        if constexpr (O3) {
+            if (T.sort_slot >= 0 && P.srec)
+                spread_sorted_item3<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
+            else
+                spread_unsorted_item<MR, true>(P, T, y, j0, j1, S, stg_raw, wcf);
+        } else {
+            if (T.sort_slot >= 0 && P.srec)
+                spread_sorted_item<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
+            else
+                spread_unsorted_item<MR, false>(P, T, y, j0, j1, S, stg_raw, wcf);
+        }
         __syncthreads();
         if constexpr (std::is_same<G, float2>::value) {
             float4 *dst = (float4 *)(P.partials + (long long)itm.z * P.grid_elems + T.grid_off);
@@ -417,6 +551,22 @@ spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int n
         }
         __syncthreads();
     }
+}
+
+// the order-1/2 items (3 CTAs per SM) and the third-order items (more
+// registers for the 2 x 2 m_row row-pair sums, 2 CTAs per SM)
+template <int MR, typename G>
+__global__ void __launch_bounds__(SPREAD_THREADS, 3)
+spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
+           int *counter, long long max_grid_bytes) {
+    spread_items<MR, G, false>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
+}
+
+template <int MR, typename G>
+__global__ void __launch_bounds__(SPREAD_THREADS, 2)
+spread3_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
+            int *counter, long long max_grid_bytes) {
+    spread_items<MR, G, true>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
 }
 
 template <typename G>
@@ -639,6 +789,8 @@ static void adjoint_attrs() {
         cudaFuncSetAttribute(adjoint_post_f32<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(spread_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread3_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread3_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         attr_done = true;
     }
 }
@@ -647,17 +799,27 @@ static void adjoint_attrs() {
 // grid in FP32 (the spread's shared-memory copy)
 template <typename G>
 static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P,
-                            const float2 *y, float2 *fhat, int n_items, int *counter, int n_blocks, int mr,
-                            long long sgrid, int max_fft_elems, int sm_count, long long max_grid_elems) {
+                            const float2 *y, float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks,
+                            int mr, long long sgrid, int max_fft_elems, int sm_count, long long max_grid_elems) {
     adjoint_attrs<G>();
     const size_t ssm = spread_smem_bytes(sgrid);
-    const int ctas = std::max(1, std::min(n_items, spread_ctas_per_sm(sgrid) * sm_count));
+    const int per_sm = spread_ctas_per_sm(sgrid);
     if (prof) stage_begin(*prof, ST_SPREAD);
-    cudaMemsetAsync(counter, 0, sizeof(int), st);
-    if (mr <= 3)
-        spread_f32<3, G><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items, counter, sgrid);
-    else
-        spread_f32<4, G><<<ctas, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items, counter, sgrid);
+    cudaMemsetAsync(counter, 0, 2 * sizeof(int), st);
+    if (n_items3 > 0) {
+        const int c3 = std::max(1, std::min(n_items3, std::min(per_sm, 2) * sm_count));
+        if (mr <= 3)
+            spread3_f32<3, G><<<c3, SPREAD_THREADS, ssm, st>>>(v, B, y, 0, n_items3, counter, sgrid);
+        else
+            spread3_f32<4, G><<<c3, SPREAD_THREADS, ssm, st>>>(v, B, y, 0, n_items3, counter, sgrid);
+    }
+    if (n_items > n_items3) {
+        const int c = std::max(1, std::min(n_items - n_items3, per_sm * sm_count));
+        if (mr <= 3)
+            spread_f32<3, G><<<c, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items3, n_items, counter + 1, sgrid);
+        else
+            spread_f32<4, G><<<c, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items3, n_items, counter + 1, sgrid);
+    }
     if (prof) stage_end(*prof, ST_SPREAD);
     const long long n4 = max_grid_elems / 2;
     const int rb = (int)std::max<long long>(1, std::min<long long>(sm_count * 8LL / std::max(1, P) + 1, (n4 + 255) / 256));
@@ -672,9 +834,9 @@ static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const
 
 // The adjoint kernels for one problem (B.plans == null) or a batch of P problems.
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
-                   float2 *fhat, int n_items, int *counter, int n_blocks, int mr, long long max_grid_bytes,
-                   int max_fft_elems, int sm_count, long long max_grid_elems, bool any_empty, double2 *scratch,
-                   int prec) {
+                   float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks, int mr,
+                   long long max_grid_bytes, int max_fft_elems, int sm_count, long long max_grid_elems,
+                   bool any_empty, double2 *scratch, int prec) {
     if (any_empty) {
         const int nb = 256;
         if (prof) stage_begin(*prof, ST_SUMY);
@@ -684,14 +846,14 @@ int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArg
     }
     if (n_blocks == 0) return cuda_status(cudaGetLastError());
     if (prec == ANOVA_PREC_F16)
-        adjoint_kernels<__half2>(prof, st, v, B, P, y, fhat, n_items, counter, n_blocks, mr, 2 * max_grid_bytes,
-                                 max_fft_elems, sm_count, max_grid_elems);
+        adjoint_kernels<__half2>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
+                                 2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems);
     else if (prec == ANOVA_PREC_BF16)
-        adjoint_kernels<__nv_bfloat162>(prof, st, v, B, P, y, fhat, n_items, counter, n_blocks, mr,
+        adjoint_kernels<__nv_bfloat162>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
                                         2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems);
     else
-        adjoint_kernels<float2>(prof, st, v, B, P, y, fhat, n_items, counter, n_blocks, mr, max_grid_bytes,
-                                max_fft_elems, sm_count, max_grid_elems);
+        adjoint_kernels<float2>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
+                                max_grid_bytes, max_fft_elems, sm_count, max_grid_elems);
     return cuda_status(cudaGetLastError());
 }
 
@@ -706,9 +868,9 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
     }
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s) mr = p.h_terms[s].mr > 0 ? p.h_terms[s].mr : mr;
-    return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.n_items, p.counter, p.n_act, mr, p.max_grid_bytes,
-                          p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0, (double2 *)p.scratch,
-                          p.precision);
+    return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.n_items, p.n_items3, p.counter, p.n_act, mr,
+                          p.max_grid_bytes, p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0,
+                          (double2 *)p.scratch, p.precision);
 }
 
 }  // namespace agft

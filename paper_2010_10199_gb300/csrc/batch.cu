@@ -38,7 +38,8 @@ struct Batch {
     int4 *d_items = nullptr;   // spread work items
     int *counter = nullptr;
     BatchArgs args;
-    int n_tiles = 0, n_items = 0, n_blocks = 0, mr = 3, pitch = 0, dmax = 1, max_fft = 1, sm_count = 152;
+    int n_tiles = 0, n_items = 0, n_items3 = 0, n_blocks = 0, mr = 3, pitch = 0, dmax = 1, max_fft = 1,
+        sm_count = 152;
     long long max_grid_bytes = 16, max_grid_elems = 0;
     bool any_empty = false;
     double2 *scratch = nullptr;
@@ -87,9 +88,9 @@ static int batch_trafo(Batch &b, cudaStream_t st, const float2 *fhat, float2 *f)
 }
 
 static int batch_adjoint(Batch &b, cudaStream_t st, const float2 *y, float2 *fhat) {
-    return adjoint_launch(nullptr, st, b.views[0], b.args, b.P, y, fhat, b.n_items, b.counter, b.n_blocks, b.mr,
-                          b.max_grid_bytes, b.max_fft, b.sm_count, b.max_grid_elems, b.any_empty, b.scratch,
-                          ANOVA_PREC_F32);
+    return adjoint_launch(nullptr, st, b.views[0], b.args, b.P, y, fhat, b.n_items, b.n_items3, b.counter,
+                          b.n_blocks, b.mr, b.max_grid_bytes, b.max_fft, b.sm_count, b.max_grid_elems, b.any_empty,
+                          b.scratch, ANOVA_PREC_F32);
 }
 
 // ----------------------------------------------------- segmented kernels --
@@ -289,20 +290,28 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
     // spread items: every problem's active terms split into K_p node chunks,
     // K_p sized for all problems sharing the GPU
     std::vector<int4> items;
+    std::vector<int> Ks(n_problems);
     for (int p = 0; p < n_problems; ++p) {
         Plan &pl = b->plans[p]->p;
-        const int K = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count);
-        b->views[p].spread_chunks = K;
-        const size_t at = items.size();
-        items.resize(at + (size_t)pl.n_act * K);
-        append_spread_items(pl, p, K, items.data() + at);
+        Ks[p] = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count);
+        b->views[p].spread_chunks = Ks[p];
+    }
+    // third-order items of every problem first, then the others
+    for (int sel : {3, 0}) {
+        for (int p = 0; p < n_problems; ++p) {
+            Plan &pl = b->plans[p]->p;
+            const size_t at = items.size();
+            items.resize(at + (size_t)pl.n_act * Ks[p]);
+            items.resize(at + append_spread_items(pl, p, Ks[p], items.data() + at, sel));
+        }
+        if (sel == 3) b->n_items3 = (int)items.size();
     }
     b->n_items = (int)items.size();
     cudaError_t e = cudaMalloc(&b->d_plans, sizeof(DevPlan) * n_problems);
     const size_t nt = tile_prob.size() + tile0.size() + blk_prob.size() + blk0.size();
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tables, sizeof(int) * nt);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int4) * std::max<size_t>(1, items.size()));
-    if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->counter, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->scratch, sizeof(double2) * 256 * n_problems);
     if (e != cudaSuccess) {
         free_batch(b);

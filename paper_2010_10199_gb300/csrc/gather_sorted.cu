@@ -96,7 +96,7 @@ __device__ __forceinline__ void horner_pair(const float4 *c, float v0, float v1,
 template <int MR>
 __global__ void __launch_bounds__(GS_THREADS, 3)
 gather_sorted_f32(DevPlan P, const int4 *__restrict__ items, unsigned long long *__restrict__ acc, const int *e_in,
-                  int n_items, int *counter, long long max_grid_bytes) {
+                  int item_begin, int item_end, int *counter, long long max_grid_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *S = (float2 *)smem;
     float4 *coef = (float4 *)(smem + max_grid_bytes);   // [8 column taps + 8 row taps][2]
@@ -105,11 +105,11 @@ gather_sorted_f32(DevPlan P, const int4 *__restrict__ items, unsigned long long 
     const long long M = P.M;
     const float sc = __int_as_float((127 + *e_in) << 23);   // 2^e, exact scaling
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(counter, 1);
+        if (tid == 0) s_item = item_begin + atomicAdd(counter, 1);
         __syncthreads();
         const int item = s_item;
         __syncthreads();
-        if (item >= n_items) break;
+        if (item >= item_end) break;
         if (P.skip && *P.skip) continue;
         const int4 itm = items[item];
         const Term &T = P.terms[P.act[itm.y]];
@@ -201,14 +201,15 @@ int launch_gather_sorted_f32(Plan &p, const float2 *fhat, float2 *f) {
         attr = true;
     }
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(3, (size_t)(MAX_SMEM + 1024) / (smem + 1024)));
-    const int ctas = std::max(1, std::min(p.n_items, per_sm * p.sm_count));
+    // the order-1/2 items (the first n_items3 belong to third-order terms)
+    const int ctas = std::max(1, std::min(p.n_items - p.n_items3, per_sm * p.sm_count));
     cudaMemsetAsync(p.counter, 0, sizeof(int), p.stream);
     if (mr <= 3)
-        gather_sorted_f32<3><<<ctas, GS_THREADS, smem, p.stream>>>(v, p.items, p.facc, p.fexp, p.n_items,
-                                                                  p.counter, p.max_grid_bytes);
+        gather_sorted_f32<3><<<ctas, GS_THREADS, smem, p.stream>>>(v, p.items, p.facc, p.fexp, p.n_items3,
+                                                                  p.n_items, p.counter, p.max_grid_bytes);
     else
-        gather_sorted_f32<4><<<ctas, GS_THREADS, smem, p.stream>>>(v, p.items, p.facc, p.fexp, p.n_items,
-                                                                  p.counter, p.max_grid_bytes);
+        gather_sorted_f32<4><<<ctas, GS_THREADS, smem, p.stream>>>(v, p.items, p.facc, p.fexp, p.n_items3,
+                                                                  p.n_items, p.counter, p.max_grid_bytes);
     const int fb = (int)std::min<long long>(4LL * p.sm_count, (p.M + 255) / 256);
     k_fixed_point_finish<<<fb, 256, 0, p.stream>>>(f, (const long long *)p.facc, p.fexp, p.M, p.skip);
     return cuda_status(cudaGetLastError());

@@ -192,6 +192,7 @@ struct Plan {
     int4 *items;            // spread work items (device, n_terms * spread_kmax slots)
     int4 *h_items;
     int n_items;
+    int n_items3;           // the first n_items3 items are those of third-order terms
     int *counter;           // work-queue counter of the spread
     float4 *srec;           // cell-sorted node records (null: none), n_sorted slots of M
     int n_sorted;
@@ -238,9 +239,9 @@ int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_gather_sorted_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
-                   float2 *fhat, int n_items, int *counter, int n_blocks, int mr, long long max_grid_bytes,
-                   int max_fft_elems, int sm_count, long long max_grid_elems, bool any_empty, double2 *scratch,
-                   int prec);
+                   float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks, int mr,
+                   long long max_grid_bytes, int max_fft_elems, int sm_count, long long max_grid_elems,
+                   bool any_empty, double2 *scratch, int prec);
 size_t spread_smem_bytes(long long max_grid_bytes);
 // Sorts the nodes by grid cell for every term with sort_slot >= 0 (sort.cu).
 int sort_nodes_by_cell(Plan &p);
@@ -253,9 +254,10 @@ int spread_ctas_per_sm(long long max_grid_bytes);
 // problems of a launch) on sm_count SMs: about three items per resident CTA,
 // at most kmax, at least 2048 nodes per chunk.
 int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count);
-// Appends the spread work items of one problem: active terms of higher order
-// first (they cost more), K chunks each.
-int append_spread_items(const Plan &p, int prob, int K, int4 *out);
+// Appends the spread work items of one problem, K chunks per active term:
+// those of the third-order terms (sel = 3) or of the others, order 2 before
+// order 1 (sel = 0).  Returns the count.
+int append_spread_items(const Plan &p, int prob, int K, int4 *out, int sel);
 int lipschitz_estimate(Plan &p, double *L);
 int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas, int n_lambda, int max_it,
                double tol, int step_mode, double L0, double eta, const uint8_t *mask, const float2 *f0,

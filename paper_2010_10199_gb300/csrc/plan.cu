@@ -165,9 +165,13 @@ int set_active_terms(Plan &p, const unsigned char *user_mask) {
     p.n_act = n;
     p.n_act3 = (int)recs3.size();
     p.n_items = 0;
+    p.n_items3 = 0;
     if (n == 0) return ANOVA_OK;
     p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count);
-    if (p.h_items) p.n_items = append_spread_items(p, 0, p.spread_K, p.h_items);
+    if (p.h_items) {
+        p.n_items3 = append_spread_items(p, 0, p.spread_K, p.h_items, 3);
+        p.n_items = p.n_items3 + append_spread_items(p, 0, p.spread_K, p.h_items + p.n_items3, 0);
+    }
     cudaError_t e = cudaMemcpyAsync(p.act, p.h_act, sizeof(int) * n, cudaMemcpyHostToDevice, p.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p.act_rec, recs.data(), sizeof(ActRec) * n, cudaMemcpyHostToDevice, p.stream);
@@ -514,7 +518,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     if (e == cudaSuccess && p.n_terms > 0)
         chk(cudaMalloc(&p.partials, (size_t)kmax * (size_t)p.grid_elems * esize));
     chk(cudaMalloc(&p.items, sizeof(int4) * (size_t)std::max(1, p.n_terms) * kmax));
-    chk(cudaMalloc(&p.counter, sizeof(int)));
+    chk(cudaMalloc(&p.counter, 2 * sizeof(int)));
     p.h_items = new int4[(size_t)std::max(1, p.n_terms) * kmax];
     p.scratch_bytes = 1 << 20;
     chk(cudaMalloc(&p.scratch, p.scratch_bytes));
@@ -526,18 +530,25 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
             chk(cudaMemcpyAsync(p.slots64, slots64.data(), sizeof(int4) * p.n_slots64, cudaMemcpyHostToDevice,
                                 p.stream));
     }
-    // cell-sorted node copies for the adjoint (terms of order <= 2), if they
-    // fit in half the free device memory
+    // cell-sorted node records (16 bytes per node for a term of order <= 2, 32
+    // for order 3; FP64 plans sort order <= 2 only), if they fit in half the
+    // free device memory.  sort_slot counts units of M records of 16 bytes.
     if (e == cudaSuccess && o.node_sort >= 0 && M > 0) {
+        auto units = [&](const Term &T) { return T.order <= 2 ? 1 : (p.precision == ANOVA_PREC_F64 ? 0 : 2); };
         int ns = 0;
-        for (int s = 0; s < p.n_terms; ++s) ns += p.h_terms[s].order <= 2;
+        for (int s = 0; s < p.n_terms; ++s) ns += units(p.h_terms[s]);
         size_t free_b = 0, total_b = 0;
         const size_t need = (size_t)ns * (size_t)M * sizeof(float4);
         if (ns > 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need <= free_b / 2) {
             if (cudaMalloc(&p.srec, need) == cudaSuccess) {
                 int slot = 0;
-                for (int s = 0; s < p.n_terms; ++s)
-                    if (p.h_terms[s].order <= 2) p.h_terms[s].sort_slot = slot++;
+                for (int s = 0; s < p.n_terms; ++s) {
+                    const int u = units(p.h_terms[s]);
+                    if (u) {
+                        p.h_terms[s].sort_slot = slot;
+                        slot += u;
+                    }
+                }
                 p.n_sorted = ns;
                 if (p.precision == ANOVA_PREC_F32) {
                     if (cudaMalloc(&p.facc, sizeof(unsigned long long) * 2 * (size_t)M) != cudaSuccess ||

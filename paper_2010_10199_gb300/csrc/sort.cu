@@ -18,15 +18,19 @@
 
 namespace agft {
 
-__device__ __forceinline__ int cell_bins(const Term &T) { return T.order == 2 ? T.n * T.n : T.n; }
+__device__ __forceinline__ int cell_bins(const Term &T) {
+    return T.order == 3 ? T.n * T.n * T.n : (T.order == 2 ? T.n * T.n : T.n);
+}
 
-__device__ __forceinline__ int cell_of(const Term &T, float xr, float xc) {
-    float tc;
-    const int fc = grid_pos(xc, T.n, tc);
-    if (T.order != 2) return fc;
-    float tr;
-    const int fr = grid_pos(xr, T.n, tr);
-    return fr * T.n + fc;
+// cell of a node: (i_row0 * n + i_row1) * n + i_col over the term's coordinates
+__device__ __forceinline__ int cell_of(const Term &T, float xr, float xr1, float xc) {
+    float t;
+    const int fc = grid_pos(xc, T.n, t);
+    if (T.order == 1) return fc;
+    const int fr = grid_pos(xr, T.n, t);
+    if (T.order == 2) return fr * T.n + fc;
+    const int fr1 = grid_pos(xr1, T.n, t);
+    return (fr * T.n + fr1) * T.n + fc;
 }
 
 // counts[slot][cell] += nodes of the block's range in that cell
@@ -37,10 +41,11 @@ __global__ void k_cell_count(const Term *terms, const float *x, long long M, int
     const int nb = cell_bins(T);
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    const float *xr = x + (long long)(T.order == 2 ? T.row0 : T.col) * M;
+    const float *xr = x + (long long)(T.order >= 2 ? T.row0 : T.col) * M;
+    const float *xr1 = x + (long long)(T.order == 3 ? T.row1 : T.col) * M;
     const float *xc = x + (long long)T.col * M;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M; j += (long long)gridDim.x * blockDim.x)
-        atomicAdd(&hist[cell_of(T, xr[j], xc[j])], 1);
+        atomicAdd(&hist[cell_of(T, xr[j], xr1[j], xc[j])], 1);
     __syncthreads();
     int *cnt = counts + (long long)T.sort_slot * max_bins;
     for (int b = threadIdx.x; b < nb; b += blockDim.x)
@@ -86,26 +91,36 @@ __global__ void k_cell_scan(const Term *terms, int *counts, int max_bins) {
     }
 }
 
-// scatter: every node goes to the next free place of its cell, as a record
-// (2 tau_row - 1, 2 tau_col - 1, first-tap grid offset, original index)
+// scatter: every node goes to the next free place of its cell, as a record.
+// Order <= 2: (2 tau_row - 1, 2 tau_col - 1, first-tap grid offset, original
+// index).  Order 3, two records: (2 tau_row0 - 1, 2 tau_row1 - 1, 2 tau_col - 1,
+// original index) and the cell's grid indices (i_row0, i_row1, i_col, 0).
 __global__ void k_cell_scatter(const Term *terms, const float *x, long long M, int *cursor, int max_bins,
                                float4 *srec) {
     const Term &T = terms[blockIdx.y];
     if (T.sort_slot < 0) return;
-    const float *xr = x + (long long)(T.order == 2 ? T.row0 : T.col) * M;
+    const float *xr = x + (long long)(T.order >= 2 ? T.row0 : T.col) * M;
+    const float *xr1 = x + (long long)(T.order == 3 ? T.row1 : T.col) * M;
     const float *xc = x + (long long)T.col * M;
     int *cur = cursor + (long long)T.sort_slot * max_bins;
     float4 *dst = srec + (long long)T.sort_slot * M;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M;
          j += (long long)gridDim.x * blockDim.x) {
-        float tc, tr = 0.f;
+        float tc, tr = 0.f, tr1 = 0.f;
         const int fc = grid_pos(xc[j], T.n, tc);
-        int fr = 0;
-        if (T.order == 2) fr = grid_pos(xr[j], T.n, tr);
-        const int pos = atomicAdd(&cur[fr * (T.order == 2 ? T.n : 0) + fc], 1);
-        const int off = fr * T.stride + fc;
-        dst[pos] = make_float4(T.order == 2 ? 2.f * tr - 1.f : 0.f, 2.f * tc - 1.f, __int_as_float(off),
-                               __int_as_float((int)j));
+        int fr = 0, fr1 = 0;
+        if (T.order >= 2) fr = grid_pos(xr[j], T.n, tr);
+        if (T.order == 3) fr1 = grid_pos(xr1[j], T.n, tr1);
+        if (T.order == 3) {
+            const int pos = atomicAdd(&cur[(fr * T.n + fr1) * T.n + fc], 1);
+            dst[2 * pos] = make_float4(2.f * tr - 1.f, 2.f * tr1 - 1.f, 2.f * tc - 1.f, __int_as_float((int)j));
+            dst[2 * pos + 1] = make_float4(__int_as_float(fr), __int_as_float(fr1), __int_as_float(fc), 0.f);
+        } else {
+            const int pos = atomicAdd(&cur[fr * (T.order == 2 ? T.n : 0) + fc], 1);
+            const int off = fr * T.stride + fc;
+            dst[pos] = make_float4(T.order == 2 ? 2.f * tr - 1.f : 0.f, 2.f * tc - 1.f, __int_as_float(off),
+                                   __int_as_float((int)j));
+        }
     }
 }
 
@@ -158,7 +173,8 @@ int sort_nodes_by_cell(Plan &p) {
     int max_bins = 1;
     for (int s = 0; s < p.n_terms; ++s) {
         const Term &T = p.h_terms[s];
-        if (T.sort_slot >= 0) max_bins = std::max(max_bins, T.order == 2 ? T.n * T.n : T.n);
+        if (T.sort_slot >= 0)
+            max_bins = std::max(max_bins, T.order == 3 ? T.n * T.n * T.n : (T.order == 2 ? T.n * T.n : T.n));
     }
     int *counts = nullptr;
     cudaError_t e = cudaMalloc(&counts, sizeof(int) * (size_t)p.n_sorted * max_bins);
