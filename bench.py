@@ -446,7 +446,7 @@ def run_lambda_path(args, local_rank):
             "config": {"workload": f"d=30, |u|<=2 (466 terms), N=32 (1D) / 16x16 (2D), M={M} uniform nodes, "
                                    f"5 active pairs + 3 singletons, noise 0.05",
                        "lambdas": f"first {K} of 20 geometric 1e-1..1e-5, times M",
-                       "fista": f"constant step L = 1.05 x power estimate, tol {args.tol}, max_it {args.max_it}, "
+                       "fista": f"constant step L = 1.05 x Lanczos estimate of ||F||^2, tol {args.tol}, max_it {args.max_it}, "
                                 f"warm-started path"},
             "results": res}
     print(json.dumps(line), flush=True)
