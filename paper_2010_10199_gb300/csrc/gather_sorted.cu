@@ -1,5 +1,5 @@
-// Forward gather of the order-1 and order-2 terms over the cell-sorted node
-// records (the window interpolation step of the NFFT behind eq. (somafm),
+// Forward gather over the cell-sorted node records (every term with records:
+// all terms of an FP32 plan that keeps them) (the window interpolation step of the NFFT behind eq. (somafm),
 // Sec. 3), FP32.
 //
 // Work items are the adjoint's (active term, node chunk) pairs.  A CTA copies
@@ -113,7 +113,7 @@ gather_sorted_f32(DevPlan P, const int4 *__restrict__ items, unsigned long long 
         if (P.skip && *P.skip) continue;
         const int4 itm = items[item];
         const Term &T = P.terms[P.act[itm.y]];
-        if (T.order > 2 || T.sort_slot < 0) continue;   // third-order terms: point-major gather
+        if (T.sort_slot < 0) continue;   // no records: the point-major gather has the term
         const long long j0 = M * itm.z / itm.w, j1 = M * (itm.z + 1) / itm.w;
         // the term's grid and window coefficients into shared memory
         {
@@ -132,6 +132,55 @@ gather_sorted_f32(DevPlan P, const int4 *__restrict__ items, unsigned long long 
         const float4 *rec = P.srec + (long long)T.sort_slot * M;
         const int stride = T.stride;
         const bool two = T.order == 2;
+        if (T.order == 3) {
+            // one node per thread: two records (window arguments and index; the
+            // cell's grid indices), 2 MR x 2 MR rows of 8 taps, indices modulo n
+            const int n = T.n;
+            for (long long p = j0 + tid; p < j1; p += GS_THREADS) {
+                const float4 q = __ldg(rec + 2 * p), qc = __ldg(rec + 2 * p + 1);
+                const int fa = __float_as_int(qc.x), fb = __float_as_int(qc.y), fc = __float_as_int(qc.z);
+                float wc[8], wb[2 * MR], dummy;
+                int col[8], rb[2 * MR];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    horner_pair(coef + 2 * t, q.z, q.z, wc[t], dummy);
+                    col[t] = wrap(fc - T.mc + 1 + t, n);
+                }
+#pragma unroll
+                for (int i = 0; i < 2 * MR; ++i) {
+                    horner_pair(coef + 16 + 2 * i, q.y, q.y, wb[i], dummy);
+                    rb[i] = wrap(fb - MR + 1 + i, n);
+                }
+                float sx = 0.f, sy = 0.f;
+#pragma unroll 1
+                for (int ia = 0; ia < 2 * MR; ++ia) {
+                    float wa;
+                    horner_pair(coef + 16 + 2 * ia, q.x, q.x, wa, dummy);
+                    const int ra = wrap(fa - MR + 1 + ia, n) * n;
+                    float ux = 0.f, uy = 0.f;
+#pragma unroll
+                    for (int ib = 0; ib < 2 * MR; ++ib) {
+                        const float2 *row = S + (ra + rb[ib]) * stride;
+                        float tx = 0.f, ty = 0.f;
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            const float2 g = row[col[t]];
+                            tx = fmaf(wc[t], g.x, tx);
+                            ty = fmaf(wc[t], g.y, ty);
+                        }
+                        ux = fmaf(wb[ib], tx, ux);
+                        uy = fmaf(wb[ib], ty, uy);
+                    }
+                    sx = fmaf(wa, ux, sx);
+                    sy = fmaf(wa, uy, sy);
+                }
+                unsigned long long *a0 = acc + 2 * (long long)__float_as_int(q.w);
+                red_add_u64(a0, __float2ll_rn(sx * sc));
+                red_add_u64(a0 + 1, __float2ll_rn(sy * sc));
+            }
+            __syncthreads();
+            continue;
+        }
         for (long long p = j0 + tid; p < j1; p += 2 * GS_THREADS) {
             const long long p1 = p + GS_THREADS;
             const bool ok1 = p1 < j1;
@@ -201,14 +250,15 @@ int launch_gather_sorted_f32(Plan &p, const float2 *fhat, float2 *f) {
         attr = true;
     }
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(3, (size_t)(MAX_SMEM + 1024) / (smem + 1024)));
-    // the order-1/2 items (the first n_items3 belong to third-order terms)
-    const int ctas = std::max(1, std::min(p.n_items - p.n_items3, per_sm * p.sm_count));
+    // the order-1/2 items, and the third-order ones (the first n_items3) when they have records
+    const int first = p.n_act3 > 0 ? p.n_items3 : 0;
+    const int ctas = std::max(1, std::min(p.n_items - first, per_sm * p.sm_count));
     cudaMemsetAsync(p.counter, 0, sizeof(int), p.stream);
     if (mr <= 3)
-        gather_sorted_f32<3><<<ctas, GS_THREADS, smem, p.stream>>>(v, p.items, p.facc, p.fexp, p.n_items3,
+        gather_sorted_f32<3><<<ctas, GS_THREADS, smem, p.stream>>>(v, p.items, p.facc, p.fexp, first,
                                                                   p.n_items, p.counter, p.max_grid_bytes);
     else
-        gather_sorted_f32<4><<<ctas, GS_THREADS, smem, p.stream>>>(v, p.items, p.facc, p.fexp, p.n_items3,
+        gather_sorted_f32<4><<<ctas, GS_THREADS, smem, p.stream>>>(v, p.items, p.facc, p.fexp, first,
                                                                   p.n_items, p.counter, p.max_grid_bytes);
     const int fb = (int)std::min<long long>(4LL * p.sm_count, (p.M + 255) / 256);
     k_fixed_point_finish<<<fb, 256, 0, p.stream>>>(f, (const long long *)p.facc, p.fexp, p.M, p.skip);

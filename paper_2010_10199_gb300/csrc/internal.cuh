@@ -181,7 +181,7 @@ struct Plan {
     // active term list (all scheduled terms unless a group mask restricts it)
     int *act;
     ActRec *act_rec;
-    ActRec *act_rec3;       // the active third-order terms alone (point-major gather of the sorted forward)
+    ActRec *act_rec3;       // active third-order terms without sorted records (point-major gather)
     int n_act3;
     int n_act;
     int *h_act;

@@ -159,7 +159,7 @@ int set_active_terms(Plan &p, const unsigned char *user_mask) {
             if (P.order == 2 && P.row0 == T.row0 && P.wr == T.wr && P.n == T.n) ng = 0;
         }
         recs.push_back(make_act_rec(T, s, ng));
-        if (T.order == 3) recs3.push_back(make_act_rec(T, s, 1));
+        if (T.order == 3 && T.sort_slot < 0) recs3.push_back(make_act_rec(T, s, 1));
         p.h_act[n++] = s;
     }
     p.n_act = n;
