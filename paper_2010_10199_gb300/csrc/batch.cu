@@ -42,6 +42,8 @@ struct Batch {
         sm_count = 152;
     long long max_grid_bytes = 16, max_grid_elems = 0;
     bool any_empty = false;
+    bool sorted_fwd = true;   // every problem has cell-sorted records for all its terms
+    long long max_M = 0;
     double2 *scratch = nullptr;
     // batched LSQR workspace
     float2 *u = nullptr, *tM = nullptr, *v = nullptr, *w = nullptr, *x = nullptr, *tn = nullptr;
@@ -83,6 +85,9 @@ static int batch_trafo(Batch &b, cudaStream_t st, const float2 *fhat, float2 *f)
     trafo_pre_f32<<<b.n_blocks, 256, pre_smem, st>>>(b.views[0], b.args, fhat);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
+    if (b.sorted_fwd)
+        return gather_sorted_launch(st, b.views[0], b.args, b.P, fhat, f, b.args.items, 0, b.n_items, b.counter,
+                                    b.max_grid_bytes, b.max_M, b.sm_count, b.mr, (double *)b.scratch);
     return gather_launch(st, b.views[0], b.args, fhat, f, b.n_tiles, b.mr, b.pitch, b.max_grid_bytes, b.dmax,
                          b.sm_count, ANOVA_PREC_F32);
 }
@@ -284,6 +289,8 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
         b->max_grid_bytes = std::max(b->max_grid_bytes, pl.max_grid_bytes);
         b->max_grid_elems = std::max(b->max_grid_elems, pl.grid_elems);
         b->any_empty = b->any_empty || pl.n_empty > 0;
+        b->sorted_fwd = b->sorted_fwd && pl.srec && pl.facc && pl.n_act3 == 0;
+        b->max_M = std::max(b->max_M, pl.M);
         b->sm_count = pl.sm_count;
     }
     b->pitch = mixed_pitch || pitch < 0 ? 0 : pitch;

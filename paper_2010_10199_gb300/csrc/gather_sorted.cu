@@ -35,8 +35,18 @@ __device__ __forceinline__ void red_add_u64(unsigned long long *addr, long long 
 // a fixed block count, so the sum (and e) never depends on timing.
 constexpr int FPE_BLOCKS = 128;
 
-__global__ void k_fixed_point_partial(const float2 *__restrict__ fhat, long long n, double *part) {
+__device__ __forceinline__ const DevPlan &plan_of(const DevPlan &single, const BatchArgs &B, int prob) {
+    return B.plans ? B.plans[prob] : single;
+}
+
+// per problem (blockIdx.y): partial sums of |Re| + |Im| of its coefficients
+__global__ void k_fixed_point_partial(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base,
+                                      double *part_base) {
     __shared__ double sh[32];
+    const DevPlan &P = plan_of(single, B, blockIdx.y);
+    if (P.skip && *P.skip) return;
+    const float2 *fhat = fhat_base + P.vec_coef_off;
+    const long long n = P.n_coeffs;
     double a = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float2 v = fhat[i];
@@ -48,24 +58,50 @@ __global__ void k_fixed_point_partial(const float2 *__restrict__ fhat, long long
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-        part[blockIdx.x] = s;
+        part_base[(long long)blockIdx.y * FPE_BLOCKS + blockIdx.x] = s;
     }
 }
 
-__global__ void k_fixed_point_exponent(const double *part, int *e_out) {
-    if (threadIdx.x != 0) return;
+// per problem (blockIdx.x): the exponent from its partial sums
+__global__ void k_fixed_point_exponent(DevPlan single, BatchArgs B, const double *part_base) {
+    const DevPlan &P = plan_of(single, B, blockIdx.x);
+    if (threadIdx.x != 0 || (P.skip && *P.skip)) return;
+    const double *part = part_base + (long long)blockIdx.x * FPE_BLOCKS;
     double s = 0.0;
     for (int b = 0; b < FPE_BLOCKS; ++b) s += part[b];
     int e = 100;
     if (s > 0) e = 61 - (int)ceil(log2(s));
-    *e_out = max(-100, min(100, e));
+    *P.fexp = max(-100, min(100, e));
 }
 
-// f[j] += acc[j] * 2^-e
-__global__ void k_fixed_point_finish(float2 *f, const long long *acc, const int *e_in, long long M, const int *skip) {
-    if (skip && *skip) return;
-    const double sc = ldexp(1.0, -*e_in);
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M; j += (long long)gridDim.x * blockDim.x) {
+// per problem (blockIdx.y): f = empty-set coefficient, accumulators = 0
+__global__ void k_sorted_forward_init(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base,
+                                      float2 *f_base) {
+    const DevPlan &P = plan_of(single, B, blockIdx.y);
+    if (P.skip && *P.skip) return;
+    const float2 *fhat = fhat_base + P.vec_coef_off;
+    float2 c0 = make_float2(0.f, 0.f);
+    for (int e = 0; e < P.n_empty; ++e) {
+        const float2 c = fhat[P.empty_off[e]];
+        c0.x += c.x;
+        c0.y += c.y;
+    }
+    float2 *f = f_base + P.vec_node_off;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < P.M; j += (long long)gridDim.x * blockDim.x) {
+        f[j] = c0;
+        P.facc[2 * j] = 0ULL;
+        P.facc[2 * j + 1] = 0ULL;
+    }
+}
+
+// per problem (blockIdx.y): f[j] += acc[j] * 2^-e
+__global__ void k_fixed_point_finish(DevPlan single, BatchArgs B, float2 *f_base) {
+    const DevPlan &P = plan_of(single, B, blockIdx.y);
+    if (P.skip && *P.skip) return;
+    const double sc = ldexp(1.0, -*P.fexp);
+    float2 *f = f_base + P.vec_node_off;
+    const long long *acc = (const long long *)P.facc;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < P.M; j += (long long)gridDim.x * blockDim.x) {
         float2 v = f[j];
         v.x += (float)((double)acc[2 * j] * sc);
         v.y += (float)((double)acc[2 * j + 1] * sc);
@@ -73,7 +109,8 @@ __global__ void k_fixed_point_finish(float2 *f, const long long *acc, const int 
     }
 }
 
-// polynomial of tap t from the shared coefficient table (two float4 per tap)
+// polynomial of tap t from the shared coefficient table (two float4 per tap),
+// at two arguments; the same operations as horner8
 __device__ __forceinline__ void horner_pair(const float4 *c, float v0, float v1, float &w0, float &w1) {
     const float4 lo = c[0], hi = c[1];
     float a = hi.w, b = hi.w;
@@ -95,23 +132,25 @@ __device__ __forceinline__ void horner_pair(const float4 *c, float v0, float v1,
 
 template <int MR>
 __global__ void __launch_bounds__(GS_THREADS, 3)
-gather_sorted_f32(DevPlan P, const int4 *__restrict__ items, unsigned long long *__restrict__ acc, const int *e_in,
-                  int item_begin, int item_end, int *counter, long long max_grid_bytes) {
+gather_sorted_f32(DevPlan single, BatchArgs B, const int4 *__restrict__ items, int item_begin, int item_end,
+                  int *counter, long long max_grid_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *S = (float2 *)smem;
     float4 *coef = (float4 *)(smem + max_grid_bytes);   // [8 column taps + 8 row taps][2]
     int &s_item = *(int *)(coef + 32);
     const int tid = threadIdx.x;
-    const long long M = P.M;
-    const float sc = __int_as_float((127 + *e_in) << 23);   // 2^e, exact scaling
     for (;;) {
         if (tid == 0) s_item = item_begin + atomicAdd(counter, 1);
         __syncthreads();
         const int item = s_item;
         __syncthreads();
         if (item >= item_end) break;
-        if (P.skip && *P.skip) continue;
         const int4 itm = items[item];
+        const DevPlan &P = plan_of(single, B, itm.x);
+        if (P.skip && *P.skip) continue;
+        const long long M = P.M;
+        unsigned long long *__restrict__ acc = P.facc;
+        const float sc = __int_as_float((127 + *P.fexp) << 23);   // 2^e, exact scaling
         const Term &T = P.terms[P.act[itm.y]];
         if (T.sort_slot < 0) continue;   // no records: the point-major gather has the term
         const long long j0 = M * itm.z / itm.w, j1 = M * (itm.z + 1) / itm.w;
@@ -233,36 +272,47 @@ gather_sorted_f32(DevPlan P, const int4 *__restrict__ items, unsigned long long 
     }
 }
 
-int launch_gather_sorted_f32(Plan &p, const float2 *fhat, float2 *f) {
-    DevPlan v = dev_view(p);
-    double *part = (double *)p.scratch;   // FPE_BLOCKS partial sums
-    k_fixed_point_partial<<<FPE_BLOCKS, 256, 0, p.stream>>>(fhat, p.n_coeffs, part);
-    k_fixed_point_exponent<<<1, 32, 0, p.stream>>>(part, p.fexp);
-    cudaMemsetAsync(p.facc, 0, sizeof(unsigned long long) * 2 * p.M, p.stream);
-    int mr = 3;
-    for (int s = 0; s < p.n_terms; ++s)
-        if (p.h_terms[s].mr > 0) mr = p.h_terms[s].mr;
-    const size_t smem = (size_t)p.max_grid_bytes + 32 * sizeof(float4) + 16;
+int gather_sorted_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *fhat,
+                         float2 *f, const int4 *items, int item_begin, int item_end, int *counter,
+                         long long max_grid_bytes, long long max_M, int sm_count, int mr, double *part) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(gather_sorted_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(gather_sorted_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         attr = true;
     }
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(3, (size_t)(MAX_SMEM + 1024) / (smem + 1024)));
-    // the order-1/2 items, and the third-order ones (the first n_items3) when they have records
-    const int first = p.n_act3 > 0 ? p.n_items3 : 0;
-    const int ctas = std::max(1, std::min(p.n_items - first, per_sm * p.sm_count));
-    cudaMemsetAsync(p.counter, 0, sizeof(int), p.stream);
-    if (mr <= 3)
-        gather_sorted_f32<3><<<ctas, GS_THREADS, smem, p.stream>>>(v, p.items, p.facc, p.fexp, first,
-                                                                  p.n_items, p.counter, p.max_grid_bytes);
-    else
-        gather_sorted_f32<4><<<ctas, GS_THREADS, smem, p.stream>>>(v, p.items, p.facc, p.fexp, first,
-                                                                  p.n_items, p.counter, p.max_grid_bytes);
-    const int fb = (int)std::min<long long>(4LL * p.sm_count, (p.M + 255) / 256);
-    k_fixed_point_finish<<<fb, 256, 0, p.stream>>>(f, (const long long *)p.facc, p.fexp, p.M, p.skip);
+    const int nb = (int)std::max<long long>(1, std::min<long long>(4LL * sm_count / std::max(1, P) + 1,
+                                                                   (max_M + 255) / 256));
+    k_fixed_point_partial<<<dim3(FPE_BLOCKS, P), 256, 0, st>>>(v, B, fhat, part);
+    k_fixed_point_exponent<<<P, 32, 0, st>>>(v, B, part);
+    k_sorted_forward_init<<<dim3(nb, P), 256, 0, st>>>(v, B, fhat, f);
+    if (item_end > item_begin) {
+        const size_t smem = (size_t)max_grid_bytes + 32 * sizeof(float4) + 16;
+        const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(3, (size_t)(MAX_SMEM + 1024) / (smem + 1024)));
+        const int ctas = std::max(1, std::min(item_end - item_begin, per_sm * sm_count));
+        cudaMemsetAsync(counter, 0, sizeof(int), st);
+        if (mr <= 3)
+            gather_sorted_f32<3><<<ctas, GS_THREADS, smem, st>>>(v, B, items, item_begin, item_end, counter,
+                                                                 max_grid_bytes);
+        else
+            gather_sorted_f32<4><<<ctas, GS_THREADS, smem, st>>>(v, B, items, item_begin, item_end, counter,
+                                                                 max_grid_bytes);
+    }
+    k_fixed_point_finish<<<dim3(nb, P), 256, 0, st>>>(v, B, f);
     return cuda_status(cudaGetLastError());
+}
+
+// single plan: every term has records (third-order ones without records were
+// handled by the point-major gather, which then wrote f; see trafo.cu)
+int launch_gather_sorted_f32(Plan &p, const float2 *fhat, float2 *f) {
+    DevPlan v = dev_view(p);
+    BatchArgs B;
+    std::memset(&B, 0, sizeof(B));
+    int mr = 3;
+    for (int s = 0; s < p.n_terms; ++s)
+        if (p.h_terms[s].mr > 0) mr = p.h_terms[s].mr;
+    return gather_sorted_launch(p.stream, v, B, 1, fhat, f, p.items, 0, p.n_items, p.counter, p.max_grid_bytes, p.M,
+                                p.sm_count, mr, (double *)p.scratch);
 }
 
 }  // namespace agft

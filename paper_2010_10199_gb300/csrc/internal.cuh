@@ -128,6 +128,9 @@ struct DevPlan {
     float2 *partials;         // adjoint partial grids [spread_chunks][grid_elems]
     int spread_chunks;        // node chunks of the adjoint (one partial grid each)
     const float4 *srec;       // [slot][M] nodes sorted by grid cell, see SortedNode
+    unsigned long long *facc; // sorted forward: fixed-point accumulators [M][2] (or null)
+    int *fexp;                // and their exponent
+    long long n_coeffs;
     long long vec_node_off;   // offset of this problem's nodes in batched node vectors
     long long vec_coef_off;   // offset of this problem's coefficients in batched coefficient vectors
 };
@@ -237,6 +240,11 @@ int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f);
 // Sorted forward (gather_sorted.cu): order-1/2 terms over the cell-sorted
 // records, accumulated into f with atomics; f must hold the other terms' sum.
 int launch_gather_sorted_f32(Plan &p, const float2 *fhat, float2 *f);
+// The same for one problem (B.plans == null) or a batch of P problems, every one
+// with records and accumulators: f = empty-set coefficient + all terms.
+int gather_sorted_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *fhat,
+                         float2 *f, const int4 *items, int item_begin, int item_end, int *counter,
+                         long long max_grid_bytes, long long max_M, int sm_count, int mr, double *part);
 int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
                    float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks, int mr,

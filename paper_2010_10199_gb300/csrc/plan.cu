@@ -207,6 +207,9 @@ DevPlan dev_view(const Plan &p) {
     v.partials = (float2 *)p.partials;
     v.spread_chunks = p.spread_K;
     v.srec = p.srec;
+    v.facc = p.facc;
+    v.fexp = p.fexp;
+    v.n_coeffs = p.n_coeffs;
     v.vec_node_off = 0;
     v.vec_coef_off = 0;
     return v;

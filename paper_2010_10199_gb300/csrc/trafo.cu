@@ -213,23 +213,10 @@ int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f) {
     if (e != cudaSuccess) return cuda_status(e);
     stage_begin(p, ST_GATHER);
     int rc;
-    if (p.srec && p.facc && p.precision == ANOVA_PREC_F32 && p.n_act3 < p.n_act) {
-        // third-order terms (if any) point-major, writing f; then the others
-        // over the cell-sorted records, added to f
-        if (p.n_act3 > 0) {
-            Plan q = p;
-            q.act_rec = p.act_rec3;
-            q.n_act = p.n_act3;
-            rc = launch_gather_f32(q, fhat, f);
-        } else {
-            const int blocks = (int)std::min<long long>(1024, (p.M + 255) / 256);
-            fill_const_f32<<<blocks, 256, 0, p.stream>>>(f, p.M, fhat, p.empty_off, p.n_empty, p.skip);
-            rc = cuda_status(cudaGetLastError());
-        }
-        if (!rc) rc = launch_gather_sorted_f32(p, fhat, f);
-    } else {
+    if (p.srec && p.facc && p.precision == ANOVA_PREC_F32 && p.n_act3 == 0)
+        rc = launch_gather_sorted_f32(p, fhat, f);   // every term over its cell-sorted records
+    else
         rc = launch_gather_f32(p, fhat, f);
-    }
     stage_end(p, ST_GATHER);
     return rc;
 }

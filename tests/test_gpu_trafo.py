@@ -91,12 +91,16 @@ def test_c2_subsample_all_terms(gft):
     _pair_check(gft, w["x"], w["terms"], w["bandwidths"], fhat=w["fhat"], y=w["y"])
 
 
-def test_third_order_terms(gft):
+@pytest.mark.parametrize("node_sort", [0, -1])
+def test_third_order_terms(gft, node_sort):
+    """Third-order terms through the cell-sorted kernels (two records per
+    node, indices modulo n) and through the point-major gather and the
+    original-order spread."""
     d = 4
     x = inputs.beta22_points(3, d, 3000)
     terms = anova.term_set(d, 3)
     bw = [0] + [20] * 4 + [12] * 6 + [10] * 4
-    _pair_check(gft, x, terms, bw)
+    _pair_check(gft, x, terms, bw, node_sort=node_sort)
 
 
 def test_mixed_bandwidths_and_orders(gft):
