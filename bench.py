@@ -282,7 +282,7 @@ def run_mine(args, rank, world, local_rank):
     grid_bytes = grid_bytes * esz // 8
     sfx = "_f64" if f64 else "_f32"
     if gms / max(gl, 1) >= sms / max(sl, 1):
-        kname, kms, klaunch = ("gather_f64" if f64 else "gather2_f32"), gms / max(gl, 1), gl
+        kname, kms, klaunch = ("gather_f64" if f64 else "gather_sorted_f32"), gms / max(gl, 1), gl
         # nodes read (one real per coordinate), f written, grids and coefficients read once
         alg_bytes = rs * d * M + esz * M + grid_bytes + esz * n
     else:
@@ -311,8 +311,10 @@ def run_mine(args, rank, world, local_rank):
                        "peak_basis": "152 SMs x 128 B/clk x median SM clock in the timed region"}}
 
     launches = 0
-    per_stage_kernels = {"trafo_pre": 1, "gather": 1, "spread": 1, "reduce_partials": 1, "adjoint_post": 1,
-                         "empty_sum": 2, "solver_vec": 1}
+    # the FP32 forward stage launches the fixed-point passes around the sorted gather
+    # (partial sums, exponent, initialisation, gather, finish)
+    per_stage_kernels = {"trafo_pre": 1, "gather": 1 if f64 else 5, "spread": 1, "reduce_partials": 1,
+                         "adjoint_post": 1, "empty_sum": 2, "solver_vec": 1}
     for name, (_, cnt) in prof.items():
         launches += cnt * per_stage_kernels.get(name, 1)
 

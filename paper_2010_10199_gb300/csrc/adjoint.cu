@@ -26,7 +26,7 @@ __device__ __forceinline__ void red_add(float *addr, float v) {
 
 __device__ __forceinline__ int freq_index_a(int q, int N) { return q < N / 2 ? q - N / 2 : q - N / 2 + 1; }
 
-constexpr int SP_CH = 512;   // nodes staged per block of a work item
+constexpr int SP_CH = 512;   // nodes staged per block of a work item (order 1/2: SP_CH or SP_CH / 2)
 
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
@@ -39,23 +39,46 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // staging area after the grid: the larger of the unsorted layout
-// (float4 [2][SP_CH]) and the sorted one (float4 [3][SP_CH] node records,
-// float2 [2][SP_CH] values of y)
-constexpr size_t SP_STAGE_BYTES = 3 * SP_CH * 16 + 2 * SP_CH * 8;
-static_assert(SP_STAGE_BYTES >= 2 * SP_CH * 16, "staging area");
+// (float4 [2][SP]) and the sorted one (float4 [3][SP] node records, float2
+// [2][SP] values of y), SP nodes per block
+__host__ __device__ constexpr size_t sp_stage_bytes(int sp) { return (size_t)sp * (3 * 16 + 2 * 8); }
+// third-order items (spread3_f32): 8 warp runs of 32 nodes, two records each
+constexpr size_t SP3_STAGE_BYTES = 3 * 256 * 32 + 2 * 256 * 8;
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
-size_t spread_smem_bytes(long long max_grid_bytes) {
-    return (size_t)max_grid_bytes + SP_STAGE_BYTES + 16;   // grid, node blocks, item slot
+// shared memory of spread_f32 (o3 = false, sp nodes per block) or spread3_f32:
+// grid, node blocks, item slot
+size_t spread_smem_bytes(long long max_grid_bytes, bool o3, int sp) {
+    return (size_t)max_grid_bytes + (o3 ? SP3_STAGE_BYTES : sp_stage_bytes(sp)) + 16;
+}
+
+// CTAs per SM that shared memory allows for spread_f32 with sp-node blocks
+static size_t smem_ctas(long long max_grid_bytes, int sp) {
+    const size_t per = spread_smem_bytes(max_grid_bytes, false, sp) + 1024;   // + the per-CTA reserve
+    return (size_t)(MAX_SMEM + 1024) / per;
+}
+
+// CTAs per SM of spread_f32 with sp-node blocks: at most 4 (64 registers) for
+// SP_CH / 2, 3 (80 registers) for SP_CH
+static int ctas_for(long long max_grid_bytes, int sp) {
+    const size_t cap = sp == SP_CH ? 3 : SPREAD_MAX_CTAS_PER_SM;
+    return (int)std::max<size_t>(1, std::min(cap, smem_ctas(max_grid_bytes, sp)));
+}
+
+// nodes per staging block.  The larger block runs best where registers, not
+// shared memory, hold it at 3 CTAs per SM (small grids); where the grids fill
+// shared memory, the smaller block gains a fourth CTA per SM (measured on the
+// d = 20 workloads: bandwidths 64/32 gain, 32/16 lose with the smaller block).
+int spread_block_nodes(long long max_grid_bytes) {
+    const bool smem_bound = smem_ctas(max_grid_bytes, SP_CH) < (size_t)SPREAD_MAX_CTAS_PER_SM;
+    return smem_bound && ctas_for(max_grid_bytes, SP_CH / 2) > ctas_for(max_grid_bytes, SP_CH) ? SP_CH / 2 : SP_CH;
 }
 
 int spread_ctas_per_sm(long long max_grid_bytes) {
-    // shared memory per CTA plus the 1 KB the hardware reserves per CTA
-    const size_t per = spread_smem_bytes(max_grid_bytes) + 1024;
-    return (int)std::max<size_t>(1, std::min<size_t>(SPREAD_MAX_CTAS_PER_SM, (size_t)(MAX_SMEM + 1024) / per));
+    return ctas_for(max_grid_bytes, spread_block_nodes(max_grid_bytes));
 }
 
 int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count) {
@@ -99,27 +122,27 @@ __device__ __forceinline__ void node_weights(const float wcf[NCOEF], float vrow,
 // rows r, r + 2, ..), two nodes per step, and adds the sums to the shared
 // grid when the cell changes and at the end of its run.  Order 1: the lane
 // groups r = 0, 1 take alternate nodes of the run.
-template <int MR>
+template <int MR, int SP>
 __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                    long long j0, long long j1, float2 *S, unsigned char *stg_raw,
                                                    const float wcf[NCOEF]) {
-    constexpr int RUN = SP_CH / 16;
+    constexpr int RUN = SP / 16;
     const int tid = threadIdx.x;
     const int lane = tid & 31, half = lane >> 4, sub = lane & 15;
     const int r = sub >> 3, k = sub & 7;
     const int hw = (tid >> 5) * 2 + half;
     const int stride = T.stride;
     const float4 *src = P.srec + (long long)T.sort_slot * P.M + j0;
-    float4 *rbuf = (float4 *)stg_raw;            // [3][SP_CH]
-    float2 *ybuf = (float2 *)(rbuf + 3 * SP_CH); // [2][SP_CH]
+    float4 *rbuf = (float4 *)stg_raw;            // [3][SP]
+    float2 *ybuf = (float2 *)(rbuf + 3 * SP); // [2][SP]
     const long long len = j1 - j0;
     const long long L = (len + 15) / 16;           // run length
     const long long nblk = (L + RUN - 1) / RUN;
     // records of run h: [h L, min((h+1) L, len))
     auto run_len = [&](int h) { return max(0LL, min(L, len - (long long)h * L)); };
     auto stage_a = [&](long long c) {
-        const int b = (int)(c % 3) * SP_CH;
-        for (int e = tid; e < SP_CH; e += SPREAD_THREADS) {
+        const int b = (int)(c % 3) * SP;
+        for (int e = tid; e < SP; e += SPREAD_THREADS) {
             const int h = e / RUN, t = e % RUN;
             const long long q = c * RUN + t;
             if (q < run_len(h)) cp_async16(&rbuf[b + e], src + (long long)h * L + q);
@@ -127,8 +150,8 @@ __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term 
     };
     // reads records this thread staged itself (same e), so its own wait suffices
     auto stage_b = [&](long long c) {
-        const int b = (int)(c % 3) * SP_CH, yb = (int)(c & 1) * SP_CH;
-        for (int e = tid; e < SP_CH; e += SPREAD_THREADS) {
+        const int b = (int)(c % 3) * SP, yb = (int)(c & 1) * SP;
+        for (int e = tid; e < SP; e += SPREAD_THREADS) {
             const int h = e / RUN, t = e % RUN;
             if (c * RUN + t < run_len(h)) cp_async8(&ybuf[yb + e], y + __float_as_int(rbuf[b + e].w));
         }
@@ -168,8 +191,8 @@ __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term 
         cp_async_commit();
         if (c + 2 < nblk) stage_a(c + 2);
         cp_async_commit();
-        const float4 *rb = rbuf + (int)(c % 3) * SP_CH + hw * RUN;
-        const float2 *yb = ybuf + (int)(c & 1) * SP_CH + hw * RUN;
+        const float4 *rb = rbuf + (int)(c % 3) * SP + hw * RUN;
+        const float2 *yb = ybuf + (int)(c & 1) * SP + hw * RUN;
         const long long left = my_len - c * RUN;   // records of this run still to come
         if (T.order == 2) {
             // both half-warps of a warp run all steps (shuffles); a node past
@@ -249,7 +272,7 @@ __device__ __forceinline__ void spread_sorted_item(const DevPlan &P, const Term 
 // coordinate's taps, lanes 8..15 the second's; shuffles hand them round.
 constexpr int SP3_RUN = 32;                     // nodes per warp and block
 constexpr int SP3_BLK = SP3_RUN * (SPREAD_THREADS / 32);
-static_assert(3 * SP3_BLK * 32 + 2 * SP3_BLK * 8 <= SP_STAGE_BYTES, "third-order staging");
+static_assert(3 * SP3_BLK * 32 + 2 * SP3_BLK * 8 <= SP3_STAGE_BYTES, "third-order staging");
 
 template <int MR>
 __device__ __forceinline__ void spread_sorted_item3(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
@@ -369,7 +392,7 @@ __device__ __forceinline__ void spread_sorted_item3(const DevPlan &P, const Term
 // in their original order, staged as float4 (first-row coordinate, last
 // coordinate, y) one block ahead; every node adds its window to the shared
 // grid with shared-memory atomics.
-template <int MR, bool O3>
+template <int MR, bool O3, int SP>
 __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                      long long j0, long long j1, float2 *S, unsigned char *stg_raw,
                                                      const float wcf[NCOEF]) {
@@ -380,16 +403,16 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
     constexpr int NW = SPREAD_THREADS / 32;
     const int order = T.order, n = T.n, stride = T.stride;
     const long long M = P.M;
-    float4 *stage = (float4 *)stg_raw;   // [2][SP_CH]
+    float4 *stage = (float4 *)stg_raw;   // [2][SP]
     const float *__restrict__ X = P.x;
     const float *xr = X + (long long)(order >= 2 ? T.row0 : T.col) * M;
     const float *xc = X + (long long)T.col * M;
     const float *xr1 = order == 3 ? X + (long long)T.row1 * M : nullptr;
-    const long long nblk = (j1 - j0 + SP_CH - 1) / SP_CH;
+    const long long nblk = (j1 - j0 + SP - 1) / SP;
     auto stage_block = [&](long long c, int buf) {
-        const long long a = j0 + c * SP_CH;
-        const int cnt = (int)min((long long)SP_CH, j1 - a);
-        float4 *dst = stage + buf * SP_CH;
+        const long long a = j0 + c * SP;
+        const int cnt = (int)min((long long)SP, j1 - a);
+        float4 *dst = stage + buf * SP;
         for (int e = tid; e < cnt; e += SPREAD_THREADS) {
             const long long j = a + e;
             cp_async4(&dst[e].x, xr + j);
@@ -404,9 +427,9 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
         cp_async_commit();
         cp_async_wait1();
         __syncthreads();
-        const float4 *stg = stage + (int)(c & 1) * SP_CH;
-        const long long a = j0 + c * SP_CH;
-        const int cnt = (int)min((long long)SP_CH, j1 - a);
+        const float4 *stg = stage + (int)(c & 1) * SP;
+        const long long a = j0 + c * SP;
+        const int cnt = (int)min((long long)SP, j1 - a);
         if (order == 2) {
             for (int i0 = 2 * warp; i0 < cnt; i0 += 2 * NW) {
                 const int i = i0 + half;
@@ -494,14 +517,14 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
 // the original order) into a shared-memory copy of the term's stored grid
 // (halos included) and writes it to partial grid z of its problem.  CTAs take
 // items from a global counter.
-template <int MR, typename G, bool O3>
+template <int MR, typename G, bool O3, int SP>
 __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchArgs &B,
                                              const float2 *__restrict__ y_base, int item_begin, int item_end,
                                              int *counter, long long max_grid_bytes) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *S = (float2 *)smem_raw;
     unsigned char *stg_raw = smem_raw + max_grid_bytes;
-    int &s_item = *(int *)(stg_raw + SP_STAGE_BYTES);
+    int &s_item = *(int *)(stg_raw + (O3 ? SP3_STAGE_BYTES : sp_stage_bytes(SP)));
     const int tid = threadIdx.x;
     const int k = tid & 7;
     for (;;) {
@@ -534,12 +557,12 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
             if (T.sort_slot >= 0 && P.srec)
                 spread_sorted_item3<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
             else
-                spread_unsorted_item<MR, true>(P, T, y, j0, j1, S, stg_raw, wcf);
+                spread_unsorted_item<MR, true, SP>(P, T, y, j0, j1, S, stg_raw, wcf);
         } else {
             if (T.sort_slot >= 0 && P.srec)
-                spread_sorted_item<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
+                spread_sorted_item<MR, SP>(P, T, y, j0, j1, S, stg_raw, wcf);
             else
-                spread_unsorted_item<MR, false>(P, T, y, j0, j1, S, stg_raw, wcf);
+                spread_unsorted_item<MR, false, SP>(P, T, y, j0, j1, S, stg_raw, wcf);
         }
         __syncthreads();
         if constexpr (std::is_same<G, float2>::value) {
@@ -555,18 +578,18 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
 
 // the order-1/2 items (3 CTAs per SM) and the third-order items (more
 // registers for the 2 x 2 m_row row-pair sums, 2 CTAs per SM)
-template <int MR, typename G>
-__global__ void __launch_bounds__(SPREAD_THREADS, 3)
+template <int MR, typename G, int SP>
+__global__ void __launch_bounds__(SPREAD_THREADS, SP == SP_CH ? 3 : SPREAD_MAX_CTAS_PER_SM)
 spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
            int *counter, long long max_grid_bytes) {
-    spread_items<MR, G, false>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
+    spread_items<MR, G, false, SP>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
 }
 
 template <int MR, typename G>
 __global__ void __launch_bounds__(SPREAD_THREADS, 2)
 spread3_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
             int *counter, long long max_grid_bytes) {
-    spread_items<MR, G, true>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
+    spread_items<MR, G, true, SP_CH / 2>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
 }
 
 template <typename G>
@@ -787,8 +810,10 @@ static void adjoint_attrs() {
     static bool attr_done = false;
     if (!attr_done) {
         cudaFuncSetAttribute(adjoint_post_f32<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(spread_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        cudaFuncSetAttribute(spread_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_f32<3, G, SP_CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_f32<4, G, SP_CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_f32<3, G, SP_CH / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_f32<4, G, SP_CH / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         attr_done = true;
@@ -802,23 +827,23 @@ static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const
                             const float2 *y, float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks,
                             int mr, long long sgrid, int max_fft_elems, int sm_count, long long max_grid_elems) {
     adjoint_attrs<G>();
-    const size_t ssm = spread_smem_bytes(sgrid);
+    const int sp = spread_block_nodes(sgrid);
+    const size_t ssm = spread_smem_bytes(sgrid, false, sp), ssm3 = spread_smem_bytes(sgrid, true, sp);
     const int per_sm = spread_ctas_per_sm(sgrid);
     if (prof) stage_begin(*prof, ST_SPREAD);
     cudaMemsetAsync(counter, 0, 2 * sizeof(int), st);
     if (n_items3 > 0) {
         const int c3 = std::max(1, std::min(n_items3, std::min(per_sm, 2) * sm_count));
         if (mr <= 3)
-            spread3_f32<3, G><<<c3, SPREAD_THREADS, ssm, st>>>(v, B, y, 0, n_items3, counter, sgrid);
+            spread3_f32<3, G><<<c3, SPREAD_THREADS, ssm3, st>>>(v, B, y, 0, n_items3, counter, sgrid);
         else
-            spread3_f32<4, G><<<c3, SPREAD_THREADS, ssm, st>>>(v, B, y, 0, n_items3, counter, sgrid);
+            spread3_f32<4, G><<<c3, SPREAD_THREADS, ssm3, st>>>(v, B, y, 0, n_items3, counter, sgrid);
     }
     if (n_items > n_items3) {
         const int c = std::max(1, std::min(n_items - n_items3, per_sm * sm_count));
-        if (mr <= 3)
-            spread_f32<3, G><<<c, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items3, n_items, counter + 1, sgrid);
-        else
-            spread_f32<4, G><<<c, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items3, n_items, counter + 1, sgrid);
+        auto k = mr <= 3 ? (sp == SP_CH ? spread_f32<3, G, SP_CH> : spread_f32<3, G, SP_CH / 2>)
+                         : (sp == SP_CH ? spread_f32<4, G, SP_CH> : spread_f32<4, G, SP_CH / 2>);
+        k<<<c, SPREAD_THREADS, ssm, st>>>(v, B, y, n_items3, n_items, counter + 1, sgrid);
     }
     if (prof) stage_end(*prof, ST_SPREAD);
     const long long n4 = max_grid_elems / 2;

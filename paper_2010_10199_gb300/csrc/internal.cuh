@@ -250,7 +250,8 @@ int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArg
                    float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks, int mr,
                    long long max_grid_bytes, int max_fft_elems, int sm_count, long long max_grid_elems,
                    bool any_empty, double2 *scratch, int prec);
-size_t spread_smem_bytes(long long max_grid_bytes);
+size_t spread_smem_bytes(long long max_grid_bytes, bool o3, int sp);
+int spread_block_nodes(long long max_grid_bytes);
 // Sorts the nodes by grid cell for every term with sort_slot >= 0 (sort.cu).
 int sort_nodes_by_cell(Plan &p);
 // FP64 path (f64.cu): window tables, forward and adjoint transforms.
