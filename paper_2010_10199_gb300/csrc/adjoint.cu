@@ -26,6 +26,9 @@ __device__ __forceinline__ void red_add(float *addr, float v) {
 
 __device__ __forceinline__ int freq_index_a(int q, int N) { return q < N / 2 ? q - N / 2 : q - N / 2 + 1; }
 
+enum { SK_STAGED = 0, SK_ORDER3 = 1, SK_MMA = 2 };
+constexpr int SPREAD_MMA_CTAS_PER_SM = 3;   // 80 registers
+
 constexpr int SP_CH = 512;   // nodes staged per block of a work item (order 1/2: SP_CH or SP_CH / 2)
 
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
@@ -37,6 +40,10 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // staging area after the grid: the larger of the unsorted layout
 // (float4 [2][SP]) and the sorted one (float4 [3][SP] node records, float2
@@ -77,12 +84,19 @@ int spread_block_nodes(long long max_grid_bytes) {
     return smem_bound && ctas_for(max_grid_bytes, SP_CH / 2) > ctas_for(max_grid_bytes, SP_CH) ? SP_CH / 2 : SP_CH;
 }
 
-int spread_ctas_per_sm(long long max_grid_bytes) {
+// the tensor-core kernel: grid, one ring per warp, item slot
+static size_t spread_mma_smem_bytes(long long max_grid_bytes);
+
+int spread_ctas_per_sm(long long max_grid_bytes, bool tc) {
+    if (tc) {
+        const size_t per = spread_mma_smem_bytes(max_grid_bytes) + 1024;
+        return (int)std::max<size_t>(1, std::min<size_t>(SPREAD_MMA_CTAS_PER_SM, (size_t)(MAX_SMEM + 1024) / per));
+    }
     return ctas_for(max_grid_bytes, spread_block_nodes(max_grid_bytes));
 }
 
-int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count) {
-    const long long resident = (long long)spread_ctas_per_sm(max_grid_bytes) * sm_count;
+int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc) {
+    const long long resident = (long long)spread_ctas_per_sm(max_grid_bytes, tc) * sm_count;
     long long K = (3 * resident + std::max(1, n_act_total) - 1) / std::max(1, n_act_total);
     K = std::min<long long>(K, (M + 2047) / 2048);
     K = std::min<long long>(K, kmax);
@@ -511,20 +525,214 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
     cp_async_wait0();
 }
 
+// ---- Tensor-core cell sums (order 1/2 terms with cell-sorted records) ----
+//
+// For the nodes j of one cell the contributions to its m_row x 8 window are
+//     G[r][k] += sum_j y_j psi_row,r(j) psi_col,k(j),
+// a product A B with A[(k, re/im)][j] = y_j psi_col,k(j) (16 x n) and
+// B[j][r] = psi_row,r(j) (n x 8).  A warp runs mma.m16n8k8 over groups of 8
+// cell-sorted nodes: lane (g, t) = (lane / 4, lane % 4) evaluates column tap g
+// and row tap g of nodes t and t + 4 (the fragment layout of the PTX ISA for
+// tf32 m16n8k8), so weights never leave the registers that feed the tensor
+// core.  Each operand is split x = hi + lo into TF32 parts and the product is
+// hi*hi + hi*lo + lo*hi (relative error near 2^-21); the three products of a
+// group are summed by the tensor core, the groups in FP32 registers.  A
+// group holding nodes of several cells is run once per cell with the other
+// nodes masked; the 16 x 8 accumulator goes to the shared grid by
+// shared-memory additions whenever the cell changes.
+
+// x = hi + lo for finite x: hi keeps the sign, the exponent and the leading
+// 10 mantissa bits of x rounded half away from zero (adding half a unit of
+// the 10th bit to the bit pattern carries into the exponent where it should),
+// lo = x - hi is exact in FP32; the tensor core reads the leading 10 mantissa
+// bits of lo (error below 2^-21 |x|)
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
+    hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Records rec[0, n) of one term for one warp, in steps of 16 (two groups of
+// 8 for the tensor core).  The warp's own ring in shared memory (MMA_RING
+// steps of records and of values y) is filled by lanes 0..15 with cp.async:
+// the records MMA_DR steps ahead, the values y[index] MMA_DY steps ahead
+// (their addresses come from the records already in the ring).  Order 1:
+// B = e_0 (the single grid row), exact in TF32.
+constexpr int MMA_STEP = 16, MMA_RING = 4, MMA_DR = 3, MMA_DY = 1;
+constexpr size_t MMA_REC_BYTES = (size_t)MMA_RING * MMA_STEP * 16;             // float4 records
+constexpr size_t MMA_RING_BYTES = MMA_REC_BYTES + (size_t)MMA_RING * MMA_STEP * 8;  // + float2 values, per warp
+static_assert(MMA_DY < MMA_DR && MMA_DR < MMA_RING && (MMA_RING & (MMA_RING - 1)) == 0, "ring depths");
+
+static size_t spread_mma_smem_bytes(long long max_grid_bytes) {
+    return (size_t)max_grid_bytes + MMA_RING_BYTES * (SPREAD_THREADS / 32) + 16;
+}
+
+template <int MR, bool ORD2>
+__device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, const float2 *__restrict__ y, int n,
+                                               float2 *S, int stride, const float ccf[NCOEF], const float rcf[NCOEF],
+                                               float4 *rring, float2 *yring) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int ns = (n + MMA_STEP - 1) / MMA_STEP;
+    int cur = -1;   // grid offset of the cell being summed
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    // d = (re row 2t, re row 2t + 1, im row 2t, im row 2t + 1) of column g
+    auto flush = [&]() {
+        float *c = (float *)(S + cur + g);
+        if (ORD2) {
+            if (2 * t < 2 * MR) {
+                red_add(c + 4 * t * stride, d[0]);
+                red_add(c + 4 * t * stride + 1, d[2]);
+                red_add(c + (4 * t + 2) * stride, d[1]);
+                red_add(c + (4 * t + 2) * stride + 1, d[3]);
+            }
+        } else if (t == 0) {
+            red_add(c, d[0]);
+            red_add(c + 1, d[2]);
+        }
+        d[0] = d[1] = d[2] = d[3] = 0.f;
+    };
+    // tensor-core products of one group added to e (hi*lo terms first)
+    auto group_mma = [&](float (&e)[4], float a0, float a1, float a2, float a3, unsigned bh0, unsigned bl0,
+                         unsigned bh1, unsigned bl1) {
+        unsigned ah[4], al[4];
+        split_tf32(a0, ah[0], al[0]);
+        split_tf32(a1, ah[1], al[1]);
+        split_tf32(a2, ah[2], al[2]);
+        split_tf32(a3, ah[3], al[3]);
+        mma_tf32(e, al, bh0, bh1);
+        if (ORD2) mma_tf32(e, ah, bl0, bl1);
+        mma_tf32(e, ah, bh0, bh1);
+    };
+    // A fresh tensor-core sum per step (at most two groups), added to d in
+    // FP32 with rounding to nearest: the tensor core's own accumulation is
+    // not rounded to nearest, and its bias would grow with the cell's node
+    // count.
+    for (int i = -MMA_DR; i < ns; ++i) {
+        // iteration i commits one cp.async group: the records of step
+        // i + MMA_DR and the values of step i + MMA_DY; steps i < 0 fill the ring
+        if (lane < MMA_STEP) {
+            const int qr = i + MMA_DR, qy = i + MMA_DY;
+            if (qr < ns)
+                cp_async16(&rring[(qr & (MMA_RING - 1)) * MMA_STEP + lane], rec + min(MMA_STEP * qr + lane, n - 1));
+            if (qy >= 0 && qy < ns) {
+                // the records of step qy were committed MMA_DR - MMA_DY iterations ago
+                cp_async_wait_n<MMA_DR - MMA_DY - 1>();
+                const int j = __float_as_int(rring[(qy & (MMA_RING - 1)) * MMA_STEP + lane].w);
+                cp_async8(&yring[(qy & (MMA_RING - 1)) * MMA_STEP + lane], y + j);
+            }
+        }
+        cp_async_commit();
+        if (i < 0) continue;
+        cp_async_wait_n<MMA_DY>();   // values of step i (and its records) have landed
+        __syncwarp();
+        float e[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int base = MMA_STEP * i + 8 * h;   // first node of this group (may be past the end)
+            const int sl = (i & (MMA_RING - 1)) * MMA_STEP + 8 * h;
+            const float4 r0 = rring[sl + t], r1 = rring[sl + t + 4];
+            const float2 y0 = yring[sl + t], y1 = yring[sl + t + 4];
+            const float wc0 = horner8(ccf, r0.y), wc1 = horner8(ccf, r1.y);
+            unsigned bh0, bl0, bh1, bl1;
+            if (ORD2) {
+                split_tf32(g < 2 * MR ? horner8(rcf, r0.x) : 0.f, bh0, bl0);
+                split_tf32(g < 2 * MR ? horner8(rcf, r1.x) : 0.f, bh1, bl1);
+            } else {
+                bh0 = bh1 = g == 0 ? 0x3f800000u : 0u;
+                bl0 = bl1 = 0u;
+            }
+            const int off0 = __float_as_int(r0.z), off1 = __float_as_int(r1.z);
+            if (__all_sync(0xffffffffu, base + 8 <= n && off0 == cur && off1 == cur)) {
+                // the whole group lies in the cell being summed
+                group_mma(e, y0.x * wc0, y0.y * wc0, y1.x * wc1, y1.y * wc1, bh0, bl0, bh1, bl1);
+            } else {
+                // past the end the ring holds the last record again: masked here
+                bool p0 = base + t < n, p1 = base + t + 4 < n;   // nodes t, t + 4 not yet added
+                for (;;) {
+                    const unsigned pm =
+                        (__ballot_sync(0xffffffffu, p0) & 0xfu) | ((__ballot_sync(0xffffffffu, p1) & 0xfu) << 4);
+                    if (!pm) break;
+                    const int f = __ffs(pm) - 1;   // first node not yet added; its cell is next
+                    const int oc = __shfl_sync(0xffffffffu, f < 4 ? off0 : off1, f & 3);
+                    const bool e0 = p0 && off0 == oc, e1 = p1 && off1 == oc;
+                    if (oc != cur) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            d[q] += e[q];
+                            e[q] = 0.f;
+                        }
+                        if (cur >= 0) flush();
+                        cur = oc;
+                    }
+                    group_mma(e, e0 ? y0.x * wc0 : 0.f, e0 ? y0.y * wc0 : 0.f, e1 ? y1.x * wc1 : 0.f,
+                              e1 ? y1.y * wc1 : 0.f, bh0, bl0, bh1, bl1);
+                    p0 = p0 && !e0;
+                    p1 = p1 && !e1;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] += e[q];
+        __syncwarp();   // ring slot i is read before a later iteration refills it
+    }
+    cp_async_wait0();
+    if (cur >= 0) flush();
+}
+
+// Sorted item of order 1/2 on the tensor cores: the item's records are cut
+// into 8 contiguous runs (multiples of 8 nodes), one per warp.
+template <int MR>
+__device__ __forceinline__ void spread_mma_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
+                                                long long j0, long long j1, float2 *S, unsigned char *stg_raw) {
+    const int warp = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
+    float ccf[NCOEF], rcf[NCOEF];
+    {
+        const float *cs = P.windows[T.wc].c[g];
+        const float *rs = P.windows[T.wr].c[min(g, 2 * MR - 1)];
+#pragma unroll
+        for (int q = 0; q < NCOEF; ++q) {
+            ccf[q] = __ldg(cs + q);
+            rcf[q] = __ldg(rs + q);
+        }
+    }
+    constexpr int NW = SPREAD_THREADS / 32;
+    const long long len = j1 - j0, per = (len + 8 * NW - 1) / (8 * NW) * 8;
+    const long long a = j0 + warp * per, b = min(j1, a + per);
+    if (a >= b) return;
+    const float4 *rec = P.srec + (long long)T.sort_slot * P.M + a;
+    unsigned char *ring = stg_raw + warp * MMA_RING_BYTES;
+    float4 *rring = (float4 *)ring;
+    float2 *yring = (float2 *)(ring + MMA_REC_BYTES);
+    if (T.order == 2)
+        spread_mma_run<MR, true>(rec, y, (int)(b - a), S, T.stride, ccf, rcf, rring, yring);
+    else
+        spread_mma_run<MR, false>(rec, y, (int)(b - a), S, T.stride, ccf, rcf, rring, yring);
+}
+
 // One work item (x = problem, y = active term, z = node chunk, w = chunks per
 // term) spreads nodes [M z / w, M (z+1) / w) of one term (in the term's cell
 // order if the plan keeps sorted copies and the term has order <= 2, else in
 // the original order) into a shared-memory copy of the term's stored grid
 // (halos included) and writes it to partial grid z of its problem.  CTAs take
 // items from a global counter.
-template <int MR, typename G, bool O3, int SP>
+// KIND: SK_STAGED (order 1/2 on the CUDA cores), SK_ORDER3, SK_MMA (order 1/2
+// with records on the tensor cores; no staging area)
+template <int MR, typename G, int KIND, int SP>
 __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchArgs &B,
                                              const float2 *__restrict__ y_base, int item_begin, int item_end,
                                              int *counter, long long max_grid_bytes) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *S = (float2 *)smem_raw;
     unsigned char *stg_raw = smem_raw + max_grid_bytes;
-    int &s_item = *(int *)(stg_raw + (O3 ? SP3_STAGE_BYTES : sp_stage_bytes(SP)));
+    constexpr bool O3 = KIND == SK_ORDER3;
+    int &s_item = *(int *)(stg_raw + (KIND == SK_MMA ? MMA_RING_BYTES * (SPREAD_THREADS / 32)
+                                                     : O3 ? SP3_STAGE_BYTES : sp_stage_bytes(SP)));
     const int tid = threadIdx.x;
     const int k = tid & 7;
     for (;;) {
@@ -546,14 +754,16 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
         // window coefficients of this lane: row tap k for lanes r = 1 of an
         // order-2 term (see node_weights), column tap k otherwise
         float wcf[NCOEF];
-        {
+        if constexpr (KIND != SK_MMA) {
             const bool row = T.order == 2 && (tid & 8);
             const float *wsrc = row ? P.windows[T.wr].c[min(k, 2 * MR - 1)] : P.windows[T.wc].c[k];
 #pragma unroll
             for (int i = 0; i < NCOEF; ++i) wcf[i] = __ldg(wsrc + i);
         }
         __syncthreads();   // grid zeroed before any addition
-        if constexpr (O3) {
+        if constexpr (KIND == SK_MMA) {
+            spread_mma_item<MR>(P, T, y, j0, j1, S, stg_raw);
+        } else if constexpr (O3) {
             if (T.sort_slot >= 0 && P.srec)
                 spread_sorted_item3<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
             else
@@ -582,14 +792,22 @@ template <int MR, typename G, int SP>
 __global__ void __launch_bounds__(SPREAD_THREADS, SP == SP_CH ? 3 : SPREAD_MAX_CTAS_PER_SM)
 spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
            int *counter, long long max_grid_bytes) {
-    spread_items<MR, G, false, SP>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
+    spread_items<MR, G, SK_STAGED, SP>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
+}
+
+// order-1/2 items of plans with cell-sorted records, on the tensor cores
+template <int MR, typename G>
+__global__ void __launch_bounds__(SPREAD_THREADS, SPREAD_MMA_CTAS_PER_SM)
+spread_mma_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
+               int *counter, long long max_grid_bytes) {
+    spread_items<MR, G, SK_MMA, 0>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
 }
 
 template <int MR, typename G>
 __global__ void __launch_bounds__(SPREAD_THREADS, 2)
 spread3_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
             int *counter, long long max_grid_bytes) {
-    spread_items<MR, G, true, SP_CH / 2>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
+    spread_items<MR, G, SK_ORDER3, SP_CH / 2>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
 }
 
 template <typename G>
@@ -815,6 +1033,8 @@ static void adjoint_attrs() {
         cudaFuncSetAttribute(spread_f32<3, G, SP_CH / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread_f32<4, G, SP_CH / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_mma_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_mma_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         attr_done = true;
     }
@@ -825,11 +1045,12 @@ static void adjoint_attrs() {
 template <typename G>
 static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P,
                             const float2 *y, float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks,
-                            int mr, long long sgrid, int max_fft_elems, int sm_count, long long max_grid_elems) {
+                            int mr, long long sgrid, int max_fft_elems, int sm_count, long long max_grid_elems,
+                            bool tc) {
     adjoint_attrs<G>();
     const int sp = spread_block_nodes(sgrid);
     const size_t ssm = spread_smem_bytes(sgrid, false, sp), ssm3 = spread_smem_bytes(sgrid, true, sp);
-    const int per_sm = spread_ctas_per_sm(sgrid);
+    const int per_sm = spread_ctas_per_sm(sgrid, false);
     if (prof) stage_begin(*prof, ST_SPREAD);
     cudaMemsetAsync(counter, 0, 2 * sizeof(int), st);
     if (n_items3 > 0) {
@@ -839,7 +1060,11 @@ static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const
         else
             spread3_f32<4, G><<<c3, SPREAD_THREADS, ssm3, st>>>(v, B, y, 0, n_items3, counter, sgrid);
     }
-    if (n_items > n_items3) {
+    if (n_items > n_items3 && tc) {
+        const int c = std::max(1, std::min(n_items - n_items3, spread_ctas_per_sm(sgrid, true) * sm_count));
+        auto k = mr <= 3 ? spread_mma_f32<3, G> : spread_mma_f32<4, G>;
+        k<<<c, SPREAD_THREADS, spread_mma_smem_bytes(sgrid), st>>>(v, B, y, n_items3, n_items, counter + 1, sgrid);
+    } else if (n_items > n_items3) {
         const int c = std::max(1, std::min(n_items - n_items3, per_sm * sm_count));
         auto k = mr <= 3 ? (sp == SP_CH ? spread_f32<3, G, SP_CH> : spread_f32<3, G, SP_CH / 2>)
                          : (sp == SP_CH ? spread_f32<4, G, SP_CH> : spread_f32<4, G, SP_CH / 2>);
@@ -861,7 +1086,7 @@ static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
                    float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks, int mr,
                    long long max_grid_bytes, int max_fft_elems, int sm_count, long long max_grid_elems,
-                   bool any_empty, double2 *scratch, int prec) {
+                   bool any_empty, double2 *scratch, int prec, bool tc) {
     if (any_empty) {
         const int nb = 256;
         if (prof) stage_begin(*prof, ST_SUMY);
@@ -872,13 +1097,13 @@ int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArg
     if (n_blocks == 0) return cuda_status(cudaGetLastError());
     if (prec == ANOVA_PREC_F16)
         adjoint_kernels<__half2>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
-                                 2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems);
+                                 2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc);
     else if (prec == ANOVA_PREC_BF16)
         adjoint_kernels<__nv_bfloat162>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
-                                        2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems);
+                                        2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc);
     else
         adjoint_kernels<float2>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
-                                max_grid_bytes, max_fft_elems, sm_count, max_grid_elems);
+                                max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc);
     return cuda_status(cudaGetLastError());
 }
 
@@ -895,7 +1120,7 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
     for (int s = 0; s < p.n_terms; ++s) mr = p.h_terms[s].mr > 0 ? p.h_terms[s].mr : mr;
     return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.n_items, p.n_items3, p.counter, p.n_act, mr,
                           p.max_grid_bytes, p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0,
-                          (double2 *)p.scratch, p.precision);
+                          (double2 *)p.scratch, p.precision, p.srec && p.spread_tc);
 }
 
 }  // namespace agft

@@ -64,26 +64,55 @@ def test_ragged_sizes(gft, M):
     _pair_check(gft, x, terms, bw)
 
 
-@pytest.mark.parametrize("node_sort", [0, -1])
+SPREAD_PATHS = {"tensor": dict(node_sort=0, spread_kernel=0), "cuda": dict(node_sort=0, spread_kernel=1),
+                "unsorted": dict(node_sort=-1)}
+
+
+@pytest.mark.parametrize("path", list(SPREAD_PATHS))
 @pytest.mark.parametrize("chunks", [0, 1, 3])
-def test_spread_paths_and_chunking(gft, node_sort, chunks):
-    """The adjoint's two spread paths (cell-sorted copies of the nodes, or the
-    original order with per-node atomics) and several node chunks per term."""
+def test_spread_paths_and_chunking(gft, path, chunks):
+    """The adjoint's three spread paths (cell-sorted records with per-cell
+    sums on the tensor cores or on the CUDA cores, or the original order with
+    per-node atomics) and several node chunks per term."""
     x = inputs.uniform_points(17, 5, 9001)
     terms = anova.term_set(5, 2)
     bw = [0] + [64] * 5 + [32] * 10
-    _pair_check(gft, x, terms, bw, node_sort=node_sort, n_ctas=chunks)
+    _pair_check(gft, x, terms, bw, n_ctas=chunks, **SPREAD_PATHS[path])
 
 
-def test_clustered_nodes(gft):
+@pytest.mark.parametrize("path", ["tensor", "cuda"])
+def test_clustered_nodes(gft, path):
     """Nodes crowded into a few grid cells: long runs of one cell in the
-    sorted spread, and cells with a single node in between."""
+    sorted spread, and cells with a single node in between (groups of 8
+    nodes spanning several cells on the tensor cores)."""
     x = inputs.uniform_points(18, 4, 6000)
     x[:, :5000] = -0.2 + 1e-3 * x[:, :5000]
     x[1, 2500:5000] = 0.37
     terms = anova.term_set(4, 2)
     bw = [0] + [32] * 4 + [16] * 6
-    _pair_check(gft, x, terms, bw)
+    _pair_check(gft, x, terms, bw, **SPREAD_PATHS[path])
+
+
+@pytest.mark.parametrize("path", ["tensor", "cuda"])
+def test_long_cell_runs(gft, path):
+    """Thousands of nodes per grid cell (small bandwidths, M = 3e5): long
+    per-cell sums, whose rounding must not drift with the run length."""
+    x = inputs.uniform_points(20, 2, 300000)
+    terms = [(), (0,), (1,), (0, 1)]
+    bw = [0, 8, 4, 4]
+    _pair_check(gft, x, terms, bw, **SPREAD_PATHS[path])
+
+
+@pytest.mark.parametrize("path", ["tensor", "cuda"])
+def test_sparse_cells_and_wide_window(gft, path):
+    """Fewer nodes than cells (almost every group of 8 holds 8 cells) and the
+    8 x 8-tap window (eps below 5e-6: m_row = 4, all 8 row taps of the
+    tensor-core tile in use)."""
+    x = inputs.uniform_points(19, 3, 777)
+    terms = anova.term_set(3, 2)
+    bw = [0] + [64] * 3 + [48] * 3
+    _pair_check(gft, x, terms, bw, **SPREAD_PATHS[path])
+    _pair_check(gft, x, terms, bw, eps=1e-6, tol=3e-6, **SPREAD_PATHS[path])
 
 
 def test_c2_subsample_all_terms(gft):
