@@ -541,23 +541,6 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
 // nodes masked; the 16 x 8 accumulator goes to the shared grid by
 // shared-memory additions whenever the cell changes.
 
-// x = hi + lo for finite x: hi keeps the sign, the exponent and the leading
-// 10 mantissa bits of x rounded half away from zero (adding half a unit of
-// the 10th bit to the bit pattern carries into the exponent where it should),
-// lo = x - hi is exact in FP32; the tensor core reads the leading 10 mantissa
-// bits of lo (error below 2^-21 |x|)
-__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
-    hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
-    lo = __float_as_uint(x - __uint_as_float(hi));
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // Records rec[0, n) of one term for one warp, in steps of 16 (two groups of
 // 8 for the tensor core).  The warp's own ring in shared memory (MMA_RING
 // steps of records and of values y) is filled by lanes 0..15 with cp.async:
@@ -1120,7 +1103,7 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
     for (int s = 0; s < p.n_terms; ++s) mr = p.h_terms[s].mr > 0 ? p.h_terms[s].mr : mr;
     return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.n_items, p.n_items3, p.counter, p.n_act, mr,
                           p.max_grid_bytes, p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0,
-                          (double2 *)p.scratch, p.precision, p.srec && p.spread_tc);
+                          (double2 *)p.scratch, p.precision, p.srec && p.cell_tc);
 }
 
 }  // namespace agft

@@ -43,7 +43,7 @@ struct Batch {
     long long max_grid_bytes = 16, max_grid_elems = 0;
     bool any_empty = false;
     bool sorted_fwd = true;   // every problem has cell-sorted records for all its terms
-    bool spread_tc = true;    // every problem runs its order-1/2 spread on the tensor cores
+    bool cell_tc = true;      // every problem runs its order-1/2 spread on the tensor cores
     long long max_M = 0;
     double2 *scratch = nullptr;
     // batched LSQR workspace
@@ -96,7 +96,7 @@ static int batch_trafo(Batch &b, cudaStream_t st, const float2 *fhat, float2 *f)
 static int batch_adjoint(Batch &b, cudaStream_t st, const float2 *y, float2 *fhat) {
     return adjoint_launch(nullptr, st, b.views[0], b.args, b.P, y, fhat, b.n_items, b.n_items3, b.counter,
                           b.n_blocks, b.mr, b.max_grid_bytes, b.max_fft, b.sm_count, b.max_grid_elems, b.any_empty,
-                          b.scratch, ANOVA_PREC_F32, b.spread_tc);
+                          b.scratch, ANOVA_PREC_F32, b.cell_tc);
 }
 
 // ----------------------------------------------------- segmented kernels --
@@ -291,7 +291,7 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
         b->max_grid_elems = std::max(b->max_grid_elems, pl.grid_elems);
         b->any_empty = b->any_empty || pl.n_empty > 0;
         b->sorted_fwd = b->sorted_fwd && pl.srec && pl.facc && pl.n_act3 == 0;
-        b->spread_tc = b->spread_tc && pl.srec && pl.spread_tc;
+        b->cell_tc = b->cell_tc && pl.srec && pl.cell_tc;
         b->max_M = std::max(b->max_M, pl.M);
         b->sm_count = pl.sm_count;
     }
@@ -302,7 +302,7 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
     std::vector<int> Ks(n_problems);
     for (int p = 0; p < n_problems; ++p) {
         Plan &pl = b->plans[p]->p;
-        Ks[p] = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count, b->spread_tc);
+        Ks[p] = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count, b->cell_tc);
         b->views[p].spread_chunks = Ks[p];
     }
     // third-order items of every problem first, then the others

@@ -36,6 +36,32 @@ struct GridEl<__nv_bfloat162> {
 
 // ---------------------------------------------------------------- windows --
 
+// ---- TF32 tensor-core products with FP32-level accuracy ----
+//
+// The fragment layouts of mma.m16n8k8 with TF32 operands (PTX ISA), lane =
+// 4 g + t: A (16 x 8) a0 = A[g][t], a1 = A[g + 8][t], a2 = A[g][t + 4],
+// a3 = A[g + 8][t + 4]; B (8 x 8) b0 = B[t][g], b1 = B[t + 4][g]; C, D
+// (16 x 8) d0 = D[g][2t], d1 = D[g][2t + 1], d2 = D[g + 8][2t],
+// d3 = D[g + 8][2t + 1].  A product a b of FP32 values is taken as
+// ah bh + ah bl + al bh with x = xh + xl split below.
+// x = hi + lo for finite x: hi keeps the sign, the exponent and the leading
+// 10 mantissa bits of x rounded half away from zero (adding half a unit of
+// the 10th bit to the bit pattern carries into the exponent where it should),
+// lo = x - hi is exact in FP32; the tensor core reads the leading 10 mantissa
+// bits of lo (error below 2^-21 |x|)
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
+    hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+// d += a b on the tensor core (mma.m16n8k8, TF32 operands, FP32 sums)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // Horner evaluation of a degree-7 polynomial held in registers.
 __device__ __forceinline__ float horner8(const float c[NCOEF], float v) {
     float s = c[NCOEF - 1];

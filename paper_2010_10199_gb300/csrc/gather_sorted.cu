@@ -220,14 +220,18 @@ gather_sorted_f32(DevPlan single, BatchArgs B, const int4 *__restrict__ items, i
             __syncthreads();
             continue;
         }
-        for (long long p = j0 + tid; p < j1; p += 2 * GS_THREADS) {
-            const long long p1 = p + GS_THREADS;
-            const bool ok1 = p1 < j1;
-            const float4 q0 = __ldg(rec + p), q1 = __ldg(rec + (ok1 ? p1 : p));
+        // a thread takes two consecutive records (mostly of one cell: then
+        // every grid value read serves both); the warp iterates as a whole
+        const int lane = tid & 31;
+        for (long long wb = j0 + 2 * (tid - lane); wb < j1; wb += 2 * GS_THREADS) {
+            const long long p = wb + 2 * lane;
+            const bool ok0 = p < j1, ok1 = p + 1 < j1;
+            const float4 q0 = __ldg(rec + (ok0 ? p : j1 - 1)), q1 = __ldg(rec + (ok1 ? p + 1 : j1 - 1));
             float wc0[8], wc1[8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) horner_pair(coef + 2 * t, q0.y, q1.y, wc0[t], wc1[t]);
             const int off0 = __float_as_int(q0.z), off1 = __float_as_int(q1.z);
+            const bool same = __all_sync(0xffffffffu, off0 == off1);
             float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f;
             if (two) {
 #pragma unroll
@@ -236,13 +240,24 @@ gather_sorted_f32(DevPlan single, BatchArgs B, const int4 *__restrict__ items, i
                     horner_pair(coef + 16 + 2 * i, q0.x, q1.x, wr0, wr1);
                     const float2 *r0 = S + off0 + i * stride, *r1 = S + off1 + i * stride;
                     float tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f;
+                    if (same) {
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        const float2 a = r0[t], b = r1[t];
-                        tx0 = fmaf(wc0[t], a.x, tx0);
-                        ty0 = fmaf(wc0[t], a.y, ty0);
-                        tx1 = fmaf(wc1[t], b.x, tx1);
-                        ty1 = fmaf(wc1[t], b.y, ty1);
+                        for (int t = 0; t < 8; ++t) {
+                            const float2 a = r0[t];
+                            tx0 = fmaf(wc0[t], a.x, tx0);
+                            ty0 = fmaf(wc0[t], a.y, ty0);
+                            tx1 = fmaf(wc1[t], a.x, tx1);
+                            ty1 = fmaf(wc1[t], a.y, ty1);
+                        }
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            const float2 a = r0[t], c = r1[t];
+                            tx0 = fmaf(wc0[t], a.x, tx0);
+                            ty0 = fmaf(wc0[t], a.y, ty0);
+                            tx1 = fmaf(wc1[t], c.x, tx1);
+                            ty1 = fmaf(wc1[t], c.y, ty1);
+                        }
                     }
                     sx0 = fmaf(wr0, tx0, sx0);
                     sy0 = fmaf(wr0, ty0, sy0);
@@ -252,16 +267,18 @@ gather_sorted_f32(DevPlan single, BatchArgs B, const int4 *__restrict__ items, i
             } else {
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
-                    const float2 a = S[off0 + t], b = S[off1 + t];
+                    const float2 a = S[off0 + t], c = same ? a : S[off1 + t];
                     sx0 = fmaf(wc0[t], a.x, sx0);
                     sy0 = fmaf(wc0[t], a.y, sy0);
-                    sx1 = fmaf(wc1[t], b.x, sx1);
-                    sy1 = fmaf(wc1[t], b.y, sy1);
+                    sx1 = fmaf(wc1[t], c.x, sx1);
+                    sy1 = fmaf(wc1[t], c.y, sy1);
                 }
             }
-            unsigned long long *a0 = acc + 2 * (long long)__float_as_int(q0.w);
-            red_add_u64(a0, __float2ll_rn(sx0 * sc));
-            red_add_u64(a0 + 1, __float2ll_rn(sy0 * sc));
+            if (ok0) {
+                unsigned long long *a0 = acc + 2 * (long long)__float_as_int(q0.w);
+                red_add_u64(a0, __float2ll_rn(sx0 * sc));
+                red_add_u64(a0 + 1, __float2ll_rn(sy0 * sc));
+            }
             if (ok1) {
                 unsigned long long *a1 = acc + 2 * (long long)__float_as_int(q1.w);
                 red_add_u64(a1, __float2ll_rn(sx1 * sc));

@@ -198,7 +198,7 @@ struct Plan {
     int n_items3;           // the first n_items3 items are those of third-order terms
     int *counter;           // work-queue counter of the spread
     float4 *srec;           // cell-sorted node records (null: none), n_sorted slots of M
-    bool spread_tc;         // order-1/2 spread of sorted records on the tensor cores
+    bool cell_tc;           // order-1/2 spread of sorted records on the tensor cores
     int n_sorted;
     unsigned long long *facc;   // sorted forward: fixed-point accumulators [M][2]
     int *fexp;              // and their exponent

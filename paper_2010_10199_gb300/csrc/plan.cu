@@ -167,7 +167,7 @@ int set_active_terms(Plan &p, const unsigned char *user_mask) {
     p.n_items = 0;
     p.n_items3 = 0;
     if (n == 0) return ANOVA_OK;
-    p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count, p.spread_tc);
+    p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count, p.cell_tc);
     if (p.h_items) {
         p.n_items3 = append_spread_items(p, 0, p.spread_K, p.h_items, 3);
         p.n_items = p.n_items3 + append_spread_items(p, 0, p.spread_K, p.h_items + p.n_items3, 0);
@@ -269,7 +269,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
     if (o.precision < ANOVA_PREC_F32 || o.precision > ANOVA_PREC_F64) return ANOVA_ERR_INVALID;
-    if (o.spread_kernel < 0 || o.spread_kernel > 1) return ANOVA_ERR_INVALID;
+    if (o.cell_kernel < 0 || o.cell_kernel > 1) return ANOVA_ERR_INVALID;
 
     if (o.eps <= 0) o.eps = 1e-5;
     if (o.sigma <= 0) o.sigma = 2.0;
@@ -554,7 +554,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
                     }
                 }
                 p.n_sorted = ns;
-                p.spread_tc = p.precision != ANOVA_PREC_F64 && o.spread_kernel == 0;
+                p.cell_tc = p.precision != ANOVA_PREC_F64 && o.cell_kernel == 0;
                 if (p.precision == ANOVA_PREC_F32) {
                     if (cudaMalloc(&p.facc, sizeof(unsigned long long) * 2 * (size_t)M) != cudaSuccess ||
                         cudaMalloc(&p.fexp, sizeof(int) * 4) != cudaSuccess) {

@@ -31,7 +31,7 @@ class AnovaError(RuntimeError):
 class PlanOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eps", ctypes.c_double), ("window_m_col", ctypes.c_int),
                 ("window_m_row", ctypes.c_int), ("sigma", ctypes.c_double), ("n_ctas", ctypes.c_int),
-                ("node_sort", ctypes.c_int), ("spread_kernel", ctypes.c_int)]
+                ("node_sort", ctypes.c_int), ("cell_kernel", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -327,7 +327,7 @@ class Plan:
     """Owns an anova plan for torch CUDA node tensor ``x`` of shape [d, M]."""
 
     def __init__(self, x, terms, bandwidths, precision: int = PREC_F32, eps: float = 0.0, sigma: float = 0.0,
-                 window_m_row: int = 0, n_ctas: int = 0, node_sort: int = 0, spread_kernel: int = 0,
+                 window_m_row: int = 0, n_ctas: int = 0, node_sort: int = 0, cell_kernel: int = 0,
                  stream=None):
         import torch
         if not (isinstance(x, torch.Tensor) and x.is_cuda):
@@ -340,7 +340,7 @@ class Plan:
         self.bandwidths = [int(b) for b in bandwidths]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opts = PlanOptions(precision=precision, eps=eps, window_m_col=0, window_m_row=window_m_row, sigma=sigma,
-                           n_ctas=n_ctas, node_sort=node_sort, spread_kernel=spread_kernel)
+                           n_ctas=n_ctas, node_sort=node_sort, cell_kernel=cell_kernel)
         self.handle = anova_plan_create(self.d, self.M, x.data_ptr() if self.M else 0, self.terms,
                                         self.bandwidths, opts, self.stream.cuda_stream)
         self.n_coeffs = anova_num_coeffs(self.handle)

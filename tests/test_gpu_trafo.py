@@ -64,7 +64,7 @@ def test_ragged_sizes(gft, M):
     _pair_check(gft, x, terms, bw)
 
 
-SPREAD_PATHS = {"tensor": dict(node_sort=0, spread_kernel=0), "cuda": dict(node_sort=0, spread_kernel=1),
+SPREAD_PATHS = {"tensor": dict(node_sort=0, cell_kernel=0), "cuda": dict(node_sort=0, cell_kernel=1),
                 "unsorted": dict(node_sort=-1)}
 
 
