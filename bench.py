@@ -280,13 +280,13 @@ def run_mine(args, rank, world, local_rank):
     grid_bytes = 8 * (n_terms2 * 69 * 72 + n_terms1 * 136)
     rs = 8 if f64 else 4
     grid_bytes = grid_bytes * esz // 8
-    sfx = "_f64" if f64 else "_f32"
     if gms / max(gl, 1) >= sms / max(sl, 1):
         kname, kms, klaunch = ("gather_f64" if f64 else "gather_sorted_f32"), gms / max(gl, 1), gl
         # nodes read (one real per coordinate), f written, grids and coefficients read once
         alg_bytes = rs * d * M + esz * M + grid_bytes + esz * n
     else:
-        kname, kms, klaunch = "spread" + sfx, sms / max(sl, 1), sl
+        # FP32 plans run the order-1/2 spread on the tensor cores (cell-sorted records)
+        kname, kms, klaunch = ("spread_f64" if f64 else "spread_mma_f32"), sms / max(sl, 1), sl
         # nodes and y read, one grid written
         alg_bytes = rs * d * M + esz * M + grid_bytes
     achieved = alg_bytes / (kms / 1e3) / 1e9
@@ -297,18 +297,30 @@ def run_mine(args, rank, world, local_rank):
         src = [os.path.join(ROOT, "paper_2010_10199_gb300", "csrc", s) for s in tj.get("sources", [])]
         if tj.get("kernel") == kname and all(os.path.exists(s) for s in src) and source_hash(src) == tj.get("hash"):
             traffic = tj.get("dram_bytes_per_launch")
-    # on-chip (shared-memory) roofline: window taps x 8 bytes read (gather) or updated (spread)
-    taps = n_terms2 * 6 * 8 + n_terms1 * 8
-    smem_bytes = taps * 8 * M
+    # Arithmetic roofline: both kernels are bound by instruction issue, far from
+    # HBM (the HBM figures are kept beside it).  Algorithmic work per node and
+    # term, as FMA-equivalent operations of the direct evaluation: the window
+    # polynomials (8 column and 2 m_row row taps, degree 7: 7 FMA each by
+    # Horner) and the tensor product of the window with y or the grid (2 m_row
+    # x 8 taps: the weight product and a complex multiply-add, 3 operations).
+    m_row = 3
+    ops2 = (8 + 2 * m_row) * 7 + 2 * m_row * 8 * 3
+    ops1 = 8 * 7 + 8 * 2
+    alg_flops = 2.0 * M * (n_terms2 * ops2 + n_terms1 * ops1)
     clk_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    smem_peak = 152 * 128 * clk_mhz * 1e6 / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "traffic_gbs": None if traffic is None else traffic / (kms / 1e3) / 1e9, "kernel": kname,
-            "kernel_ms": kms, "alg_bytes_per_launch": alg_bytes, "peak_source": peak_kind,
-            "onchip": {"bound": "smem", "achieved": smem_bytes / (kms / 1e3) / 1e9, "peak": smem_peak,
-                       "unit": "GB/s", "frac": smem_bytes / (kms / 1e3) / 1e9 / smem_peak,
-                       "peak_basis": "152 SMs x 128 B/clk x median SM clock in the timed region"}}
+    if f64:
+        alu_peak, alu_basis = 1.25, "nominal FP64 rate of the GB300 (1.25 TFLOP/s)"
+    else:
+        alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+        alu_basis = "FP32 FMA: 152 SMs x 128 lanes x 2 flops x median SM clock in the timed region"
+    achieved_flops = alg_flops / (kms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved_flops, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": achieved_flops / alu_peak, "traffic": traffic, "kernel": kname, "kernel_ms": kms,
+            "alg_flops_per_launch": alg_flops, "peak_basis": alu_basis,
+            "hbm": {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "alg_bytes_per_launch": alg_bytes,
+                    "traffic_gbs": None if traffic is None else traffic / (kms / 1e3) / 1e9,
+                    "peak_source": peak_kind}}
 
     launches = 0
     # the FP32 forward stage launches the fixed-point passes around the sorted gather
