@@ -541,13 +541,13 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
 // nodes masked; the 16 x 8 accumulator goes to the shared grid by
 // shared-memory additions whenever the cell changes.
 
-// Records rec[0, n) of one term for one warp, in steps of 16 (two groups of
+// Records rec[0, n) of one term for one warp, in steps of 32 (four groups of
 // 8 for the tensor core).  The warp's own ring in shared memory (MMA_RING
-// steps of records and of values y) is filled by lanes 0..15 with cp.async:
+// steps of records and of values y) is filled by its lanes with cp.async:
 // the records MMA_DR steps ahead, the values y[index] MMA_DY steps ahead
 // (their addresses come from the records already in the ring).  Order 1:
 // B = e_0 (the single grid row), exact in TF32.
-constexpr int MMA_STEP = 16, MMA_RING = 4, MMA_DR = 3, MMA_DY = 1;
+constexpr int MMA_STEP = 32, MMA_RING = 4, MMA_DR = 3, MMA_DY = 1;
 constexpr size_t MMA_REC_BYTES = (size_t)MMA_RING * MMA_STEP * 16;             // float4 records
 constexpr size_t MMA_RING_BYTES = MMA_REC_BYTES + (size_t)MMA_RING * MMA_STEP * 8;  // + float2 values, per warp
 static_assert(MMA_DY < MMA_DR && MMA_DR < MMA_RING && (MMA_RING & (MMA_RING - 1)) == 0, "ring depths");
@@ -592,14 +592,14 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         if (ORD2) mma_tf32(e, ah, bl0, bl1);
         mma_tf32(e, ah, bh0, bh1);
     };
-    // A fresh tensor-core sum per step (at most two groups), added to d in
+    // A fresh tensor-core sum per step (at most four groups), added to d in
     // FP32 with rounding to nearest: the tensor core's own accumulation is
     // not rounded to nearest, and its bias would grow with the cell's node
     // count.
     for (int i = -MMA_DR; i < ns; ++i) {
         // iteration i commits one cp.async group: the records of step
         // i + MMA_DR and the values of step i + MMA_DY; steps i < 0 fill the ring
-        if (lane < MMA_STEP) {
+        {
             const int qr = i + MMA_DR, qy = i + MMA_DY;
             if (qr < ns)
                 cp_async16(&rring[(qr & (MMA_RING - 1)) * MMA_STEP + lane], rec + min(MMA_STEP * qr + lane, n - 1));
@@ -615,8 +615,9 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         cp_async_wait_n<MMA_DY>();   // values of step i (and its records) have landed
         __syncwarp();
         float e[4] = {0.f, 0.f, 0.f, 0.f};
+        const bool whole = MMA_STEP * (i + 1) <= n;   // no group of this step runs past the end
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < MMA_STEP / 8; ++h) {
             const int base = MMA_STEP * i + 8 * h;   // first node of this group (may be past the end)
             const int sl = (i & (MMA_RING - 1)) * MMA_STEP + 8 * h;
             const float4 r0 = rring[sl + t], r1 = rring[sl + t + 4];
@@ -631,7 +632,7 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
                 bl0 = bl1 = 0u;
             }
             const int off0 = __float_as_int(r0.z), off1 = __float_as_int(r1.z);
-            if (__all_sync(0xffffffffu, base + 8 <= n && off0 == cur && off1 == cur)) {
+            if (__all_sync(0xffffffffu, (whole || base + 8 <= n) && off0 == cur && off1 == cur)) {
                 // the whole group lies in the cell being summed
                 group_mma(e, y0.x * wc0, y0.y * wc0, y1.x * wc1, y1.y * wc1, bh0, bl0, bh1, bl1);
             } else {
