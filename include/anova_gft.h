@@ -83,10 +83,11 @@ typedef struct {
     int node_sort;      /* adjoint: 0 = keep a copy of the nodes sorted by grid cell for every
                            term of order <= 2 when it fits in half the free device memory
                            (16 bytes per node and term); -1 = never */
-    int cell_kernel;    /* adjoint of terms of order <= 2 with sorted nodes (FP32, FP16 and
-                           BF16 plans): 0 = per-cell window sums on the tensor cores
-                           (operands split into two TF32 parts, three products, FP32 sums),
-                           1 = on the CUDA cores (FP32) */
+    int cell_kernel;    /* terms of order <= 2 with sorted nodes: 0 = the per-cell products on
+                           the tensor cores (operands split into two TF32 parts, three
+                           products, FP32 sums): the adjoint spread of FP32, FP16 and BF16
+                           plans, and the forward gather of FP32 plans without third-order
+                           terms; 1 = on the CUDA cores (FP32) */
 } anova_plan_options;
 
 /*

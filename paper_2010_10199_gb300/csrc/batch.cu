@@ -87,8 +87,9 @@ static int batch_trafo(Batch &b, cudaStream_t st, const float2 *fhat, float2 *f)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
     if (b.sorted_fwd)
-        return gather_sorted_launch(st, b.views[0], b.args, b.P, fhat, f, b.args.items, 0, b.n_items, b.counter,
-                                    b.max_grid_bytes, b.max_M, b.sm_count, b.mr, (double *)b.scratch);
+        return gather_sorted_launch(st, b.views[0], b.args, b.P, fhat, f, b.args.items, b.n_items3, b.n_items,
+                                    b.counter, b.max_grid_bytes, b.max_M, b.sm_count, b.mr, (double *)b.scratch,
+                                    b.cell_tc);
     return gather_launch(st, b.views[0], b.args, fhat, f, b.n_tiles, b.mr, b.pitch, b.max_grid_bytes, b.dmax,
                          b.sm_count, ANOVA_PREC_F32);
 }

@@ -289,31 +289,236 @@ gather_sorted_f32(DevPlan single, BatchArgs B, const int4 *__restrict__ items, i
     }
 }
 
+// ---- Forward gather of order-1/2 terms on the tensor cores ----
+//
+// For the nodes j of one cell, H[j][r] = sum_k psi_col,k(j) G[r][k] (G the
+// m_row x 8 grid window of the cell, complex) is the product of the 16 x 8
+// matrix of column weights of 16 nodes with the 8 x 8 window (real and
+// imaginary parts one mma.m16n8k8 each, TF32 operands split into two parts);
+// f_j = sum_r psi_row,r(j) H[j][r] then takes two FMAs per lane and a
+// butterfly over the 4 lanes that hold node j's rows.  Lane (g, t) evaluates
+// column taps t, t + 4 and row taps 2t, 2t + 1 of nodes g and g + 8 of a tile
+// of 16 cell-sorted nodes, from coefficients held in registers (a table in
+// shared memory read at 4 taps at once would saturate its data path).  A
+// warp takes two tiles per step.  A tile holding nodes of several cells is
+// run once per cell with the other nodes' rows of A zeroed.  The sums go to
+// the 64-bit fixed-point accumulators as in gather_sorted_f32, one (node,
+// real or imaginary part) per lane.  Grid values are read from shared memory
+// only when the cell changes, so the data path carries the records and the
+// accumulator additions.
+constexpr int GM_TILE = 16;
+
+__device__ __forceinline__ void mma3_tf32(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
+                                          unsigned bh0, unsigned bh1, unsigned bl0, unsigned bl1) {
+    mma_tf32(d, al, bh0, bh1);
+    mma_tf32(d, ah, bl0, bl1);
+    mma_tf32(d, ah, bh0, bh1);
+}
+
+template <int MR>
+__device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, int n, const float2 *S, int stride,
+                                               bool ord2, const float4 *coef, unsigned long long *__restrict__ acc,
+                                               float sc) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float ca[NCOEF], cb[NCOEF], ra[NCOEF], rb[NCOEF];   // column taps t, t + 4; row taps 2t, 2t + 1
+    auto fetch = [&](const float4 *c, float (&dst)[NCOEF]) {
+        const float4 lo = c[0], hi = c[1];
+        dst[0] = lo.x, dst[1] = lo.y, dst[2] = lo.z, dst[3] = lo.w;
+        dst[4] = hi.x, dst[5] = hi.y, dst[6] = hi.z, dst[7] = hi.w;
+    };
+    fetch(coef + 2 * t, ca);
+    fetch(coef + 2 * (t + 4), cb);
+    fetch(coef + 16 + 2 * (2 * t), ra);
+    fetch(coef + 16 + 2 * (2 * t + 1), rb);
+    const int nstep = (n + 2 * GM_TILE - 1) / (2 * GM_TILE);
+    // record u of step i; past the end the last record is read again (not written back)
+    auto ld = [&](int i, int u) { return __ldg(rec + min(2 * GM_TILE * i + u, n - 1)); };
+    float4 q[4] = {ld(0, g), ld(0, g + 8), ld(0, g + 16), ld(0, g + 24)};
+    int cur = -1;            // cell whose window is in bh, bl
+    unsigned bh[4], bl[4];   // B fragments: real part (b0, b1), imaginary part (b0, b1)
+    const bool row_ok = ord2 ? g < 2 * MR : g == 0;   // grid row g of the window exists
+    auto load_b = [&](int off) {
+        float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+        if (row_ok) {
+            v0 = S[off + g * stride + t];
+            v1 = S[off + g * stride + t + 4];
+        }
+        split_tf32(v0.x, bh[0], bl[0]);
+        split_tf32(v1.x, bh[1], bl[1]);
+        split_tf32(v0.y, bh[2], bl[2]);
+        split_tf32(v1.y, bh[3], bl[3]);
+    };
+    // tile h of the step: rows of A from records q[2h] (node g) and q[2h + 1] (node g + 8)
+    auto tile_slow = [&](const unsigned (&ah)[4], const unsigned (&al)[4], int off0, int off1, float (&dre)[4],
+                         float (&dim)[4]) {
+        bool p0 = true, p1 = true;   // nodes g, g + 8 not yet covered
+        for (;;) {
+            // lanes t = 0 speak for their nodes
+            const unsigned m0 = __ballot_sync(0xffffffffu, p0) & 0x11111111u;
+            const unsigned m1 = __ballot_sync(0xffffffffu, p1) & 0x11111111u;
+            if (!(m0 | m1)) break;
+            const int src = __ffs(m0 ? m0 : m1) - 1;
+            const int oc = __shfl_sync(0xffffffffu, m0 ? off0 : off1, src);
+            const bool e0 = p0 && off0 == oc, e1 = p1 && off1 == oc;
+            if (oc != cur) {
+                load_b(oc);
+                cur = oc;
+            }
+            const unsigned mh[4] = {e0 ? ah[0] : 0u, e1 ? ah[1] : 0u, e0 ? ah[2] : 0u, e1 ? ah[3] : 0u};
+            const unsigned ml[4] = {e0 ? al[0] : 0u, e1 ? al[1] : 0u, e0 ? al[2] : 0u, e1 ? al[3] : 0u};
+            mma3_tf32(dre, mh, ml, bh[0], bh[1], bl[0], bl[1]);
+            mma3_tf32(dim, mh, ml, bh[2], bh[3], bl[2], bl[3]);
+            p0 = p0 && !e0;
+            p1 = p1 && !e1;
+        }
+    };
+    for (int i = 0; i < nstep; ++i) {
+        const float4 nq[4] = {ld(i + 1, g), ld(i + 1, g + 8), ld(i + 1, g + 16), ld(i + 1, g + 24)};
+        // A of both tiles: column weights, taps t (a0: node g, a1: node g + 8) and t + 4 (a2, a3)
+        unsigned ah[2][4], al[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            split_tf32(horner8(ca, q[2 * h].y), ah[h][0], al[h][0]);
+            split_tf32(horner8(ca, q[2 * h + 1].y), ah[h][1], al[h][1]);
+            split_tf32(horner8(cb, q[2 * h].y), ah[h][2], al[h][2]);
+            split_tf32(horner8(cb, q[2 * h + 1].y), ah[h][3], al[h][3]);
+        }
+        float dre[2][4] = {}, dim[2][4] = {};
+        const int o[4] = {__float_as_int(q[0].z), __float_as_int(q[1].z), __float_as_int(q[2].z),
+                          __float_as_int(q[3].z)};
+        if (__all_sync(0xffffffffu, o[0] == cur && o[1] == cur && o[2] == cur && o[3] == cur)) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                mma3_tf32(dre[h], ah[h], al[h], bh[0], bh[1], bl[0], bl[1]);
+                mma3_tf32(dim[h], ah[h], al[h], bh[2], bh[3], bl[2], bl[3]);
+            }
+        } else {
+            tile_slow(ah[0], al[0], o[0], o[1], dre[0], dim[0]);
+            tile_slow(ah[1], al[1], o[2], o[3], dre[1], dim[1]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 &q0 = q[2 * h], &q1 = q[2 * h + 1];
+            // row weights: taps 2t (r0: node g, r1: node g + 8) and 2t + 1 (r2, r3)
+            float r[4];
+            if (ord2) {
+                r[0] = horner8(ra, q0.x);
+                r[1] = horner8(ra, q1.x);
+                r[2] = horner8(rb, q0.x);
+                r[3] = horner8(rb, q1.x);
+            } else {
+                r[0] = r[1] = t == 0 ? 1.f : 0.f;
+                r[2] = r[3] = 0.f;
+            }
+            // d0, d1: node g, rows 2t, 2t + 1; d2, d3: node g + 8
+            float fx0 = fmaf(r[2], dre[h][1], r[0] * dre[h][0]), fy0 = fmaf(r[2], dim[h][1], r[0] * dim[h][0]);
+            float fx1 = fmaf(r[3], dre[h][3], r[1] * dre[h][2]), fy1 = fmaf(r[3], dim[h][3], r[1] * dim[h][2]);
+#pragma unroll
+            for (int m = 1; m <= 2; m <<= 1) {
+                fx0 += __shfl_xor_sync(0xffffffffu, fx0, m);
+                fy0 += __shfl_xor_sync(0xffffffffu, fy0, m);
+                fx1 += __shfl_xor_sync(0xffffffffu, fx1, m);
+                fy1 += __shfl_xor_sync(0xffffffffu, fy1, m);
+            }
+            // lane t writes (node g: re, im; node g + 8: re, im)[t]
+            const float v = t == 0 ? fx0 : t == 1 ? fy0 : t == 2 ? fx1 : fy1;
+            const int node = 2 * GM_TILE * i + GM_TILE * h + (t < 2 ? g : g + 8);
+            const int j = __float_as_int(t < 2 ? q0.w : q1.w);
+            if (node < n) red_add_u64(acc + 2 * (long long)j + (t & 1), __float2ll_rn(v * sc));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = nq[k];
+    }
+}
+
+template <int MR>
+__global__ void __launch_bounds__(GS_THREADS, 2)
+gather_mma_f32(DevPlan single, BatchArgs B, const int4 *__restrict__ items, int item_begin, int item_end,
+               int *counter, long long max_grid_bytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *S = (float2 *)smem;
+    float4 *coef = (float4 *)(smem + max_grid_bytes);   // [8 column taps + 8 row taps][2]
+    int &s_item = *(int *)(coef + 32);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (;;) {
+        if (tid == 0) s_item = item_begin + atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= item_end) break;
+        const int4 itm = items[item];
+        const DevPlan &P = plan_of(single, B, itm.x);
+        if (P.skip && *P.skip) continue;
+        const long long M = P.M;
+        const float sc = __int_as_float((127 + *P.fexp) << 23);   // 2^e, exact scaling
+        const Term &T = P.terms[P.act[itm.y]];
+        const long long j0 = M * itm.z / itm.w, j1 = M * (itm.z + 1) / itm.w;
+        {
+            const float4 *gsrc = (const float4 *)(P.grids + T.grid_off);
+            float4 *S4 = (float4 *)S;
+            const long long n4 = T.grid_bytes / 16;
+            for (long long e = tid; e < n4; e += GS_THREADS) S4[e] = __ldg(gsrc + e);
+            if (tid < 32) {
+                const int tap = tid >> 1, h = tid & 1;
+                const float *src = tap < 8 ? P.windows[T.wc].c[tap] : P.windows[T.wr].c[min(tap - 8, 2 * MR - 1)];
+                coef[tid] = make_float4(__ldg(src + 4 * h), __ldg(src + 4 * h + 1), __ldg(src + 4 * h + 2),
+                                        __ldg(src + 4 * h + 3));
+            }
+        }
+        __syncthreads();
+        // warp w takes a contiguous run of the item's records (whole steps of two tiles)
+        constexpr int NW = GS_THREADS / 32;
+        const long long len = j1 - j0, per = (len + 2 * GM_TILE * NW - 1) / (2 * GM_TILE * NW) * (2 * GM_TILE);
+        const long long a = j0 + warp * per, b = min(j1, a + per);
+        if (a < b)
+            gather_mma_run<MR>(P.srec + (long long)T.sort_slot * M + a, (int)(b - a), S, T.stride, T.order == 2,
+                               coef, P.facc, sc);
+        __syncthreads();   // the grid is read by every warp before the next item replaces it
+    }
+}
+
 int gather_sorted_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *fhat,
-                         float2 *f, const int4 *items, int item_begin, int item_end, int *counter,
-                         long long max_grid_bytes, long long max_M, int sm_count, int mr, double *part) {
+                         float2 *f, const int4 *items, int n_items3, int item_end, int *counter,
+                         long long max_grid_bytes, long long max_M, int sm_count, int mr, double *part, bool tc) {
+    const int item_begin = 0;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(gather_sorted_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(gather_sorted_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(gather_mma_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(gather_mma_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         attr = true;
     }
+    // Order-1/2 items on the tensor cores only where no third-order item (the
+    // first n_items3, always on the CUDA cores) precedes them: two launches in
+    // a row idle the GPU at the seam, which costs more than the tensor cores
+    // gain (10 % on the d = 10, |u| <= 3 workload).
+    const int cuda_end = tc && n_items3 == 0 ? 0 : item_end;
     const int nb = (int)std::max<long long>(1, std::min<long long>(4LL * sm_count / std::max(1, P) + 1,
                                                                    (max_M + 255) / 256));
     k_fixed_point_partial<<<dim3(FPE_BLOCKS, P), 256, 0, st>>>(v, B, fhat, part);
     k_fixed_point_exponent<<<P, 32, 0, st>>>(v, B, part);
     k_sorted_forward_init<<<dim3(nb, P), 256, 0, st>>>(v, B, fhat, f);
-    if (item_end > item_begin) {
-        const size_t smem = (size_t)max_grid_bytes + 32 * sizeof(float4) + 16;
-        const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(3, (size_t)(MAX_SMEM + 1024) / (smem + 1024)));
-        const int ctas = std::max(1, std::min(item_end - item_begin, per_sm * sm_count));
-        cudaMemsetAsync(counter, 0, sizeof(int), st);
+    const size_t smem = (size_t)max_grid_bytes + 32 * sizeof(float4) + 16;
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(3, (size_t)(MAX_SMEM + 1024) / (smem + 1024)));
+    if (item_end > item_begin) cudaMemsetAsync(counter, 0, 2 * sizeof(int), st);
+    if (cuda_end > item_begin) {
+        const int ctas = std::max(1, std::min(cuda_end - item_begin, per_sm * sm_count));
         if (mr <= 3)
-            gather_sorted_f32<3><<<ctas, GS_THREADS, smem, st>>>(v, B, items, item_begin, item_end, counter,
+            gather_sorted_f32<3><<<ctas, GS_THREADS, smem, st>>>(v, B, items, item_begin, cuda_end, counter,
                                                                  max_grid_bytes);
         else
-            gather_sorted_f32<4><<<ctas, GS_THREADS, smem, st>>>(v, B, items, item_begin, item_end, counter,
+            gather_sorted_f32<4><<<ctas, GS_THREADS, smem, st>>>(v, B, items, item_begin, cuda_end, counter,
                                                                  max_grid_bytes);
+    }
+    if (item_end > cuda_end) {
+        const int ctas = std::max(1, std::min(item_end - cuda_end, std::min(per_sm, 2) * sm_count));
+        if (mr <= 3)
+            gather_mma_f32<3><<<ctas, GS_THREADS, smem, st>>>(v, B, items, cuda_end, item_end, counter + 1,
+                                                              max_grid_bytes);
+        else
+            gather_mma_f32<4><<<ctas, GS_THREADS, smem, st>>>(v, B, items, cuda_end, item_end, counter + 1,
+                                                              max_grid_bytes);
     }
     k_fixed_point_finish<<<dim3(nb, P), 256, 0, st>>>(v, B, f);
     return cuda_status(cudaGetLastError());
@@ -328,8 +533,8 @@ int launch_gather_sorted_f32(Plan &p, const float2 *fhat, float2 *f) {
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s)
         if (p.h_terms[s].mr > 0) mr = p.h_terms[s].mr;
-    return gather_sorted_launch(p.stream, v, B, 1, fhat, f, p.items, 0, p.n_items, p.counter, p.max_grid_bytes, p.M,
-                                p.sm_count, mr, (double *)p.scratch);
+    return gather_sorted_launch(p.stream, v, B, 1, fhat, f, p.items, p.n_items3, p.n_items, p.counter,
+                                p.max_grid_bytes, p.M, p.sm_count, mr, (double *)p.scratch, p.cell_tc);
 }
 
 }  // namespace agft

@@ -243,9 +243,12 @@ int launch_gather_f32(Plan &p, const float2 *fhat, float2 *f);
 int launch_gather_sorted_f32(Plan &p, const float2 *fhat, float2 *f);
 // The same for one problem (B.plans == null) or a batch of P problems, every one
 // with records and accumulators: f = empty-set coefficient + all terms.
+// Sorted forward of one problem or a batch: fixed-point passes around the
+// gather of items [0, item_end); the first n_items3 are third-order items;
+// with tc and none of those, the gather runs on the tensor cores.
 int gather_sorted_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *fhat,
-                         float2 *f, const int4 *items, int item_begin, int item_end, int *counter,
-                         long long max_grid_bytes, long long max_M, int sm_count, int mr, double *part);
+                         float2 *f, const int4 *items, int n_items3, int item_end, int *counter,
+                         long long max_grid_bytes, long long max_M, int sm_count, int mr, double *part, bool tc);
 int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
                    float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks, int mr,
