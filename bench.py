@@ -281,7 +281,8 @@ def run_mine(args, rank, world, local_rank):
     rs = 8 if f64 else 4
     grid_bytes = grid_bytes * esz // 8
     if gms / max(gl, 1) >= sms / max(sl, 1):
-        kname, kms, klaunch = ("gather_f64" if f64 else "gather_sorted_f32"), gms / max(gl, 1), gl
+        # FP32 plans without third-order terms run the gather on the tensor cores
+        kname, kms, klaunch = ("gather_f64" if f64 else "gather_mma_f32"), gms / max(gl, 1), gl
         # nodes read (one real per coordinate), f written, grids and coefficients read once
         alg_bytes = rs * d * M + esz * M + grid_bytes + esz * n
     else:
