@@ -324,7 +324,8 @@ int anova_profile_read(anova_plan_t plan, double *ms, int64_t *launches, const c
  * time is the mean of `reps` timed pairs after one warm-up pair on `stream`.
  * Candidates: sigma in {1.75, 2, 2.5} x row half-width in {3, 4}; then, around
  * the fastest one within eps_target, node chunks per term (n_ctas) in
- * {4, 16, 64} and the original node order (node_sort = -1).
+ * {4, 16, 64}, the original node order (node_sort = -1) and the CUDA-core
+ * cell kernels (cell_kernel = 1).
  *   opts       : in: base options (precision must be ANOVA_PREC_F32);
  *                out: the fastest candidate with est_error <= eps_target
  *   d .. bandwidth : as for anova_plan_create
@@ -340,6 +341,7 @@ typedef struct {
     int window_m_row;
     int n_ctas;
     int node_sort;
+    int cell_kernel;
     double ms_pair;    /* mean time of one forward + adjoint pair */
     double est_error;  /* estimated relative l2 error against the reference plan */
     int chosen;        /* 1 for the candidate written to opts */

@@ -1,6 +1,7 @@
 // Plan autotuner: picks the oversampling factor, the row window half-width,
-// the number of node chunks per term of the adjoint and the node order of the
-// spread for one node set and term list, by timing transform pairs of
+// the number of node chunks per term of the adjoint, the node order of the
+// spread and the cell kernels (tensor or CUDA cores) for one node set and term
+// list, by timing transform pairs of
 // candidate plans on the device and estimating each candidate's error against
 // a wider-window, more oversampled reference plan (the NFFT error falls with
 // both, Sec. 3 after eq. (somafm)).  The fastest candidate whose estimated
@@ -186,6 +187,7 @@ int anova_plan_autotune(anova_plan_options *opts, int d, int64_t M, const void *
             o.window_m_row = mr;
             o.n_ctas = 0;
             o.node_sort = 0;
+            o.cell_kernel = 0;
             rc = trial(o);
             if (rc) break;
         }
@@ -204,6 +206,11 @@ int anova_plan_autotune(anova_plan_options *opts, int d, int64_t M, const void *
             o.node_sort = -1;
             rc = trial(o);
         }
+        if (!rc) {
+            anova_plan_options o = base;
+            o.cell_kernel = 1;
+            rc = trial(o);
+        }
         b = best();
     }
     cudaEventDestroy(e0);
@@ -215,6 +222,7 @@ int anova_plan_autotune(anova_plan_options *opts, int d, int64_t M, const void *
             t.window_m_row = done[i].o.window_m_row;
             t.n_ctas = done[i].o.n_ctas;
             t.node_sort = done[i].o.node_sort;
+            t.cell_kernel = done[i].o.cell_kernel;
             t.ms_pair = done[i].ms;
             t.est_error = done[i].err;
             t.chosen = i == b;

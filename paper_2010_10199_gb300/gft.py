@@ -58,8 +58,8 @@ N_SCREEN_FEATURES = 7
 
 class TuneTrial(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("window_m_row", ctypes.c_int), ("n_ctas", ctypes.c_int),
-                ("node_sort", ctypes.c_int), ("ms_pair", ctypes.c_double), ("est_error", ctypes.c_double),
-                ("chosen", ctypes.c_int)]
+                ("node_sort", ctypes.c_int), ("cell_kernel", ctypes.c_int), ("ms_pair", ctypes.c_double),
+                ("est_error", ctypes.c_double), ("chosen", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -204,7 +204,7 @@ def autotune(x, terms, bandwidths, eps: float = 1e-5, reps: int = 3, stream=None
             td[3 * i + j] = u[j] if j < len(u) else -1
         bw[i] = int(bandwidths[i]) if len(u) else 0
     opts = PlanOptions(precision=PREC_F32, eps=0.0, window_m_col=0, window_m_row=0, sigma=0.0, n_ctas=0,
-                       node_sort=0)
+                       node_sort=0, cell_kernel=0)
     trials = (TuneTrial * 32)()
     nt = ctypes.c_int(0)
     st = stream if stream is not None else torch.cuda.current_stream()
@@ -212,7 +212,7 @@ def autotune(x, terms, bandwidths, eps: float = 1e-5, reps: int = 3, stream=None
                                     int(reps), trials, 32, ctypes.byref(nt), ctypes.c_void_p(st.cuda_stream or None))
     _check("anova_plan_autotune", rc)
     chosen = {"sigma": opts.sigma, "window_m_row": opts.window_m_row, "n_ctas": opts.n_ctas,
-              "node_sort": opts.node_sort}
+              "node_sort": opts.node_sort, "cell_kernel": opts.cell_kernel}
     return chosen, [trials[i].as_dict() for i in range(nt.value)]
 
 

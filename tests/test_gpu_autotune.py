@@ -35,8 +35,9 @@ def test_autotune_choice_meets_target(gft):
     assert len(pick) == 1
     assert pick[0]["ms_pair"] == min(t["ms_pair"] for t in ok)
     assert chosen["sigma"] == pick[0]["sigma"] and chosen["window_m_row"] == pick[0]["window_m_row"]
+    assert len(trials) >= 8 and any(t["cell_kernel"] == 1 for t in trials)
     P = gft.Plan(xd, terms, bw, sigma=chosen["sigma"], window_m_row=chosen["window_m_row"],
-                 n_ctas=chosen["n_ctas"], node_sort=chosen["node_sort"])
+                 n_ctas=chosen["n_ctas"], node_sort=chosen["node_sort"], cell_kernel=chosen["cell_kernel"])
     fhat = inputs.decaying_coefficients(2, terms, bw)
     y = inputs.complex_normal(2, 4, x.shape[1])
     xo = f32_nodes(x)
