@@ -26,7 +26,7 @@ __device__ __forceinline__ void red_add(float *addr, float v) {
 
 __device__ __forceinline__ int freq_index_a(int q, int N) { return q < N / 2 ? q - N / 2 : q - N / 2 + 1; }
 
-enum { SK_STAGED = 0, SK_ORDER3 = 1, SK_MMA = 2 };
+enum { SK_STAGED = 0, SK_ORDER3 = 1, SK_MMA = 2, SK_MMA3 = 3 };
 constexpr int SPREAD_MMA_CTAS_PER_SM = 3;   // 80 registers
 
 constexpr int SP_CH = 512;   // nodes staged per block of a work item (order 1/2: SP_CH or SP_CH / 2)
@@ -699,6 +699,178 @@ __device__ __forceinline__ void spread_mma_item(const DevPlan &P, const Term &T,
         spread_mma_run<MR, false>(rec, y, (int)(b - a), S, T.stride, ccf, rcf, rring, yring);
 }
 
+// ---- Third-order cell sums on the tensor cores ----
+//
+// For the nodes j of one cell of a term (a, b, c) the window sums are
+//     G[ia][ib][k] += sum_j psi_a,ia(j) psi_b,ib(j) y_j psi_c,k(j).
+// For each row tap ia this is one product A B_ia: A[(k, re/im)][j] =
+// y_j psi_c,k(j) as in the order-2 kernel (shared by all ia) and
+// B_ia[j][ib] = psi_a,ia(j) psi_b,ib(j), 2 m_row mma.m16n8k8 (three TF32
+// products each) per group of 8 nodes.  Column n of B_ia holds second-row tap
+// ib = n / 2 (n even) or n / 2 + 4 (n odd), so the two taps a lane's D
+// fragment covers, t and t + 4, are 4 grid rows apart, which spreads its
+// shared-memory additions over more banks.  Lane (g, t) evaluates column tap
+// g, second-row tap ib(g) and first-row tap g of nodes t, t + 4; shuffles hand
+// each lane the first coordinate's taps of its nodes.  The sums stay in the D
+// fragments (4 per ia) and go to the shared grid (indices modulo n) when the
+// cell changes and after 8 steps of 16 nodes in one cell, which keeps the
+// tensor core's own accumulation chains short.
+constexpr int MMA3_STEP = 16, MMA3_RING = 4, MMA3_DR = 3, MMA3_DY = 1;
+constexpr size_t MMA3_REC_BYTES = (size_t)MMA3_RING * MMA3_STEP * 32;              // two float4 per node
+constexpr size_t MMA3_RING_BYTES = MMA3_REC_BYTES + (size_t)MMA3_RING * MMA3_STEP * 8;  // + float2 values
+static_assert(MMA3_DY < MMA3_DR && MMA3_DR < MMA3_RING && (MMA3_RING & (MMA3_RING - 1)) == 0, "ring depths");
+
+static size_t spread3_mma_smem_bytes(long long max_grid_bytes) {
+    return (size_t)max_grid_bytes + MMA3_RING_BYTES * (SPREAD_THREADS / 32) + 16;
+}
+
+template <int MR>
+__device__ __forceinline__ void spread3_mma_run(const float4 *__restrict__ rec, const float2 *__restrict__ y, int n,
+                                                float2 *S, const Term &T, const float ccf[NCOEF],
+                                                const float rcf[NCOEF], const float bcf[NCOEF], float4 *rring,
+                                                float2 *yring) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int ib_g = (g >> 1) + 4 * (g & 1);   // second-row tap of B column g
+    const int nn = T.n, stride = T.stride, mc = T.mc;
+    const int ns = (n + MMA3_STEP - 1) / MMA3_STEP;
+    int cur = -1, cfa = 0, cfb = 0, cfc = 0;   // the cell being summed: number and grid indices
+    float d[2 * MR][4];
+#pragma unroll
+    for (int a = 0; a < 2 * MR; ++a) d[a][0] = d[a][1] = d[a][2] = d[a][3] = 0.f;
+    // d[ia] = (re ib t, re ib t + 4, im ib t, im ib t + 4) of column tap g
+    int chain = 0;   // steps summed into d since the last flush
+    auto flush = [&]() {
+        const int col = wrap(cfc - mc + 1 + g, nn);
+        const int rb0 = wrap(cfb - MR + 1 + t, nn), rb1 = wrap(cfb - MR + 1 + t + 4, nn);
+#pragma unroll
+        for (int a = 0; a < 2 * MR; ++a) {
+            const int ra = wrap(cfa - MR + 1 + a, nn) * nn;
+            float *c0 = (float *)(S + (ra + rb0) * stride + col);
+            red_add(c0, d[a][0]);
+            red_add(c0 + 1, d[a][2]);
+            if (t + 4 < 2 * MR) {
+                float *c1 = (float *)(S + (ra + rb1) * stride + col);
+                red_add(c1, d[a][1]);
+                red_add(c1 + 1, d[a][3]);
+            }
+            d[a][0] = d[a][1] = d[a][2] = d[a][3] = 0.f;
+        }
+        chain = 0;
+    };
+    for (int i = -MMA3_DR; i < ns; ++i) {
+        // iteration i commits one cp.async group: the records of step i + MMA3_DR
+        // and the values of step i + MMA3_DY; lanes 0..15 copy one node each
+        if (lane < MMA3_STEP) {
+            const int qr = i + MMA3_DR, qy = i + MMA3_DY;
+            if (qr < ns) {
+                const float4 *src = rec + 2 * min(MMA3_STEP * qr + lane, n - 1);
+                float4 *dst = &rring[((qr & (MMA3_RING - 1)) * MMA3_STEP + lane) * 2];
+                cp_async16(dst, src);
+                cp_async16(dst + 1, src + 1);
+            }
+            if (qy >= 0 && qy < ns) {
+                cp_async_wait_n<MMA3_DR - MMA3_DY - 1>();
+                const int j = __float_as_int(rring[((qy & (MMA3_RING - 1)) * MMA3_STEP + lane) * 2].w);
+                cp_async8(&yring[(qy & (MMA3_RING - 1)) * MMA3_STEP + lane], y + j);
+            }
+        }
+        cp_async_commit();
+        if (i < 0) continue;
+        cp_async_wait_n<MMA3_DY>();
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < MMA3_STEP / 8; ++h) {
+            const int base = MMA3_STEP * i + 8 * h;   // first node of this group (may be past the end)
+            const int sl = (i & (MMA3_RING - 1)) * MMA3_STEP + 8 * h;
+            const float4 q0 = rring[2 * (sl + t)], c0 = rring[2 * (sl + t) + 1];
+            const float4 q1 = rring[2 * (sl + t + 4)], c1 = rring[2 * (sl + t + 4) + 1];
+            const float2 y0 = yring[sl + t], y1 = yring[sl + t + 4];
+            const float wc0 = horner8(ccf, q0.z), wc1 = horner8(ccf, q1.z);
+            // second row coordinate: tap g of nodes t, t + 4 (the B column);
+            // first row coordinate: tap g here, handed round below
+            const bool gok = ib_g < 2 * MR;
+            const float wb0 = gok ? horner8(bcf, q0.y) : 0.f, wb1 = gok ? horner8(bcf, q1.y) : 0.f;
+            const float wa0 = horner8(rcf, q0.x), wa1 = horner8(rcf, q1.x);
+            const int key0 = __float_as_int(c0.w), key1 = __float_as_int(c1.w);
+            bool p0 = base + t < n, p1 = base + t + 4 < n;   // nodes t, t + 4 not yet added
+            const bool fast = __all_sync(0xffffffffu, p0 && p1 && key0 == cur && key1 == cur);
+            for (;;) {
+                bool e0 = p0, e1 = p1;
+                if (!fast) {
+                    const unsigned pm =
+                        (__ballot_sync(0xffffffffu, p0) & 0xfu) | ((__ballot_sync(0xffffffffu, p1) & 0xfu) << 4);
+                    if (!pm) break;
+                    const int f = __ffs(pm) - 1;   // first node not yet added; its cell is next
+                    const int src = f & 3;
+                    const bool second = f >= 4;
+                    const int oc = __shfl_sync(0xffffffffu, second ? key1 : key0, src);
+                    e0 = p0 && key0 == oc;
+                    e1 = p1 && key1 == oc;
+                    if (oc != cur) {
+                        if (cur >= 0) flush();
+                        cur = oc;
+                        cfa = __shfl_sync(0xffffffffu, __float_as_int(second ? c1.x : c0.x), src);
+                        cfb = __shfl_sync(0xffffffffu, __float_as_int(second ? c1.y : c0.y), src);
+                        cfc = __shfl_sync(0xffffffffu, __float_as_int(second ? c1.z : c0.z), src);
+                    }
+                }
+                unsigned ah[4], al[4];
+                split_tf32(e0 ? y0.x * wc0 : 0.f, ah[0], al[0]);
+                split_tf32(e0 ? y0.y * wc0 : 0.f, ah[1], al[1]);
+                split_tf32(e1 ? y1.x * wc1 : 0.f, ah[2], al[2]);
+                split_tf32(e1 ? y1.y * wc1 : 0.f, ah[3], al[3]);
+#pragma unroll
+                for (int a = 0; a < 2 * MR; ++a) {
+                    // first coordinate's tap a of nodes t, t + 4 from lane (a, t)
+                    const float va0 = __shfl_sync(0xffffffffu, wa0, 4 * a + t);
+                    const float va1 = __shfl_sync(0xffffffffu, wa1, 4 * a + t);
+                    unsigned bh0, bl0, bh1, bl1;
+                    split_tf32(va0 * wb0, bh0, bl0);
+                    split_tf32(va1 * wb1, bh1, bl1);
+                    mma_tf32(d[a], al, bh0, bh1);
+                    mma_tf32(d[a], ah, bl0, bl1);
+                    mma_tf32(d[a], ah, bh0, bh1);
+                }
+                if (fast) break;
+                p0 = p0 && !e0;
+                p1 = p1 && !e1;
+            }
+        }
+        // at most 8 steps per tensor-core chain
+        if (cur >= 0 && ++chain == 8) flush();
+        __syncwarp();   // ring slot i is read before a later iteration refills it
+    }
+    cp_async_wait0();
+    if (cur >= 0) flush();
+}
+
+template <int MR>
+__device__ __forceinline__ void spread3_mma_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
+                                                 long long j0, long long j1, float2 *S, unsigned char *stg_raw) {
+    const int warp = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
+    // column tap g, first-row tap g, second-row tap of B column g
+    float ccf[NCOEF], rcf[NCOEF], bcf[NCOEF];
+    {
+        const int ib = (g >> 1) + 4 * (g & 1);
+        const float *cs = P.windows[T.wc].c[g];
+        const float *rs = P.windows[T.wr].c[min(g, 2 * MR - 1)];
+        const float *bs = P.windows[T.wr].c[min(ib, 2 * MR - 1)];
+#pragma unroll
+        for (int q = 0; q < NCOEF; ++q) {
+            ccf[q] = __ldg(cs + q);
+            rcf[q] = __ldg(rs + q);
+            bcf[q] = __ldg(bs + q);
+        }
+    }
+    constexpr int NW = SPREAD_THREADS / 32;
+    const long long len = j1 - j0, per = (len + 8 * NW - 1) / (8 * NW) * 8;
+    const long long a = j0 + warp * per, b = min(j1, a + per);
+    if (a >= b) return;
+    unsigned char *ring = stg_raw + warp * MMA3_RING_BYTES;
+    spread3_mma_run<MR>(P.srec + (long long)T.sort_slot * P.M + 2 * a, y, (int)(b - a), S, T, ccf, rcf, bcf,
+                        (float4 *)ring, (float2 *)(ring + MMA3_REC_BYTES));
+}
+
 // One work item (x = problem, y = active term, z = node chunk, w = chunks per
 // term) spreads nodes [M z / w, M (z+1) / w) of one term (in the term's cell
 // order if the plan keeps sorted copies and the term has order <= 2, else in
@@ -715,8 +887,10 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
     float2 *S = (float2 *)smem_raw;
     unsigned char *stg_raw = smem_raw + max_grid_bytes;
     constexpr bool O3 = KIND == SK_ORDER3;
-    int &s_item = *(int *)(stg_raw + (KIND == SK_MMA ? MMA_RING_BYTES * (SPREAD_THREADS / 32)
-                                                     : O3 ? SP3_STAGE_BYTES : sp_stage_bytes(SP)));
+    int &s_item = *(int *)(stg_raw + (KIND == SK_MMA    ? MMA_RING_BYTES * (SPREAD_THREADS / 32)
+                                      : KIND == SK_MMA3 ? MMA3_RING_BYTES * (SPREAD_THREADS / 32)
+                                      : O3              ? SP3_STAGE_BYTES
+                                                        : sp_stage_bytes(SP)));
     const int tid = threadIdx.x;
     const int k = tid & 7;
     for (;;) {
@@ -738,7 +912,7 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
         // window coefficients of this lane: row tap k for lanes r = 1 of an
         // order-2 term (see node_weights), column tap k otherwise
         float wcf[NCOEF];
-        if constexpr (KIND != SK_MMA) {
+        if constexpr (KIND != SK_MMA && KIND != SK_MMA3) {
             const bool row = T.order == 2 && (tid & 8);
             const float *wsrc = row ? P.windows[T.wr].c[min(k, 2 * MR - 1)] : P.windows[T.wc].c[k];
 #pragma unroll
@@ -747,6 +921,8 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
         __syncthreads();   // grid zeroed before any addition
         if constexpr (KIND == SK_MMA) {
             spread_mma_item<MR>(P, T, y, j0, j1, S, stg_raw);
+        } else if constexpr (KIND == SK_MMA3) {
+            spread3_mma_item<MR>(P, T, y, j0, j1, S, stg_raw);
         } else if constexpr (O3) {
             if (T.sort_slot >= 0 && P.srec)
                 spread_sorted_item3<MR>(P, T, y, j0, j1, S, stg_raw, wcf);
@@ -785,6 +961,14 @@ __global__ void __launch_bounds__(SPREAD_THREADS, SPREAD_MMA_CTAS_PER_SM)
 spread_mma_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
                int *counter, long long max_grid_bytes) {
     spread_items<MR, G, SK_MMA, 0>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
+}
+
+// third-order items of plans with cell-sorted records, on the tensor cores
+template <int MR, typename G>
+__global__ void __launch_bounds__(SPREAD_THREADS, 2)
+spread3_mma_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
+                int *counter, long long max_grid_bytes) {
+    spread_items<MR, G, SK_MMA3, 0>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
 }
 
 template <int MR, typename G>
@@ -1017,6 +1201,8 @@ static void adjoint_attrs() {
         cudaFuncSetAttribute(spread_f32<3, G, SP_CH / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread_f32<4, G, SP_CH / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread3_mma_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread3_mma_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread_mma_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread_mma_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
@@ -1037,7 +1223,13 @@ static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const
     const int per_sm = spread_ctas_per_sm(sgrid, false);
     if (prof) stage_begin(*prof, ST_SPREAD);
     cudaMemsetAsync(counter, 0, 2 * sizeof(int), st);
-    if (n_items3 > 0) {
+    if (n_items3 > 0 && tc) {
+        const size_t sm3 = spread3_mma_smem_bytes(sgrid);
+        const int per3 = (int)std::max<size_t>(1, std::min<size_t>(2, (size_t)(MAX_SMEM + 1024) / (sm3 + 1024)));
+        const int c3 = std::max(1, std::min(n_items3, per3 * sm_count));
+        auto k = mr <= 3 ? spread3_mma_f32<3, G> : spread3_mma_f32<4, G>;
+        k<<<c3, SPREAD_THREADS, sm3, st>>>(v, B, y, 0, n_items3, counter, sgrid);
+    } else if (n_items3 > 0) {
         const int c3 = std::max(1, std::min(n_items3, std::min(per_sm, 2) * sm_count));
         if (mr <= 3)
             spread3_f32<3, G><<<c3, SPREAD_THREADS, ssm3, st>>>(v, B, y, 0, n_items3, counter, sgrid);

@@ -94,7 +94,8 @@ __global__ void k_cell_scan(const Term *terms, int *counts, int max_bins) {
 // scatter: every node goes to the next free place of its cell, as a record.
 // Order <= 2: (2 tau_row - 1, 2 tau_col - 1, first-tap grid offset, original
 // index).  Order 3, two records: (2 tau_row0 - 1, 2 tau_row1 - 1, 2 tau_col - 1,
-// original index) and the cell's grid indices (i_row0, i_row1, i_col, 0).
+// original index) and the cell's grid indices and cell number (i_row0, i_row1,
+// i_col, (i_row0 n + i_row1) n + i_col).
 __global__ void k_cell_scatter(const Term *terms, const float *x, long long M, int *cursor, int max_bins,
                                float4 *srec) {
     const Term &T = terms[blockIdx.y];
@@ -114,7 +115,8 @@ __global__ void k_cell_scatter(const Term *terms, const float *x, long long M, i
         if (T.order == 3) {
             const int pos = atomicAdd(&cur[(fr * T.n + fr1) * T.n + fc], 1);
             dst[2 * pos] = make_float4(2.f * tr - 1.f, 2.f * tr1 - 1.f, 2.f * tc - 1.f, __int_as_float((int)j));
-            dst[2 * pos + 1] = make_float4(__int_as_float(fr), __int_as_float(fr1), __int_as_float(fc), 0.f);
+            dst[2 * pos + 1] = make_float4(__int_as_float(fr), __int_as_float(fr1), __int_as_float(fc),
+                                           __int_as_float((fr * T.n + fr1) * T.n + fc));
         } else {
             const int pos = atomicAdd(&cur[fr * (T.order == 2 ? T.n : 0) + fc], 1);
             const int off = fr * T.stride + fc;

@@ -120,16 +120,29 @@ def test_c2_subsample_all_terms(gft):
     _pair_check(gft, w["x"], w["terms"], w["bandwidths"], fhat=w["fhat"], y=w["y"])
 
 
-@pytest.mark.parametrize("node_sort", [0, -1])
-def test_third_order_terms(gft, node_sort):
+@pytest.mark.parametrize("path", list(SPREAD_PATHS))
+def test_third_order_terms(gft, path):
     """Third-order terms through the cell-sorted kernels (two records per
-    node, indices modulo n) and through the point-major gather and the
-    original-order spread."""
+    node, indices modulo n; window sums on the tensor cores or the CUDA
+    cores) and through the point-major gather and the original-order
+    spread."""
     d = 4
     x = inputs.beta22_points(3, d, 3000)
     terms = anova.term_set(d, 3)
     bw = [0] + [20] * 4 + [12] * 6 + [10] * 4
-    _pair_check(gft, x, terms, bw, node_sort=node_sort)
+    _pair_check(gft, x, terms, bw, **SPREAD_PATHS[path])
+
+
+@pytest.mark.parametrize("path", ["tensor", "cuda"])
+def test_third_order_dense_cells_and_wide_window(gft, path):
+    """A third-order term with hundreds of nodes per cell (long cell runs over
+    several steps), a ragged node count, and the 8 x 8 x 8-tap window
+    (eps below 5e-6: m_row = 4)."""
+    x = inputs.uniform_points(21, 3, 100003)
+    terms = [(), (0,), (1,), (2,), (0, 1, 2)]
+    bw = [0, 8, 8, 8, 4]
+    _pair_check(gft, x, terms, bw, **SPREAD_PATHS[path])
+    _pair_check(gft, x, terms, bw, eps=1e-6, tol=3e-6, **SPREAD_PATHS[path])
 
 
 def test_mixed_bandwidths_and_orders(gft):
