@@ -351,6 +351,8 @@ def run_mine(args, rank, world, local_rank):
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+                # algorithmic (node, non-empty term) pairs of both transforms per second, all ranks
+                "point_terms_per_s": value * 2 * args.M * (n_terms2 + n_terms1),
                 "wall_s": wall}
         print(json.dumps(line), flush=True)
     P.close()
