@@ -3,9 +3,13 @@
 //
 //   1. spread: work items (term, node chunk) from a global queue.  An item
 //      accumulates y_j times the window into a shared-memory copy of the
-//      term's stored grid (halos included) with shared-memory atomics,
-//      half-warp per node (2 rows x 8 columns of the window per instruction),
-//      then writes it to partial grid z of the term (z = chunk index).
+//      term's stored grid (halos included), then writes it to partial grid z
+//      of the term (z = chunk index).  With cell-sorted node records the sums
+//      of one grid cell's nodes are formed first -- on the tensor cores
+//      (spread_mma_f32, spread3_mma_f32) or in registers on the CUDA cores
+//      (spread_f32 sorted items, spread3_f32) -- and added to the shared grid
+//      once per cell; without records every node's window is added with
+//      shared-memory atomics.
 //   2. reduce_partials: grid = sum_z partials[z] in a fixed order.
 //   3. adjoint_post: per term, fold the halos back onto the periodic grid, FFT
 //      with sign -, multiply by the deconvolution factors and crop the block

@@ -1,15 +1,17 @@
 // Forward gather over the cell-sorted node records (every term with records:
-// all terms of an FP32 plan that keeps them) (the window interpolation step of the NFFT behind eq. (somafm),
-// Sec. 3), FP32.
+// all terms of an FP32 plan that keeps them), the window interpolation step
+// of the NFFT behind eq. (somafm), Sec. 3, FP32.
 //
 // Work items are the adjoint's (active term, node chunk) pairs.  A CTA copies
-// the term's stored grid into shared memory and gives each thread one node at
-// a time (two in flight): the thread evaluates the node's 8 column and 2 m_row
-// row window weights from the per-tap polynomials (coefficients broadcast from
-// shared memory, 16 bytes at a time), reads the 6 x 8 grid values around the
-// node's cell (the nodes of a warp mostly share a cell, so the reads are
-// broadcasts) and adds sum_i w_row[i] sum_t w_col[t] g[i][t] into node j's
-// accumulator.  The accumulators are 64-bit integers holding the values in
+// the term's stored grid into shared memory.  gather_sorted_f32 gives each
+// thread two consecutive records: the thread evaluates each node's 8 column
+// and 2 m_row row window weights from the per-tap polynomials (coefficients
+// broadcast from shared memory, 16 bytes at a time), reads the 6 x 8 grid
+// values around the cell (the nodes of a warp mostly share a cell, so the
+// reads are broadcasts, and one read serves both nodes when the pair shares a
+// cell) and adds sum_i w_row[i] sum_t w_col[t] g[i][t] into node j's
+// accumulator.  gather_mma_f32 (below) forms the same sums on the tensor
+// cores.  The accumulators are 64-bit integers holding the values in
 // fixed point, v * 2^e with 2^e chosen from ||fhat||_1 (a bound on every
 // partial sum), so the additions are exact and their order, which the
 // hardware does not fix, cannot change the result: the forward is bitwise
