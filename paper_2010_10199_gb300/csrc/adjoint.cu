@@ -620,6 +620,11 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         __syncwarp();
         float e[4] = {0.f, 0.f, 0.f, 0.f};
         const bool whole = MMA_STEP * (i + 1) <= n;   // no group of this step runs past the end
+        // the records are in cell order: if the step's first and last nodes lie in
+        // the cell being summed, all of them do (the same test in every lane)
+        const int sl0 = (i & (MMA_RING - 1)) * MMA_STEP;
+        const bool step_in_cell = whole && __float_as_int(rring[sl0].z) == cur &&
+                                  __float_as_int(rring[sl0 + MMA_STEP - 1].z) == cur;
 #pragma unroll
         for (int h = 0; h < MMA_STEP / 8; ++h) {
             const int base = MMA_STEP * i + 8 * h;   // first node of this group (may be past the end)
@@ -636,7 +641,7 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
                 bl0 = bl1 = 0u;
             }
             const int off0 = __float_as_int(r0.z), off1 = __float_as_int(r1.z);
-            if (__all_sync(0xffffffffu, (whole || base + 8 <= n) && off0 == cur && off1 == cur)) {
+            if (step_in_cell || __all_sync(0xffffffffu, (whole || base + 8 <= n) && off0 == cur && off1 == cur)) {
                 // the whole group lies in the cell being summed
                 group_mma(e, y0.x * wc0, y0.y * wc0, y1.x * wc1, y1.y * wc1, bh0, bl0, bh1, bl1);
             } else {
