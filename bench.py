@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--cell-kernel", type=int, default=0, choices=[0, 1],
+                    help="pairs mode: 0 = per-cell products on the tensor cores, 1 = on the CUDA cores")
     ap.add_argument("--mode", default="pairs", choices=["pairs", "lambda-path", "batch", "lsqr-path"])
     ap.add_argument("--lambdas", type=int, default=20, help="lambda-path mode: first K values of the path")
     ap.add_argument("--max-it", type=int, default=5000, help="lambda-path mode: FISTA iterations per lambda")
@@ -200,7 +202,8 @@ def run_mine(args, rank, world, local_rank):
     tcdt = torch.complex128 if f64 else torch.complex64
     esz = 16 if f64 else 8
     xd = torch.from_numpy(w["x"].astype(rdt)).to(dev)
-    P = gft.Plan(xd, w["terms"], w["bandwidths"], precision=gft.PREC_F64 if f64 else gft.PREC_F32)
+    P = gft.Plan(xd, w["terms"], w["bandwidths"], precision=gft.PREC_F64 if f64 else gft.PREC_F32,
+                 cell_kernel=args.cell_kernel)
     n = P.n_coeffs
     fhat_h = torch.from_numpy(w["fhat"].astype(cdt)).pin_memory()
     y_h = torch.from_numpy(w["y"].astype(cdt)).pin_memory()
@@ -282,12 +285,14 @@ def run_mine(args, rank, world, local_rank):
     grid_bytes = grid_bytes * esz // 8
     if gms / max(gl, 1) >= sms / max(sl, 1):
         # FP32 plans without third-order terms run the gather on the tensor cores
-        kname, kms, klaunch = ("gather_f64" if f64 else "gather_mma_f32"), gms / max(gl, 1), gl
+        kname, kms, klaunch = ("gather_f64" if f64 else "gather_sorted_f32" if args.cell_kernel else "gather_mma_f32"), \
+            gms / max(gl, 1), gl
         # nodes read (one real per coordinate), f written, grids and coefficients read once
         alg_bytes = rs * d * M + esz * M + grid_bytes + esz * n
     else:
         # FP32 plans run the order-1/2 spread on the tensor cores (cell-sorted records)
-        kname, kms, klaunch = ("spread_f64" if f64 else "spread_mma_f32"), sms / max(sl, 1), sl
+        kname, kms, klaunch = ("spread_f64" if f64 else "spread_f32" if args.cell_kernel else "spread_mma_f32"), \
+            sms / max(sl, 1), sl
         # nodes and y read, one grid written
         alg_bytes = rs * d * M + esz * M + grid_bytes
     achieved = alg_bytes / (kms / 1e3) / 1e9
@@ -347,6 +352,7 @@ def run_mine(args, rank, world, local_rank):
                 "config": {"workload": WORKLOAD, "M": args.M,
                            "precision": "fp64 throughout" if f64 else "fp32 grids and accumulation",
                            "window": "Kaiser-Bessel, sigma=2, 6 row x 8 column taps",
+                           "cell_products": "CUDA cores" if args.cell_kernel else "tensor cores (TF32 split, 3 products)",
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
