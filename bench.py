@@ -185,6 +185,18 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def replica_throughput(seconds: float, units: int, world: int, device) -> tuple[float, float]:
+    """Whole-job throughput of `world` independent replicas that each processed
+    `units` units in `seconds`: the job lasts as long as its slowest rank (MAX
+    over ranks), and the units of all ranks count.  Returns (units/s, seconds)."""
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    slowest = float(t.item())
+    return units * world / slowest, slowest
+
+
 def run_mine(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -242,12 +254,7 @@ def run_mine(args, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     prof = P.profile_read(reset=True)
     P.profile(False)
-    total_s = sum(step_ms) / 1e3
-    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_max = float(t.item())
-    value = args.steps * world / total_max
+    value, total_max = replica_throughput(sum(step_ms) / 1e3, args.steps, world, dev)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -267,11 +274,8 @@ def run_mine(args, rank, world, local_rank):
             if k > 0:
                 ee[k - 1][1].record(stream)
         torch.cuda.synchronize()
-        e_s = sum(a.elapsed_time(b) for a, b in ee) / 1e3
-        te = torch.tensor([e_s], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": args.steps * world / float(te.item()), "unit": UNIT,
+        e_value, _ = replica_throughput(sum(a.elapsed_time(b) for a, b in ee) / 1e3, args.steps, world, dev)
+        e2e = {"value": e_value, "unit": UNIT,
                "h2d_bytes_per_step": esz * (n + args.M), "d2h_bytes_per_step": esz * (n + args.M)}
 
     # roofline of the dominant kernel (algorithmic bytes per launch / live event time)
