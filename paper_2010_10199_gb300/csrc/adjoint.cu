@@ -88,12 +88,12 @@ int spread_block_nodes(long long max_grid_bytes) {
     return smem_bound && ctas_for(max_grid_bytes, SP_CH / 2) > ctas_for(max_grid_bytes, SP_CH) ? SP_CH / 2 : SP_CH;
 }
 
-// the tensor-core kernel: grid, one ring per warp, item slot
-static size_t spread_mma_smem_bytes(long long max_grid_bytes);
+// the tensor-core kernel with STEP-node steps: grid, one ring per warp, item slot
+static size_t spread_mma_smem_bytes(long long max_grid_bytes, int step);
 
 int spread_ctas_per_sm(long long max_grid_bytes, bool tc) {
     if (tc) {
-        const size_t per = spread_mma_smem_bytes(max_grid_bytes) + 1024;
+        const size_t per = spread_mma_smem_bytes(max_grid_bytes, 32) + 1024;
         return (int)std::max<size_t>(1, std::min<size_t>(SPREAD_MMA_CTAS_PER_SM, (size_t)(MAX_SMEM + 1024) / per));
     }
     return ctas_for(max_grid_bytes, spread_block_nodes(max_grid_bytes));
@@ -545,25 +545,37 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
 // nodes masked; the 16 x 8 accumulator goes to the shared grid by
 // shared-memory additions whenever the cell changes.
 
-// Records rec[0, n) of one term for one warp, in steps of 32 (four groups of
-// 8 for the tensor core).  The warp's own ring in shared memory (MMA_RING
-// steps of records and of values y) is filled by its lanes with cp.async:
-// the records MMA_DR steps ahead, the values y[index] MMA_DY steps ahead
-// (their addresses come from the records already in the ring).  Order 1:
-// B = e_0 (the single grid row), exact in TF32.
-constexpr int MMA_STEP = 32, MMA_RING = 4, MMA_DR = 3, MMA_DY = 1;
-constexpr size_t MMA_REC_BYTES = (size_t)MMA_RING * MMA_STEP * 16;             // float4 records
-constexpr size_t MMA_RING_BYTES = MMA_REC_BYTES + (size_t)MMA_RING * MMA_STEP * 8;  // + float2 values, per warp
-static_assert(MMA_DY < MMA_DR && MMA_DR < MMA_RING && (MMA_RING & (MMA_RING - 1)) == 0, "ring depths");
+// Records rec[0, n) of one term for one warp, in steps of STEP nodes (STEP / 8
+// groups of 8 for the tensor core): 32 where cells hold a few hundred nodes,
+// 64 where they hold thousands (half the step overheads; the one-test-per-step
+// fast path below needs the whole step in one cell).  The warp's own rings in
+// shared memory (RING steps of records, YRING steps of values y) are filled by
+// its lanes with cp.async: the records DR steps ahead, the values y[index] DY
+// steps ahead (their addresses come from the records already in the ring).
+// Order 1: B = e_0 (the single grid row), exact in TF32.
+template <int STEP>
+struct MmaRing {
+    static constexpr int RING = STEP == 32 ? 4 : 3, YRING = STEP == 32 ? 4 : 2, DR = STEP == 32 ? 3 : 2, DY = 1;
+    static constexpr size_t REC_BYTES = (size_t)RING * STEP * 16;           // float4 records
+    static constexpr size_t BYTES = REC_BYTES + (size_t)YRING * STEP * 8;   // + float2 values, per warp
+    static_assert(DY < DR && DR < RING && DY < YRING && STEP % 32 == 0, "ring depths");
+};
 
-static size_t spread_mma_smem_bytes(long long max_grid_bytes) {
-    return (size_t)max_grid_bytes + MMA_RING_BYTES * (SPREAD_THREADS / 32) + 16;
+__host__ __device__ constexpr size_t mma_ring_bytes(int step) {
+    return step == 64 ? MmaRing<64>::BYTES : MmaRing<32>::BYTES;
 }
 
-template <int MR, bool ORD2>
+static size_t spread_mma_smem_bytes(long long max_grid_bytes, int step) {
+    return (size_t)max_grid_bytes + mma_ring_bytes(step) * (SPREAD_THREADS / 32) + 16;
+}
+
+template <int MR, bool ORD2, int MMA_STEP>
 __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, const float2 *__restrict__ y, int n,
                                                float2 *S, int stride, const float ccf[NCOEF], const float rcf[NCOEF],
                                                float4 *rring, float2 *yring) {
+    using R = MmaRing<MMA_STEP>;
+    constexpr unsigned MMA_RING = R::RING, MMA_YRING = R::YRING;
+    constexpr int MMA_DR = R::DR, MMA_DY = R::DY;
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int ns = (n + MMA_STEP - 1) / MMA_STEP;
     int cur = -1;   // grid offset of the cell being summed
@@ -596,7 +608,7 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         if (ORD2) mma_tf32(e, ah, bl0, bl1);
         mma_tf32(e, ah, bh0, bh1);
     };
-    // A fresh tensor-core sum per step (at most four groups), added to d in
+    // A fresh tensor-core sum per step (at most eight groups), added to d in
     // FP32 with rounding to nearest: the tensor core's own accumulation is
     // not rounded to nearest, and its bias would grow with the cell's node
     // count.
@@ -606,12 +618,17 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         {
             const int qr = i + MMA_DR, qy = i + MMA_DY;
             if (qr < ns)
-                cp_async16(&rring[(qr & (MMA_RING - 1)) * MMA_STEP + lane], rec + min(MMA_STEP * qr + lane, n - 1));
+#pragma unroll
+                for (int u = lane; u < MMA_STEP; u += 32)
+                    cp_async16(&rring[((unsigned)qr % MMA_RING) * MMA_STEP + u], rec + min(MMA_STEP * qr + u, n - 1));
             if (qy >= 0 && qy < ns) {
                 // the records of step qy were committed MMA_DR - MMA_DY iterations ago
                 cp_async_wait_n<MMA_DR - MMA_DY - 1>();
-                const int j = __float_as_int(rring[(qy & (MMA_RING - 1)) * MMA_STEP + lane].w);
-                cp_async8(&yring[(qy & (MMA_RING - 1)) * MMA_STEP + lane], y + j);
+#pragma unroll
+                for (int u = lane; u < MMA_STEP; u += 32) {
+                    const int j = __float_as_int(rring[((unsigned)qy % MMA_RING) * MMA_STEP + u].w);
+                    cp_async8(&yring[((unsigned)qy % MMA_YRING) * MMA_STEP + u], y + j);
+                }
             }
         }
         cp_async_commit();
@@ -622,15 +639,15 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         const bool whole = MMA_STEP * (i + 1) <= n;   // no group of this step runs past the end
         // the records are in cell order: if the step's first and last nodes lie in
         // the cell being summed, all of them do (the same test in every lane)
-        const int sl0 = (i & (MMA_RING - 1)) * MMA_STEP;
+        const int sl0 = ((unsigned)i % MMA_RING) * MMA_STEP, yl0 = ((unsigned)i % MMA_YRING) * MMA_STEP;
         const bool step_in_cell = whole && __float_as_int(rring[sl0].z) == cur &&
                                   __float_as_int(rring[sl0 + MMA_STEP - 1].z) == cur;
 #pragma unroll
         for (int h = 0; h < MMA_STEP / 8; ++h) {
             const int base = MMA_STEP * i + 8 * h;   // first node of this group (may be past the end)
-            const int sl = (i & (MMA_RING - 1)) * MMA_STEP + 8 * h;
+            const int sl = sl0 + 8 * h, yl = yl0 + 8 * h;
             const float4 r0 = rring[sl + t], r1 = rring[sl + t + 4];
-            const float2 y0 = yring[sl + t], y1 = yring[sl + t + 4];
+            const float2 y0 = yring[yl + t], y1 = yring[yl + t + 4];
             const float wc0 = horner8(ccf, r0.y), wc1 = horner8(ccf, r1.y);
             unsigned bh0, bl0, bh1, bl1;
             if (ORD2) {
@@ -680,7 +697,7 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
 
 // Sorted item of order 1/2 on the tensor cores: the item's records are cut
 // into 8 contiguous runs (multiples of 8 nodes), one per warp.
-template <int MR>
+template <int MR, int STEP>
 __device__ __forceinline__ void spread_mma_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                 long long j0, long long j1, float2 *S, unsigned char *stg_raw) {
     const int warp = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
@@ -699,13 +716,13 @@ __device__ __forceinline__ void spread_mma_item(const DevPlan &P, const Term &T,
     const long long a = j0 + warp * per, b = min(j1, a + per);
     if (a >= b) return;
     const float4 *rec = P.srec + (long long)T.sort_slot * P.M + a;
-    unsigned char *ring = stg_raw + warp * MMA_RING_BYTES;
+    unsigned char *ring = stg_raw + warp * MmaRing<STEP>::BYTES;
     float4 *rring = (float4 *)ring;
-    float2 *yring = (float2 *)(ring + MMA_REC_BYTES);
+    float2 *yring = (float2 *)(ring + MmaRing<STEP>::REC_BYTES);
     if (T.order == 2)
-        spread_mma_run<MR, true>(rec, y, (int)(b - a), S, T.stride, ccf, rcf, rring, yring);
+        spread_mma_run<MR, true, STEP>(rec, y, (int)(b - a), S, T.stride, ccf, rcf, rring, yring);
     else
-        spread_mma_run<MR, false>(rec, y, (int)(b - a), S, T.stride, ccf, rcf, rring, yring);
+        spread_mma_run<MR, false, STEP>(rec, y, (int)(b - a), S, T.stride, ccf, rcf, rring, yring);
 }
 
 // ---- Third-order cell sums on the tensor cores ----
@@ -896,7 +913,7 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
     float2 *S = (float2 *)smem_raw;
     unsigned char *stg_raw = smem_raw + max_grid_bytes;
     constexpr bool O3 = KIND == SK_ORDER3;
-    int &s_item = *(int *)(stg_raw + (KIND == SK_MMA    ? MMA_RING_BYTES * (SPREAD_THREADS / 32)
+    int &s_item = *(int *)(stg_raw + (KIND == SK_MMA    ? mma_ring_bytes(SP) * (SPREAD_THREADS / 32)
                                       : KIND == SK_MMA3 ? MMA3_RING_BYTES * (SPREAD_THREADS / 32)
                                       : O3              ? SP3_STAGE_BYTES
                                                         : sp_stage_bytes(SP)));
@@ -929,7 +946,7 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
         }
         __syncthreads();   // grid zeroed before any addition
         if constexpr (KIND == SK_MMA) {
-            spread_mma_item<MR>(P, T, y, j0, j1, S, stg_raw);
+            spread_mma_item<MR, SP>(P, T, y, j0, j1, S, stg_raw);
         } else if constexpr (KIND == SK_MMA3) {
             spread3_mma_item<MR>(P, T, y, j0, j1, S, stg_raw);
         } else if constexpr (O3) {
@@ -964,12 +981,13 @@ spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int i
     spread_items<MR, G, SK_STAGED, SP>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
 }
 
-// order-1/2 items of plans with cell-sorted records, on the tensor cores
-template <int MR, typename G>
+// order-1/2 items of plans with cell-sorted records, on the tensor cores, in
+// steps of STEP nodes
+template <int MR, typename G, int STEP>
 __global__ void __launch_bounds__(SPREAD_THREADS, SPREAD_MMA_CTAS_PER_SM)
 spread_mma_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
                int *counter, long long max_grid_bytes) {
-    spread_items<MR, G, SK_MMA, 0>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
+    spread_items<MR, G, SK_MMA, STEP>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
 }
 
 // third-order items of plans with cell-sorted records, on the tensor cores
@@ -1212,8 +1230,10 @@ static void adjoint_attrs() {
         cudaFuncSetAttribute(spread3_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_mma_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_mma_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        cudaFuncSetAttribute(spread_mma_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        cudaFuncSetAttribute(spread_mma_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_mma_f32<3, G, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_mma_f32<4, G, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_mma_f32<3, G, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_mma_f32<4, G, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         attr_done = true;
     }
@@ -1225,7 +1245,7 @@ template <typename G>
 static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P,
                             const float2 *y, float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks,
                             int mr, long long sgrid, int max_fft_elems, int sm_count, long long max_grid_elems,
-                            bool tc) {
+                            bool tc, int mma_step) {
     adjoint_attrs<G>();
     const int sp = spread_block_nodes(sgrid);
     const size_t ssm = spread_smem_bytes(sgrid, false, sp), ssm3 = spread_smem_bytes(sgrid, true, sp);
@@ -1246,9 +1266,13 @@ static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const
             spread3_f32<4, G><<<c3, SPREAD_THREADS, ssm3, st>>>(v, B, y, 0, n_items3, counter, sgrid);
     }
     if (n_items > n_items3 && tc) {
-        const int c = std::max(1, std::min(n_items - n_items3, spread_ctas_per_sm(sgrid, true) * sm_count));
-        auto k = mr <= 3 ? spread_mma_f32<3, G> : spread_mma_f32<4, G>;
-        k<<<c, SPREAD_THREADS, spread_mma_smem_bytes(sgrid), st>>>(v, B, y, n_items3, n_items, counter + 1, sgrid);
+        const size_t sm = spread_mma_smem_bytes(sgrid, mma_step);
+        const int per = (int)std::max<size_t>(
+            1, std::min<size_t>(SPREAD_MMA_CTAS_PER_SM, (size_t)(MAX_SMEM + 1024) / (sm + 1024)));
+        const int c = std::max(1, std::min(n_items - n_items3, per * sm_count));
+        auto k = mr <= 3 ? (mma_step == 64 ? spread_mma_f32<3, G, 64> : spread_mma_f32<3, G, 32>)
+                         : (mma_step == 64 ? spread_mma_f32<4, G, 64> : spread_mma_f32<4, G, 32>);
+        k<<<c, SPREAD_THREADS, sm, st>>>(v, B, y, n_items3, n_items, counter + 1, sgrid);
     } else if (n_items > n_items3) {
         const int c = std::max(1, std::min(n_items - n_items3, per_sm * sm_count));
         auto k = mr <= 3 ? (sp == SP_CH ? spread_f32<3, G, SP_CH> : spread_f32<3, G, SP_CH / 2>)
@@ -1271,7 +1295,7 @@ static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
                    float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks, int mr,
                    long long max_grid_bytes, int max_fft_elems, int sm_count, long long max_grid_elems,
-                   bool any_empty, double2 *scratch, int prec, bool tc) {
+                   bool any_empty, double2 *scratch, int prec, bool tc, int mma_step) {
     if (any_empty) {
         const int nb = 256;
         if (prof) stage_begin(*prof, ST_SUMY);
@@ -1282,13 +1306,13 @@ int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArg
     if (n_blocks == 0) return cuda_status(cudaGetLastError());
     if (prec == ANOVA_PREC_F16)
         adjoint_kernels<__half2>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
-                                 2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc);
+                                 2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc, mma_step);
     else if (prec == ANOVA_PREC_BF16)
         adjoint_kernels<__nv_bfloat162>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
-                                        2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc);
+                                        2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc, mma_step);
     else
         adjoint_kernels<float2>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
-                                max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc);
+                                max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc, mma_step);
     return cuda_status(cudaGetLastError());
 }
 
@@ -1303,9 +1327,18 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
     }
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s) mr = p.h_terms[s].mr > 0 ? p.h_terms[s].mr : mr;
+    // spread steps of 64 nodes where the order-1/2 cells hold a thousand nodes
+    // or more on average (d = 30 workload: 1950), else 32 (d = 20: 244)
+    long long cells = 1;
+    for (int s = 0; s < p.n_terms; ++s) {
+        const Term &T = p.h_terms[s];
+        if (T.order == 2) cells = std::max(cells, (long long)T.n * T.n);
+        if (T.order == 1) cells = std::max(cells, (long long)T.n);
+    }
+    const int mma_step = p.M >= 1000 * cells ? 64 : 32;
     return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.n_items, p.n_items3, p.counter, p.n_act, mr,
                           p.max_grid_bytes, p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0,
-                          (double2 *)p.scratch, p.precision, p.srec && p.cell_tc);
+                          (double2 *)p.scratch, p.precision, p.srec && p.cell_tc, mma_step);
 }
 
 }  // namespace agft

@@ -97,7 +97,7 @@ static int batch_trafo(Batch &b, cudaStream_t st, const float2 *fhat, float2 *f)
 static int batch_adjoint(Batch &b, cudaStream_t st, const float2 *y, float2 *fhat) {
     return adjoint_launch(nullptr, st, b.views[0], b.args, b.P, y, fhat, b.n_items, b.n_items3, b.counter,
                           b.n_blocks, b.mr, b.max_grid_bytes, b.max_fft, b.sm_count, b.max_grid_elems, b.any_empty,
-                          b.scratch, ANOVA_PREC_F32, b.cell_tc);
+                          b.scratch, ANOVA_PREC_F32, b.cell_tc, 32);
 }
 
 // ----------------------------------------------------- segmented kernels --

@@ -253,7 +253,7 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
                    float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks, int mr,
                    long long max_grid_bytes, int max_fft_elems, int sm_count, long long max_grid_elems,
-                   bool any_empty, double2 *scratch, int prec, bool tc);
+                   bool any_empty, double2 *scratch, int prec, bool tc, int mma_step);
 size_t spread_smem_bytes(long long max_grid_bytes, bool o3, int sp);
 int spread_block_nodes(long long max_grid_bytes);
 // Sorts the nodes by grid cell for every term with sort_slot >= 0 (sort.cu).
