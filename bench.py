@@ -10,8 +10,17 @@ grouped_adjoint through the C ABI.  Inputs are resident in HBM for ``value``;
 both results) inside the timed region.  L2 is flushed (256 MB write) before
 every timed step, outside the step's events.
 
+The default line also carries ``lambda_path``: the group-lasso lambda path of
+the d = 30 workload (466 terms, M = 2e6, 20 lambda values) solved three ways
+-- FP32 with the learned group screen, FP32 on all groups, FP64 on all groups
+(the plain path) -- with their times, iterations, active groups and KKT
+residuals per lambda, the agreement of the screened FP32 path with the FP64
+path, and the SM clocks sampled over that region (``--no-lambda-path`` leaves
+it out).
+
 ``--impl reference`` times the FP64 oracle (direct summation on the host
-cores) on a bounded node sample of the same workload and scales to M = 1e6.
+cores): every step is one pair on a bounded node sample of the same workload,
+and ``value`` is the oracle's rate in pairs of the full workload per second.
 
 ``--precision f64`` measures the same pairs on an FP64 plan (the plain FP64
 path).  ``--mode lambda-path`` runs the group-lasso lambda path of the d = 30
@@ -66,6 +75,7 @@ def parse():
     ap.add_argument("--max-it", type=int, default=5000, help="lambda-path mode: FISTA iterations per lambda")
     ap.add_argument("--tol", type=float, default=1e-6, help="lambda-path mode: FISTA relative-change stop")
     ap.add_argument("--skip-f64", action="store_true", help="lambda-path mode: leave out the FP64 path")
+    ap.add_argument("--no-lambda-path", action="store_true", help="pairs mode: leave out the lambda-path object")
     a = ap.parse_args()
     if a.M <= 0:
         a.M = {"pairs": 1_000_000, "lambda-path": 2_000_000, "lsqr-path": 500_000}.get(a.mode, 1_000_000)
@@ -143,11 +153,29 @@ def oracle_pair_seconds(w, m: int):
     return time.perf_counter() - t0, ndft.default_threads()
 
 
+def pairs_config(args) -> dict:
+    """The workload of the pairs line (both arms print the same)."""
+    return {"workload": WORKLOAD, "M": args.M, "l2": "flushed (256 MB write) before every timed step",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def pairs_method(args) -> dict:
+    """How this library computes the pairs (the GPU arm only)."""
+    return {"precision": "fp64 throughout" if args.precision == "f64" else "fp32 grids and accumulation",
+            "window": "Kaiser-Bessel, sigma=2, 6 row x 8 column taps",
+            "cell_products": "CUDA cores" if args.cell_kernel else "tensor cores (TF32 split, 3 products)"}
+
+
 def run_reference(args, rank, world):
+    """The oracle arm: every step is one F and one F^H of the FP64 direct sums
+    on the first `cpu_sample` nodes of the workload (all 211 terms), on the
+    host cores.  `ms_per_step` is that measured step; `value` is the oracle's
+    rate in pairs of the full workload per second, i.e. the sampled fraction of
+    a pair (m / M) done per step over the step time."""
     if rank != 0:
         return
     from paper_2010_10199_gb300 import inputs
-    m = args.cpu_sample
+    m = min(args.cpu_sample, args.M)
     w = inputs.c2_scale(M=max(m, 1))
     times = []
     cores = 1
@@ -155,15 +183,16 @@ def run_reference(args, rank, world):
         t, cores = oracle_pair_seconds(w, m)
         if i >= args.warmup:
             times.append(t)
-    per_pair_full = sum(times) / len(times) * (args.M / m)
-    value = 1.0 / per_pair_full
+    step_s = sum(times) / len(times)
+    value = (m / args.M) / step_s
+    sample = (f"each step: one pair on the first {m} of {args.M} nodes, all 211 terms, FP64 direct sums "
+              f"({step_s:.2f} s); value = {m}/{args.M} of a pair per step / step time")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_pair_full * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64)",
-            "config": {"workload": WORKLOAD, "M": args.M, "sample_nodes": m},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{m} of {args.M} nodes per step, all 211 terms; scaled linearly in M"},
+            "config": pairs_config(args), "sample": sample,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -321,8 +350,9 @@ def run_mine(args, rank, world, local_rank):
     if f64:
         alu_peak, alu_basis = 1.25, "nominal FP64 rate of the GB300 (1.25 TFLOP/s)"
     else:
-        alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
-        alu_basis = "FP32 FMA: 152 SMs x 128 lanes x 2 flops x median SM clock in the timed region"
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = n_sm * 128 * 2 * clk_mhz * 1e6 / 1e12
+        alu_basis = f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 flops x median SM clock in the timed region"
     achieved_flops = alg_flops / (kms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved_flops, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": achieved_flops / alu_peak, "traffic": traffic, "kernel": kname, "kernel_ms": kms,
@@ -353,32 +383,40 @@ def run_mine(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
                 "data": "synthetic (seeded SplitMix64)",
-                "config": {"workload": WORKLOAD, "M": args.M,
-                           "precision": "fp64 throughout" if f64 else "fp32 grids and accumulation",
-                           "window": "Kaiser-Bessel, sigma=2, 6 row x 8 column taps",
-                           "cell_products": "CUDA cores" if args.cell_kernel else "tensor cores (TF32 split, 3 products)",
-                           "l2": "flushed (256 MB write) before every timed step",
-                           "parallelism": f"replicas x{world}"},
+                "config": pairs_config(args), "method": pairs_method(args),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
                 # algorithmic (node, non-empty term) pairs of both transforms per second, all ranks
                 "point_terms_per_s": value * 2 * args.M * (n_terms2 + n_terms1),
                 "wall_s": wall}
-        print(json.dumps(line), flush=True)
     P.close()
+    del xd, fhat, y, f, g, flush
+    if rank == 0:
+        if world == 1 and not args.no_lambda_path and args.precision == "f32":
+            torch.cuda.empty_cache()
+            line["lambda_path"] = lambda_path_result(args, local_rank, 2_000_000, 20)
+        print(json.dumps(line), flush=True)
 
 
 # ----------------------------------------------------------- lambda path ---
 
-def run_lambda_path(args, local_rank):
+LAMBDA_WORKLOAD = ("d=30, |u|<=2 (466 terms), N=32 (1D) / 16x16 (2D), 98806 coeffs, M={M} uniform nodes, "
+                   "5 active pairs + 3 singletons, noise 0.05")
+
+
+def lambda_path_result(args, local_rank, M: int, K: int) -> dict:
     """Group-lasso lambda path of the d = 30 workload: FP32 with the learned
     screen vs FP32 on all groups vs FP64 on all groups (the plain path).
 
     The workload's lambda values are read for the node-averaged data term
     (1 / (2M)) ||y - F f||^2; the paper's functional has 1/2 ||y - F f||^2, so
-    the path runs with M times the listed values.  The screen is trained on the
-    paths of three problems of the same family at M / 8 nodes (seeds 101..103);
-    that training time is reported apart from the path times."""
+    the path runs with M times the listed values.  Read literally, every listed
+    value lies far below the groups' KKT scores at f = 0 (reported as
+    `literal_reading`).  The screen is trained on the paths of three problems
+    of the same family at M / 8 nodes (seeds 101..103); that training time is
+    reported apart from the path times.  Every solution's KKT residuals
+    (anova_kkt_check, one F and one F^H over all terms on the solution's own
+    plan) are reported per lambda: max over groups of the relative residual."""
     import numpy as np
     import torch
 
@@ -388,11 +426,11 @@ def run_lambda_path(args, local_rank):
     cuda_build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    M = args.M
-    K = max(1, min(20, args.lambdas))
+    K = max(1, min(20, K))
     w = inputs.c4_fista(M=M)
     terms, bw = w["terms"], w["bandwidths"]
     lams = [float(M * v) for v in w["lambdas"][:K]]
+    G = len(terms)
 
     def sync_time(fn):
         torch.cuda.synchronize()
@@ -427,11 +465,14 @@ def run_lambda_path(args, local_rank):
     x32 = torch.from_numpy(w["x"].astype(np.float32)).to(dev)
     y32 = torch.from_numpy(w["y"].astype(np.complex64)).to(dev)
     P32 = gft.Plan(x32, terms, bw)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
     (scr, sinfo, stats), t_scr = sync_time(
         lambda: gft.fista_screened_path(P32, net, y32, lams, max_it=args.max_it, tol=args.tol, threshold=0.5))
     (full32, finfo, rc32), t_full32 = sync_time(lambda: P32.fista(y32, lams, max_it=args.max_it, tol=args.tol))
+    clk32 = clocks.stop()
 
-    blocks = [P32.term_offset(u) for u in range(len(terms))]
+    blocks = [P32.term_offset(u) for u in range(G)]
 
     def groups(path):
         out = []
@@ -445,37 +486,72 @@ def run_lambda_path(args, local_rank):
         b = b.to(torch.complex128)
         return float(torch.linalg.vector_norm(a - b) / max(float(torch.linalg.vector_norm(b)), 1e-300))
 
+    def kkt_max(P, yv, path):
+        return [float(max(P.kkt(yv, path[i].contiguous(), lams[i], rtol=1e-3)[0])) for i in range(K)]
+
+    # the literal reading: KKT scores ||(F^H y)_u|| of every group at f = 0
+    zero = torch.zeros(P32.n_coeffs, dtype=torch.complex64, device=dev)
+    v0, _ = P32.kkt(y32, zero, 1.0, rtol=0.0)
+    scores = [1.0 + v for v in v0]   # (||q_u|| - 1) / 1 + 1
     g_scr, g_full32 = groups(scr), groups(full32)
     res = {"fp32_screened_s": t_scr, "fp32_full_s": t_full32, "screen_training_s": t_train,
            "fp32_screened_iterations": int(sum(i["iterations"] for i in sinfo)),
            "fp32_full_iterations": int(sum(i["iterations"] for i in finfo)),
-           "screen_term_iterations": stats.get("term_iterations") if isinstance(stats, dict) else None,
-           "active_groups": [int(a.sum()) for a in g_full32],
+           "iterations_per_lambda": {"fp32_screened": [int(i["iterations"]) for i in sinfo],
+                                     "fp32_full": [int(i["iterations"]) for i in finfo]},
+           "screen_term_iterations": stats.get("term_iterations"),
+           "full_term_iterations": stats.get("full_term_iterations"),
+           "active_groups_per_lambda": [int(a.sum()) for a in g_full32],
+           "kkt_max_residual_per_lambda": {"fp32_screened": kkt_max(P32, y32, scr),
+                                           "fp32_full": kkt_max(P32, y32, full32)},
            "screened_vs_fp32_full": {"max_rel_l2": max(rel(scr[i], full32[i]) for i in range(K)),
-                                     "active_sets_equal": all(np.array_equal(a, b) for a, b in zip(g_scr, g_full32))}}
+                                     "active_sets_equal": all(np.array_equal(a, b) for a, b in zip(g_scr, g_full32))},
+           "clocks_fp32": clk32}
+    del full32
     P32.close()
     value = None
     if not args.skip_f64:
+        torch.cuda.empty_cache()
         x64 = torch.from_numpy(w["x"]).to(dev)
         y64 = torch.from_numpy(w["y"]).to(dev)
         P64 = gft.Plan(x64, terms, bw, precision=gft.PREC_F64)
+        clocks = ClockSampler(local_rank)
+        clocks.start()
         (p64, i64, rc64), t64 = sync_time(lambda: P64.fista(y64, lams, max_it=args.max_it, tol=args.tol))
+        clk64 = clocks.stop()
         g64 = groups(p64)
         res.update({"fp64_full_s": t64, "fp64_full_iterations": int(sum(i["iterations"] for i in i64)),
-                    "screened_vs_fp64_full": {"max_rel_l2": max(rel(scr[i], p64[i]) for i in range(K)),
-                                              "active_sets_equal": all(np.array_equal(a, b)
-                                                                       for a, b in zip(g_scr, g64))}})
+                    "clocks_fp64": clk64})
+        res["iterations_per_lambda"]["fp64_full"] = [int(i["iterations"]) for i in i64]
+        res["kkt_max_residual_per_lambda"]["fp64_full"] = kkt_max(P64, y64, p64)
+        res["screened_vs_fp64_full"] = {
+            "max_rel_l2": max(rel(scr[i], p64[i]) for i in range(K)),
+            "rel_l2_per_lambda": [rel(scr[i], p64[i]) for i in range(K)],
+            "active_sets_equal": all(np.array_equal(a, b) for a, b in zip(g_scr, g64))}
         value = t64 / t_scr
         P64.close()
-    line = {"metric": "FISTA lambda-path time: plain FP64 full-group path / FP32 screened path",
-            "value": value, "unit": "x", "higher_is_better": True, "n_gpus": 1,
-            "dtype": "f32 (screened) vs f64 (plain)", "data": "synthetic (seeded SplitMix64)",
-            "config": {"workload": f"d=30, |u|<=2 (466 terms), N=32 (1D) / 16x16 (2D), M={M} uniform nodes, "
-                                   f"5 active pairs + 3 singletons, noise 0.05",
-                       "lambdas": f"first {K} of 20 geometric 1e-1..1e-5, times M",
-                       "fista": f"constant step L = 1.05 x Lanczos estimate of ||F||^2, tol {args.tol}, max_it {args.max_it}, "
-                                f"warm-started path"},
+    res["fp64_full_over_fp32_screened"] = value
+    return {"metric": "FISTA lambda-path time: plain FP64 full-group path / FP32 screened path",
+            "value": value, "unit": "x", "higher_is_better": True,
+            "workload": LAMBDA_WORKLOAD.format(M=M),
+            "lambdas": {"used": [v / M for v in lams], "scale": "x M (node-averaged data term reading)",
+                        "literal_reading": {"values": [v / M for v in lams],
+                                            "group_kkt_scores_at_zero_min": min(scores),
+                                            "group_kkt_scores_at_zero_max": max(scores),
+                                            "note": "every listed value is below every group's score at f = 0"
+                                                    if min(scores) > max(v / M for v in lams) else
+                                                    "some group score at f = 0 is below a listed value"}},
+            "fista": f"constant step L = 1.05 x Lanczos estimate of ||F||^2, tol {args.tol}, max_it {args.max_it}, "
+                     f"warm-started path; screen: 7-128-128-1 MLP, threshold 0.5, KKT re-admission",
             "results": res}
+
+
+def run_lambda_path(args, local_rank):
+    r = lambda_path_result(args, local_rank, args.M, args.lambdas)
+    line = {"metric": r["metric"], "value": r["value"], "unit": "x", "higher_is_better": True, "n_gpus": 1,
+            "dtype": "f32 (screened) vs f64 (plain)", "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": r["workload"], "lambdas": r["lambdas"], "fista": r["fista"]},
+            "results": r["results"]}
     print(json.dumps(line), flush=True)
 
 
@@ -570,7 +646,9 @@ def run_lsqr_path(args, local_rank):
     for lam in w["lambdas"]:
         fh, info, rc = P.lsqr(y, float(lam), max_it=args.max_it, atol=1e-6, btol=1e-6)
         per.append({"lambda": float(lam), "iterations": info["iterations"], "seconds": info["seconds"],
-                    "rnorm": info["rnorm"], "status": rc})
+                    "stop_reason": ["max_it", "breakdown", "residual test", "normal-equation test"][
+                        info["stop_reason"]],
+                    "rnorm": info["rnorm"], "arnorm": info["arnorm"], "status": rc})
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
     its = sum(q["iterations"] for q in per)
@@ -579,7 +657,8 @@ def run_lsqr_path(args, local_rank):
             "data": "synthetic (seeded SplitMix64)",
             "config": {"workload": f"d=10, |u|<=3 (176 terms), N=100 / 24x24 / 10x10x10, M={args.M} Beta(2,2) nodes",
                        "lsqr": f"atol = btol = 1e-6, at most {args.max_it} iterations per lambda, graph-replayed"},
-            "results": {"iterations": its, "ms_per_iteration": 1e3 * total / max(its, 1), "per_lambda": per}}
+            "results": {"iterations": its, "ms_per_iteration": 1e3 * total / max(its, 1),
+                        "converged_lambdas": sum(q["stop_reason"] != "max_it" for q in per), "per_lambda": per}}
     print(json.dumps(line), flush=True)
 
 

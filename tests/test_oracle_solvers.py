@@ -206,12 +206,81 @@ def test_power_iteration_matches_svd():
     assert abs(est - np.linalg.norm(Fm, 2) ** 2) / est < 1e-8
 
 
-def test_sobol_indices_sum_to_one():
-    f = inputs.complex_normal(5, 2, 30)
-    offs, lens = np.array([0, 1, 10]), np.array([1, 9, 20])
-    rho = solvers.sobol_indices(f, offs, lens)
-    assert rho[0] == 0 and abs(rho.sum() - 1) < 1e-14
-    assert solvers.active_set(rho, [(), (0,), (0, 1)], [0.5, 0.5]) == [0] + [i for i in (1, 2) if rho[i] > 0.5]
+def _sobol_pins_hold(sobol) -> bool:
+    """Values of rho(u) = sigma^2(f_u) / sigma^2(f) (eq. (gsi)) worked out by
+    hand through Parseval: sigma^2(f_u) = sum_{k in block u} |c_k|^2 and
+    sigma^2(f) = ||f||^2 - |c_0|^2 = the sum over the non-empty blocks."""
+    ok = True
+    # blocks: empty {c_0 = 100}, u1 {2}, u2 {1}: energies 4 and 1 -> 4/5, 1/5;
+    # c_0 is the mean and does not enter the variance
+    f = np.array([100.0, 2.0, 1.0], dtype=np.complex128)
+    rho = sobol(f, np.array([0, 1, 2]), np.array([1, 1, 1]))
+    ok &= bool(np.allclose(rho, [0.0, 0.8, 0.2], rtol=0, atol=1e-15))
+    # several coefficients per block, complex values: |1+1j|^2 + |1|^2 = 3,
+    # |2j|^2 + |-1|^2 + |0|^2 = 5, |3|^2 = 9 -> 3/17, 5/17, 9/17
+    f = np.array([7 - 3j, 1 + 1j, 1, 2j, -1, 0, 3], dtype=np.complex128)
+    rho = sobol(f, np.array([0, 1, 3, 6]), np.array([1, 2, 3, 1]))
+    ok &= bool(np.allclose(rho, [0.0, 3 / 17, 5 / 17, 9 / 17], rtol=0, atol=1e-15))
+    return ok
+
+
+def test_sobol_indices_match_hand_values():
+    assert _sobol_pins_hold(solvers.sobol_indices)
+
+
+def test_sobol_pins_catch_planted_mistakes():
+    """Each plausible mistake in rho(u) fails the hand-worked values above."""
+    def no_square(f, offs, lens):       # |c_k| instead of |c_k|^2 (Parseval's square dropped)
+        e = np.array([float(np.sum(np.abs(f[o:o + n]))) for o, n in zip(offs, lens)])
+        r = np.zeros_like(e)
+        r[1:] = e[1:] / e[1:].sum()
+        return r
+
+    def with_mean(f, offs, lens):       # ||f||^2 instead of ||f||^2 - |c_0|^2 in the denominator
+        e = np.array([float(np.sum(np.abs(f[o:o + n]) ** 2)) for o, n in zip(offs, lens)])
+        r = e / e.sum()
+        r[0] = 0.0
+        return r
+
+    def real_only(f, offs, lens):       # Re(c_k)^2 only
+        e = np.array([float(np.sum(f[o:o + n].real ** 2)) for o, n in zip(offs, lens)])
+        r = np.zeros_like(e)
+        r[1:] = e[1:] / e[1:].sum()
+        return r
+
+    for bad in (no_square, with_mean, real_only):
+        assert not _sobol_pins_hold(bad), bad.__name__
+
+
+def _active_set_pins_hold(active) -> bool:
+    """U* = {empty} cup {u : rho(u) > eps_|u|} (eq. (activeset)): strict
+    inequality, the threshold chosen by the order of u, the empty set always in."""
+    terms = [(), (0,), (1,), (0, 1), (0, 1, 2), (2,)]
+    rho = np.array([0.0, 0.3, 0.1, 0.1, 0.05, 0.1])
+    eps = [0.1, 0.05, 0.01]   # eps_1, eps_2, eps_3
+    # (0,): 0.3 > 0.1 in; (1,): 0.1 = eps_1 out; (0,1): 0.1 > 0.05 in;
+    # (0,1,2): 0.05 > 0.01 in; (2,): 0.1 = eps_1 out; the empty set in although rho = 0
+    ok = active(rho, terms, eps) == [0, 1, 3, 4]
+    ok &= active(np.zeros(6), terms, eps) == [0]
+    return bool(ok)
+
+
+def test_active_set_matches_hand_values():
+    assert _active_set_pins_hold(solvers.active_set)
+
+
+def test_active_set_pins_catch_planted_mistakes():
+    def ge(rho, terms, eps):            # >= instead of >
+        return [i for i, u in enumerate(terms) if len(u) == 0 or rho[i] >= eps[len(u) - 1]]
+
+    def no_empty(rho, terms, eps):      # the empty set left out
+        return [i for i, u in enumerate(terms) if len(u) > 0 and rho[i] > eps[len(u) - 1]]
+
+    def order_index(rho, terms, eps):   # eps indexed by |u| instead of |u| - 1
+        return [i for i, u in enumerate(terms) if len(u) == 0 or rho[i] > eps[min(len(u), len(eps) - 1)]]
+
+    for bad in (ge, no_empty, order_index):
+        assert not _active_set_pins_hold(bad), bad.__name__
 
 
 def test_lsqr_residual_estimate_is_the_damped_residual():
