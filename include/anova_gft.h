@@ -387,11 +387,29 @@ int anova_plan_autotune(anova_plan_options *opts, int d, int64_t M, const void *
  * stream capture.  Every call reuses the same array and overwrites the
  * previous call's contents, so calls that can overlap on the GPU (different
  * streams or devices sharing a context, or host threads) race: serialise them.
+ * A call on a stream that is capturing returns ANOVA_ERR_UNSUPPORTED and
+ * enqueues nothing: its table uploads read host staging memory that the next
+ * call overwrites.  An error left pending by earlier, unrelated work is
+ * cleared at entry, not reported.
  * Returns after enqueueing the work.
  */
 int grouped_trafo_noalloc(int d, int64_t M, const float *x_dev, int n_terms, const int32_t *term_dims,
                           const int32_t *bandwidth, const anova_cfloat *fhat_dev, anova_cfloat *f_dev,
                           void *stream);
+
+/*
+ * anova_debug_fail_allocation -- fault injection for tests (no counterpart in
+ * the paper).  After a call with k > 0, the k-th following device or host
+ * allocation made by anova_plan_create (or by the first solver call on a plan,
+ * which creates the solver workspace) fails as if the device or host were out
+ * of memory; the allocations after it succeed again.  k = 0 cancels a pending
+ * failure.  A failing plan creation returns ANOVA_ERR_NOMEM after freeing
+ * everything it had allocated, or -- where the failed allocation was an
+ * optional one (the cell-sorted node copy, the fixed-point accumulators) --
+ * builds the plan without it.  Process-wide; not for concurrent use.
+ * Errors: ANOVA_ERR_INVALID for k < 0.
+ */
+int anova_debug_fail_allocation(int k);
 
 /* Human-readable name of a status code (static string). */
 const char *anova_status_string(int status);

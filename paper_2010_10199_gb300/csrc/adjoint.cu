@@ -91,16 +91,27 @@ int spread_block_nodes(long long max_grid_bytes) {
 // the tensor-core kernel with STEP-node steps: grid, one ring per warp, item slot
 static size_t spread_mma_smem_bytes(long long max_grid_bytes, int step);
 
-int spread_ctas_per_sm(long long max_grid_bytes, bool tc) {
+int spread_ctas_per_sm(long long max_grid_bytes, bool tc, int step) {
     if (tc) {
-        const size_t per = spread_mma_smem_bytes(max_grid_bytes, 32) + 1024;
+        const size_t per = spread_mma_smem_bytes(max_grid_bytes, step) + 1024;
         return (int)std::max<size_t>(1, std::min<size_t>(SPREAD_MMA_CTAS_PER_SM, (size_t)(MAX_SMEM + 1024) / per));
     }
     return ctas_for(max_grid_bytes, spread_block_nodes(max_grid_bytes));
 }
 
-int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc) {
-    const long long resident = (long long)spread_ctas_per_sm(max_grid_bytes, tc) * sm_count;
+int spread_step_for(const Plan &p) {
+    long long cells = 1;
+    for (int s = 0; s < p.n_terms; ++s) {
+        const Term &T = p.h_terms[s];
+        if (T.order == 2) cells = std::max(cells, (long long)T.n * T.n);
+        if (T.order == 1) cells = std::max(cells, (long long)T.n);
+    }
+    return p.M >= 1000 * cells ? 64 : 32;
+}
+
+int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc,
+                      int step) {
+    const long long resident = (long long)spread_ctas_per_sm(max_grid_bytes, tc, step) * sm_count;
     long long K = (3 * resident + std::max(1, n_act_total) - 1) / std::max(1, n_act_total);
     K = std::min<long long>(K, (M + 2047) / 2048);
     K = std::min<long long>(K, kmax);
@@ -1220,8 +1231,8 @@ __global__ void sum_y_stage2(DevPlan single, BatchArgs B, const double2 *part_ba
 
 template <typename G>
 static void adjoint_attrs() {
-    static bool attr_done = false;
-    if (!attr_done) {
+    static std::atomic<unsigned long long> attr_seen{0};
+    once_per_device(attr_seen, [] {
         cudaFuncSetAttribute(adjoint_post_f32<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(spread_f32<3, G, SP_CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread_f32<4, G, SP_CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
@@ -1235,8 +1246,7 @@ static void adjoint_attrs() {
         cudaFuncSetAttribute(spread_mma_f32<3, G, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread_mma_f32<4, G, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        attr_done = true;
-    }
+    });
 }
 
 // spread + reduce + post for grids stored as G; sgrid = bytes of the largest
@@ -1249,7 +1259,7 @@ static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const
     adjoint_attrs<G>();
     const int sp = spread_block_nodes(sgrid);
     const size_t ssm = spread_smem_bytes(sgrid, false, sp), ssm3 = spread_smem_bytes(sgrid, true, sp);
-    const int per_sm = spread_ctas_per_sm(sgrid, false);
+    const int per_sm = spread_ctas_per_sm(sgrid, false, mma_step);
     if (prof) stage_begin(*prof, ST_SPREAD);
     cudaMemsetAsync(counter, 0, 2 * sizeof(int), st);
     if (n_items3 > 0 && tc) {
@@ -1328,14 +1338,9 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s) mr = p.h_terms[s].mr > 0 ? p.h_terms[s].mr : mr;
     // spread steps of 64 nodes where the order-1/2 cells hold a thousand nodes
-    // or more on average (d = 30 workload: 1950), else 32 (d = 20: 244)
-    long long cells = 1;
-    for (int s = 0; s < p.n_terms; ++s) {
-        const Term &T = p.h_terms[s];
-        if (T.order == 2) cells = std::max(cells, (long long)T.n * T.n);
-        if (T.order == 1) cells = std::max(cells, (long long)T.n);
-    }
-    const int mma_step = p.M >= 1000 * cells ? 64 : 32;
+    // or more on average (d = 30 workload: 1950), else 32 (d = 20: 244); the
+    // plan chose it, and sized its node chunks for it
+    const int mma_step = p.mma_step == 64 ? 64 : 32;
     return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.n_items, p.n_items3, p.counter, p.n_act, mr,
                           p.max_grid_bytes, p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0,
                           (double2 *)p.scratch, p.precision, p.srec && p.cell_tc, mma_step);

@@ -78,11 +78,10 @@ static int upload_views(Batch &b) {
 
 static int batch_trafo(Batch &b, cudaStream_t st, const float2 *fhat, float2 *f) {
     const size_t pre_smem = (size_t)b.max_fft * 2 * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_seen{0};
+    once_per_device(attr_seen, [] {
         cudaFuncSetAttribute(trafo_pre_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    });
     trafo_pre_f32<<<b.n_blocks, 256, pre_smem, st>>>(b.views[0], b.args, fhat);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
@@ -303,7 +302,7 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
     std::vector<int> Ks(n_problems);
     for (int p = 0; p < n_problems; ++p) {
         Plan &pl = b->plans[p]->p;
-        Ks[p] = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count, b->cell_tc);
+        Ks[p] = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count, b->cell_tc, 32);
         b->views[p].spread_chunks = Ks[p];
     }
     // third-order items of every problem first, then the others

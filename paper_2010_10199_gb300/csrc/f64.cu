@@ -212,11 +212,10 @@ int launch_trafo_f64(Plan &p, const double2 *fhat, double2 *f) {
         fill_const_f64<<<blocks, 256, 0, p.stream>>>(f, p.M, fhat, p.empty_off, p.n_empty, p.skip);
         return cuda_status(cudaGetLastError());
     }
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_seen{0};
+    once_per_device(attr_seen, [] {
         cudaFuncSetAttribute(trafo_pre_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
-    }
+    });
     const size_t pre_smem = (size_t)p.max_fft_elems * 2 * sizeof(double2);
     stage_begin(p, ST_PRE);
     trafo_pre_f64<<<p.n_act, 256, pre_smem, p.stream>>>(v, fhat);
@@ -512,12 +511,11 @@ int launch_adjoint_f64(Plan &p, const double2 *y, double2 *fhat) {
         cudaMemsetAsync(fhat, 0, sizeof(double2) * p.n_coeffs, st);
         return cuda_status(cudaGetLastError());
     }
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_seen{0};
+    once_per_device(attr_seen, [] {
         cudaFuncSetAttribute(spread_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(adjoint_post_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
-    }
+    });
     if (p.n_empty > 0) {
         const int nb = 256;
         stage_begin(p, ST_SUMY);

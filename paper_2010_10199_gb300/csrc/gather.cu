@@ -337,11 +337,10 @@ gather2_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ fhat_base, f
 template <int MR, int PITCH, typename G>
 static void launch_one(cudaStream_t st, const DevPlan &v, const BatchArgs &B, const float2 *fhat, float2 *f,
                        int n_tiles, size_t smem, int ctas, int pitch, long long max_grid_bytes, int dmax) {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_seen{0};
+    once_per_device(attr_seen, [] {
         cudaFuncSetAttribute(gather2_f32<MR, PITCH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        attr = true;
-    }
+    });
     gather2_f32<MR, PITCH, G><<<ctas, G2_THREADS, smem, st>>>(v, B, fhat, f, n_tiles, pitch, max_grid_bytes, dmax);
 }
 

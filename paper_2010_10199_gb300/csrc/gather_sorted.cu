@@ -483,14 +483,13 @@ int gather_sorted_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, 
                          float2 *f, const int4 *items, int n_items3, int item_end, int *counter,
                          long long max_grid_bytes, long long max_M, int sm_count, int mr, double *part, bool tc) {
     const int item_begin = 0;
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_seen{0};
+    once_per_device(attr_seen, [] {
         cudaFuncSetAttribute(gather_sorted_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(gather_sorted_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(gather_mma_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(gather_mma_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        attr = true;
-    }
+    });
     // Order-1/2 items on the tensor cores only where no third-order item (the
     // first n_items3, always on the CUDA cores) precedes them: two launches in
     // a row idle the GPU at the seam, which costs more than the tensor cores

@@ -11,8 +11,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
+#include <new>
 
 #include "anova_gft.h"
 
@@ -199,6 +201,7 @@ struct Plan {
     int *counter;           // work-queue counter of the spread
     float4 *srec;           // cell-sorted node records (null: none), n_sorted slots of M
     bool cell_tc;           // order-1/2 spread of sorted records on the tensor cores
+    int mma_step;           // ring step (nodes) of that spread, see spread_step_for
     int n_sorted;
     unsigned long long *facc;   // sorted forward: fixed-point accumulators [M][2]
     int *fexp;              // and their exponent
@@ -220,7 +223,23 @@ struct Plan {
 
 DevPlan dev_view(const Plan &p);
 int set_active_terms(Plan &p, const unsigned char *user_mask);
-inline cudaError_t cuda_err_of(int status) { return status == ANOVA_OK ? cudaSuccess : cudaErrorUnknown; }
+inline cudaError_t cuda_err_of(int status) {
+    return status == ANOVA_OK ? cudaSuccess : status == ANOVA_ERR_NOMEM ? cudaErrorMemoryAllocation : cudaErrorUnknown;
+}
+
+// Allocations of plan construction and of the solver workspaces go through
+// these two, so that a test can make the k-th of them fail the way an
+// exhausted device or host would (anova_debug_fail_allocation).
+bool alloc_fault();
+cudaError_t plan_malloc_raw(void **ptr, size_t bytes);
+template <typename T>
+inline cudaError_t plan_malloc(T **ptr, size_t bytes) {
+    return plan_malloc_raw((void **)ptr, bytes);
+}
+template <typename T>
+inline T *plan_new(size_t n) {
+    return alloc_fault() ? nullptr : new (std::nothrow) T[n];
+}
 
 // host-side table builders shared with plan construction (plan.cu)
 double deconv_factor(int k, int n, int m, double b);
@@ -262,12 +281,17 @@ int sort_nodes_by_cell(Plan &p);
 int build_window_tables_f64(Plan &p);
 int launch_trafo_f64(Plan &p, const double2 *fhat, double2 *f);
 int launch_adjoint_f64(Plan &p, const double2 *y, double2 *fhat);
-// CTAs per SM of the order-1/2 spread kernel (tc: the tensor-core one)
-int spread_ctas_per_sm(long long max_grid_bytes, bool tc);
+// CTAs per SM of the order-1/2 spread kernel (tc: the tensor-core one with
+// `step`-node ring steps)
+int spread_ctas_per_sm(long long max_grid_bytes, bool tc, int step);
+// Ring step of the tensor-core spread for a plan: 64 nodes where its
+// order-1/2 cells hold a thousand nodes or more on average, else 32.
+int spread_step_for(const Plan &p);
 // Node chunks per term for a spread over n_act_total active terms (all
 // problems of a launch) on sm_count SMs: about three items per resident CTA,
 // at most kmax, at least 2048 nodes per chunk.
-int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc);
+int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc,
+                      int step);
 // Appends the spread work items of one problem, K chunks per active term:
 // those of the third-order terms (sel = 3) or of the others, order 2 before
 // order 1 (sel = 0).  Returns the count.
@@ -276,6 +300,21 @@ int lipschitz_estimate(Plan &p, double *L);
 int fista_impl(Plan &p, const float2 *y, const double *w, const double *lambdas, int n_lambda, int max_it,
                double tol, int step_mode, double L0, double eta, const uint8_t *mask, const float2 *f0,
                float2 *path, anova_solve_info *info, double *L_out);
+
+// Runs `set` (kernel attribute calls) unless it already ran on the current
+// device: attributes such as the dynamic shared-memory limit belong to a
+// device, so each device needs its own call.  One bit per device id < 64 in
+// `seen`; larger ids run `set` every time.  Concurrent first calls may both
+// run `set`, which is harmless.
+template <typename F>
+inline void once_per_device(std::atomic<unsigned long long> &seen, F &&set) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ULL << dev : 0ULL;
+    if (bit && (seen.load(std::memory_order_acquire) & bit)) return;
+    set();
+    if (bit) seen.fetch_or(bit, std::memory_order_release);
+}
 
 // status from a CUDA error
 inline int cuda_status(cudaError_t e) {

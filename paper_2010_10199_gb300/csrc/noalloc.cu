@@ -71,9 +71,19 @@ extern "C" int grouped_trafo_noalloc(int d, int64_t M, const float *x_dev, int n
         if (ord > 0 && bandwidth[i] > 4096) return ANOVA_ERR_UNSUPPORTED;
     }
     if (M == 0) return ANOVA_OK;
+    cudaGetLastError();   // do not report an earlier, unrelated error
+    cudaStream_t st = (cudaStream_t)stream;
+    // The table uploads below read host staging arrays that the next call
+    // overwrites, so a captured call would replay another call's tables:
+    // refuse a capturing stream before anything is enqueued.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return ANOVA_ERR_UNSUPPORTED;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return ANOVA_ERR_UNSUPPORTED;
 
     std::lock_guard<std::mutex> guard(s_lock);
-    cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);

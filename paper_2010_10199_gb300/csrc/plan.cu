@@ -167,7 +167,7 @@ int set_active_terms(Plan &p, const unsigned char *user_mask) {
     p.n_items = 0;
     p.n_items3 = 0;
     if (n == 0) return ANOVA_OK;
-    p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count, p.cell_tc);
+    p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count, p.cell_tc, p.mma_step);
     if (p.h_items) {
         p.n_items3 = append_spread_items(p, 0, p.spread_K, p.h_items, 3);
         p.n_items = p.n_items3 + append_spread_items(p, 0, p.spread_K, p.h_items + p.n_items3, 0);
@@ -215,6 +215,25 @@ DevPlan dev_view(const Plan &p) {
     return v;
 }
 
+// 0: no injected failure; k > 0: the k-th next allocation through
+// plan_malloc / plan_new fails (then the counter is 0 again)
+static std::atomic<int> g_fail_after{0};
+
+bool alloc_fault() {
+    int k = g_fail_after.load();
+    while (k > 0)
+        if (g_fail_after.compare_exchange_weak(k, k - 1)) return k == 1;
+    return false;
+}
+
+cudaError_t plan_malloc_raw(void **ptr, size_t bytes) {
+    if (alloc_fault()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
 static void free_plan(Plan &p) {
     profiler_free(p);
     if (p.solver && p.solver_free) p.solver_free(p.solver);
@@ -257,9 +276,9 @@ const char *anova_status_string(int s) {
 
 const char *anova_version(void) { return "anova-gft 0.1 (sm_103a)"; }
 
-int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, int n_terms,
-                      const int32_t *term_dims, const int32_t *bandwidth, const anova_plan_options *opts,
-                      void *stream) {
+static int plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, int n_terms,
+                       const int32_t *term_dims, const int32_t *bandwidth, const anova_plan_options *opts,
+                       void *stream) {
     if (!out) return ANOVA_ERR_INVALID;
     *out = nullptr;
     cudaGetLastError();   // do not report an earlier, unrelated error
@@ -293,9 +312,20 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         if (ord > 0 && bandwidth[i] > 4096) return ANOVA_ERR_UNSUPPORTED;
     }
 
-    anova_plan_s *h = new (std::nothrow) anova_plan_s;
+    anova_plan_s *h = alloc_fault() ? nullptr : new (std::nothrow) anova_plan_s;
     if (!h) return ANOVA_ERR_NOMEM;
     std::memset(&h->p, 0, sizeof(Plan));
+    // frees the plan on every return but the successful one (also when a
+    // host container throws std::bad_alloc on the way out)
+    struct Guard {
+        anova_plan_s *h;
+        ~Guard() {
+            if (h) {
+                free_plan(h->p);
+                delete h;
+            }
+        }
+    } guard{h};
     Plan &p = h->p;
     p.stream = (cudaStream_t)stream;
     p.precision = o.precision;
@@ -310,23 +340,21 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     int mc = o.window_m_col > 0 ? o.window_m_col : 4;
     int mr = o.window_m_row > 0 ? o.window_m_row : (o.eps >= 5e-6 ? 3 : 4);
     if (mc != 4) {   // eight column lanes per row segment
-        free_plan(p);
-        delete h;
         return ANOVA_ERR_UNSUPPORTED;
     }
     if (mr < 3 || mr > 4) {
-        free_plan(p);
-        delete h;
         return ANOVA_ERR_UNSUPPORTED;
     }
 
     // user layout
-    p.h_user_off = new long long[n_terms];
-    p.h_user_len = new long long[n_terms];
-    p.h_user_n = new int[n_terms];
-    p.h_user_mc = new int[n_terms];
-    p.h_user_mr = new int[n_terms];
-    p.h_user_order = new int[n_terms];
+    p.h_user_off = plan_new<long long>(n_terms);
+    p.h_user_len = plan_new<long long>(n_terms);
+    p.h_user_n = plan_new<int>(n_terms);
+    p.h_user_mc = plan_new<int>(n_terms);
+    p.h_user_mr = plan_new<int>(n_terms);
+    p.h_user_order = plan_new<int>(n_terms);
+    if (!p.h_user_off || !p.h_user_len || !p.h_user_n || !p.h_user_mc || !p.h_user_mr || !p.h_user_order)
+        return ANOVA_ERR_NOMEM;
     long long off = 0;
     std::vector<int> order(n_terms);
     std::vector<long long> empties;
@@ -360,7 +388,8 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         return ta[2] < tb[2];
     });
     p.n_terms = (int)sched.size();
-    p.h_terms = new Term[p.n_terms > 0 ? p.n_terms : 1];
+    p.h_terms = plan_new<Term>(p.n_terms > 0 ? p.n_terms : 1);
+    if (!p.h_terms) return ANOVA_ERR_NOMEM;
 
     // windows (dedupe on m, n, N) and deconvolution tables
     std::vector<Window> wins;
@@ -461,11 +490,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
             if (P.order == 2 && P.row0 == T.row0 && P.wr == T.wr && P.n == T.n) T.new_rowgroup = 0;
         }
     }
-    if (status != ANOVA_OK) {
-        free_plan(p);
-        delete h;
-        return status;
-    }
+    if (status != ANOVA_OK) return status;
     p.grid_elems = goff;
     p.max_grid_bytes = maxbytes;
     p.max_fft_elems = max_fft;
@@ -497,19 +522,20 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         if (r != cudaSuccess && e == cudaSuccess) e = r;
     };
     size_t xbytes = (size_t)d * M * (p.precision == ANOVA_PREC_F64 ? 8 : 4);
-    if (xbytes) chk(cudaMalloc(&p.x, xbytes));
-    chk(cudaMalloc(&p.terms, sizeof(Term) * std::max(1, p.n_terms)));
-    chk(cudaMalloc(&p.windows, sizeof(Window) * std::max<size_t>(1, wins.size())));
-    chk(cudaMalloc(&p.deconv, sizeof(float) * std::max<size_t>(1, dec.size())));
-    chk(cudaMalloc(&p.deconvd, sizeof(double) * std::max<size_t>(1, decd.size())));
-    chk(cudaMalloc(&p.empty_off, sizeof(long long) * std::max<size_t>(1, empties.size())));
+    if (xbytes) chk(plan_malloc(&p.x, xbytes));
+    chk(plan_malloc(&p.terms, sizeof(Term) * std::max(1, p.n_terms)));
+    chk(plan_malloc(&p.windows, sizeof(Window) * std::max<size_t>(1, wins.size())));
+    chk(plan_malloc(&p.deconv, sizeof(float) * std::max<size_t>(1, dec.size())));
+    chk(plan_malloc(&p.deconvd, sizeof(double) * std::max<size_t>(1, decd.size())));
+    chk(plan_malloc(&p.empty_off, sizeof(long long) * std::max<size_t>(1, empties.size())));
     const size_t esize = p.precision == ANOVA_PREC_F64 ? 16 : (p.precision == ANOVA_PREC_F32 ? 8 : 4);   // bytes per grid element
-    chk(cudaMalloc(&p.grids, (size_t)std::max<long long>(1, p.grid_elems) * esize));
-    chk(cudaMalloc(&p.err, sizeof(int) * 4));
-    chk(cudaMalloc(&p.act, sizeof(int) * std::max(1, p.n_terms)));
-    chk(cudaMalloc(&p.act_rec, sizeof(ActRec) * std::max(1, p.n_terms)));
-    chk(cudaMalloc(&p.act_rec3, sizeof(ActRec) * std::max(1, p.n_terms)));
-    p.h_act = new int[std::max(1, p.n_terms)];
+    chk(plan_malloc(&p.grids, (size_t)std::max<long long>(1, p.grid_elems) * esize));
+    chk(plan_malloc(&p.err, sizeof(int) * 4));
+    chk(plan_malloc(&p.act, sizeof(int) * std::max(1, p.n_terms)));
+    chk(plan_malloc(&p.act_rec, sizeof(ActRec) * std::max(1, p.n_terms)));
+    chk(plan_malloc(&p.act_rec3, sizeof(ActRec) * std::max(1, p.n_terms)));
+    p.h_act = plan_new<int>(std::max(1, p.n_terms));
+    if (!p.h_act && e == cudaSuccess) e = cudaErrorMemoryAllocation;
     // adjoint partial grids: one per node chunk of a term (work items of the
     // spread are (term, chunk) pairs), bounded to 8 GB
     long long k_cap = std::max<long long>(1, (8LL << 30) / std::max<long long>(1, p.grid_elems * 8));
@@ -520,16 +546,17 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
     p.gather_ctas = (int)std::min<long long>((long long)p.sm_count,
                                              std::max<long long>(1, (M + GATHER_TILE - 1) / GATHER_TILE));
     if (e == cudaSuccess && p.n_terms > 0)
-        chk(cudaMalloc(&p.partials, (size_t)kmax * (size_t)p.grid_elems * esize));
-    chk(cudaMalloc(&p.items, sizeof(int4) * (size_t)std::max(1, p.n_terms) * kmax));
-    chk(cudaMalloc(&p.counter, 2 * sizeof(int)));
-    p.h_items = new int4[(size_t)std::max(1, p.n_terms) * kmax];
+        chk(plan_malloc(&p.partials, (size_t)kmax * (size_t)p.grid_elems * esize));
+    chk(plan_malloc(&p.items, sizeof(int4) * (size_t)std::max(1, p.n_terms) * kmax));
+    chk(plan_malloc(&p.counter, 2 * sizeof(int)));
+    p.h_items = plan_new<int4>((size_t)std::max(1, p.n_terms) * kmax);
+    if (!p.h_items && e == cudaSuccess) e = cudaErrorMemoryAllocation;
     p.scratch_bytes = 1 << 20;
-    chk(cudaMalloc(&p.scratch, p.scratch_bytes));
+    chk(plan_malloc(&p.scratch, p.scratch_bytes));
     if (p.n_slots64 > 0 && M > 0) {
-        chk(cudaMalloc(&p.slots64, sizeof(int4) * p.n_slots64));
-        chk(cudaMalloc(&p.wt64, sizeof(double) * 8 * (size_t)p.n_slots64 * M));
-        chk(cudaMalloc(&p.wb64, sizeof(int) * (size_t)p.n_slots64 * M));
+        chk(plan_malloc(&p.slots64, sizeof(int4) * p.n_slots64));
+        chk(plan_malloc(&p.wt64, sizeof(double) * 8 * (size_t)p.n_slots64 * M));
+        chk(plan_malloc(&p.wb64, sizeof(int) * (size_t)p.n_slots64 * M));
         if (e == cudaSuccess)
             chk(cudaMemcpyAsync(p.slots64, slots64.data(), sizeof(int4) * p.n_slots64, cudaMemcpyHostToDevice,
                                 p.stream));
@@ -544,7 +571,7 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         size_t free_b = 0, total_b = 0;
         const size_t need = (size_t)ns * (size_t)M * sizeof(float4);
         if (ns > 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need <= free_b / 2) {
-            if (cudaMalloc(&p.srec, need) == cudaSuccess) {
+            if (plan_malloc(&p.srec, need) == cudaSuccess) {
                 int slot = 0;
                 for (int s = 0; s < p.n_terms; ++s) {
                     const int u = units(p.h_terms[s]);
@@ -556,8 +583,8 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
                 p.n_sorted = ns;
                 p.cell_tc = p.precision != ANOVA_PREC_F64 && o.cell_kernel == 0;
                 if (p.precision == ANOVA_PREC_F32) {
-                    if (cudaMalloc(&p.facc, sizeof(unsigned long long) * 2 * (size_t)M) != cudaSuccess ||
-                        cudaMalloc(&p.fexp, sizeof(int) * 4) != cudaSuccess) {
+                    if (plan_malloc(&p.facc, sizeof(unsigned long long) * 2 * (size_t)M) != cudaSuccess ||
+                        plan_malloc(&p.fexp, sizeof(int) * 4) != cudaSuccess) {
                         cudaGetLastError();   // the forward falls back to the point-major gather
                         if (p.facc) cudaFree(p.facc);
                         p.facc = nullptr;
@@ -570,8 +597,6 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
         }
     }
     if (e != cudaSuccess) {
-        free_plan(p);
-        delete h;
         cudaGetLastError();
         return cuda_status(e);
     }
@@ -597,17 +622,36 @@ int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, in
             wrap_nodes_f32<<<blocks, 256, 0, p.stream>>>((const float *)x_dev, (float *)p.x, total);
         chk(cudaGetLastError());
     }
+    p.mma_step = spread_step_for(p);
     if (e == cudaSuccess && p.precision == ANOVA_PREC_F64) chk(cuda_err_of(build_window_tables_f64(p)));
     if (e == cudaSuccess) chk(cuda_err_of(sort_nodes_by_cell(p)));
     if (e == cudaSuccess) chk(cuda_err_of(set_active_terms(p, nullptr)));
     chk(cudaStreamSynchronize(p.stream));
     // wins vector is copied; keep host term table
     if (e != cudaSuccess) {
-        free_plan(p);
-        delete h;
+        cudaGetLastError();
         return cuda_status(e);
     }
+    guard.h = nullptr;
     *out = h;
+    return ANOVA_OK;
+}
+
+int anova_plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, int n_terms,
+                      const int32_t *term_dims, const int32_t *bandwidth, const anova_plan_options *opts,
+                      void *stream) {
+    try {
+        return plan_create(out, d, M, x_dev, n_terms, term_dims, bandwidth, opts, stream);
+    } catch (const std::bad_alloc &) {
+        return ANOVA_ERR_NOMEM;
+    } catch (...) {
+        return ANOVA_ERR_CUDA;
+    }
+}
+
+int anova_debug_fail_allocation(int k) {
+    if (k < 0) return ANOVA_ERR_INVALID;
+    g_fail_after.store(k);
     return ANOVA_OK;
 }
 

@@ -103,7 +103,7 @@ SolverWork *get_work(Plan &p, int &rc) {
     const size_t bm = es * std::max<long long>(1, p.M), bn = es * std::max<long long>(1, p.n_coeffs);
     cudaError_t e = cudaSuccess;
     auto A = [&](void **ptr, size_t b) {
-        if (e == cudaSuccess) e = cudaMalloc(ptr, b);
+        if (e == cudaSuccess) e = plan_malloc(ptr, b);
     };
     A((void **)&W->uM, bm);
     A((void **)&W->tM, bm);

@@ -66,7 +66,10 @@ __device__ inline void lsqr_init_dev(SolverState *st) {
     st->iters = 0;
     st->stop = 0;
     st->status = 0;
-    if (st->alpha == 0.0 || st->beta == 0.0) {
+    if (!isfinite(st->alpha) || !isfinite(st->beta)) {   // non-finite data (NaN or Inf in y)
+        st->status = ANOVA_ERR_NOT_FINITE;
+        st->done = 1;
+    } else if (st->alpha == 0.0 || st->beta == 0.0) {
         st->done = 1;
         st->stop = 1;
     }
@@ -84,6 +87,11 @@ __device__ inline void lsqr_scalars_dev(SolverState *st) {
     const double psi = s1 * st->phibar;
     const double phibar1 = c1 * st->phibar;
     const double rho = hypot(rhohat, beta);
+    if (!isfinite(rho) || !isfinite(alpha)) {
+        st->status = ANOVA_ERR_NOT_FINITE;
+        st->done = 1;
+        return;
+    }
     if (!(rho > 0)) {   // alpha = beta = 0: the Krylov space is exhausted
         st->stop = 1;
         st->done = 1;

@@ -179,7 +179,7 @@ int sort_nodes_by_cell(Plan &p) {
             max_bins = std::max(max_bins, T.order == 3 ? T.n * T.n * T.n : (T.order == 2 ? T.n * T.n : T.n));
     }
     int *counts = nullptr;
-    cudaError_t e = cudaMalloc(&counts, sizeof(int) * (size_t)p.n_sorted * max_bins);
+    cudaError_t e = plan_malloc(&counts, sizeof(int) * (size_t)p.n_sorted * max_bins);
     if (e != cudaSuccess) return cuda_status(e);
     const size_t hist_bytes = sizeof(int) * (size_t)max_bins;
     const bool f64 = p.precision == ANOVA_PREC_F64;

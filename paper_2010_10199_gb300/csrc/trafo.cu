@@ -196,13 +196,12 @@ int launch_trafo_f32(Plan &p, const float2 *fhat, float2 *f) {
         return cuda_status(cudaGetLastError());
     }
     size_t pre_smem = (size_t)p.max_fft_elems * 2 * sizeof(float2);
-    static bool attr_done = false;
-    if (!attr_done) {
+    static std::atomic<unsigned long long> attr_seen{0};
+    once_per_device(attr_seen, [] {
         cudaFuncSetAttribute(trafo_pre_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(trafo_pre_f16, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(trafo_pre_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_done = true;
-    }
+    });
     stage_begin(p, ST_PRE);
     BatchArgs B;
     std::memset(&B, 0, sizeof(B));

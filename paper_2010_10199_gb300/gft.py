@@ -152,6 +152,8 @@ def load(path: str | None = None):
     lib.anova_kkt_check.restype = ctypes.c_int
     lib.grouped_trafo_noalloc.argtypes = [ctypes.c_int, ctypes.c_int64, vp, ctypes.c_int, i32p, i32p, vp, vp, vp]
     lib.grouped_trafo_noalloc.restype = ctypes.c_int
+    lib.anova_debug_fail_allocation.argtypes = [ctypes.c_int]
+    lib.anova_debug_fail_allocation.restype = ctypes.c_int
     lib.anova_status_string.argtypes = [ctypes.c_int]
     lib.anova_status_string.restype = ctypes.c_char_p
     lib.anova_version.argtypes = []
@@ -311,6 +313,11 @@ def anova_profile_read(h, reset: bool = False) -> dict:
     ns = ctypes.c_int()
     _check("anova_profile_read", load().anova_profile_read(h, ms, cnt, names, n, ctypes.byref(ns), 1 if reset else 0))
     return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(min(ns.value, n))}
+
+
+def anova_debug_fail_allocation(k: int):
+    """Make the k-th following plan allocation fail (test fault injection; 0 cancels)."""
+    return _check("anova_debug_fail_allocation", load().anova_debug_fail_allocation(int(k)))
 
 
 def anova_status_string(status: int) -> str:

@@ -49,6 +49,26 @@ def test_lsqr_c1_fixed_iterations(gft):
     assert abs(info["rnorm"] - ref.rnorm) <= 1e-4 * ref.rnorm   # sqrt(||r||^2 + 2 lam ||f||^2) estimate
 
 
+def test_lsqr_third_order_workload_shape(gft):
+    """LSQR on the shape of the d = 10, |u| <= 3 workload (176 terms, N =
+    100 / 24x24 / 10x10x10, 112 276 unknowns, Beta(2,2) nodes) at 3000 nodes:
+    a fixed iteration count against the oracle's LSQR on the direct FP64 sums."""
+    w = inputs.c3_lsqr(M=3000)
+    x, terms, bw, y = w["x"], w["terms"], w["bandwidths"], w["y"]
+    n = anova.n_coeffs(terms, bw)
+    assert n == 112276
+    xo = f32_nodes(x)
+    F = lambda f: ndft.trafo(xo, terms, bw, f)
+    FH = lambda r: ndft.adjoint(xo, terms, bw, r)
+    lam, iters = 0.1, 20
+    ref = solvers.tikhonov_lsqr(F, FH, y, n, lam, None, iters=iters)
+    P = _plan(gft, x, terms, bw)
+    fh, info, rc = P.lsqr(cplx_dev(y), lam, max_it=iters)
+    assert rc == 0 and info["iterations"] == iters
+    assert rel_l2(host(fh), ref.x) <= TOL
+    assert abs(info["rnorm"] - ref.rnorm) <= 1e-4 * ref.rnorm
+
+
 def test_lsqr_converged_matches_normal_equations(gft):
     w = inputs.c1_small()
     x, terms, bw, y = w["x"], w["terms"], w["bandwidths"], w["y"]

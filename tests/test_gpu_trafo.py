@@ -34,6 +34,10 @@ def _plan(gft, x, terms, bw, **kw):
 
 
 def _pair_check(gft, x, terms, bw, fhat=None, y=None, tol=TOL, seed=1, **plan_kw):
+    """Forward and adjoint against the oracle: the whole vectors, every
+    coefficient block of the adjoint on its own, and the forward of each order
+    class of terms on its own (the other blocks zero), so that an error
+    confined to a few terms cannot hide in a whole-vector norm."""
     xo = f32_nodes(x)
     n = anova.n_coeffs(terms, bw)
     M = x.shape[1]
@@ -48,6 +52,24 @@ def _pair_check(gft, x, terms, bw, fhat=None, y=None, tol=TOL, seed=1, **plan_kw
     ef, eg = rel_l2(f, f_ref), rel_l2(g, g_ref)
     assert ef <= tol, f"forward rel l2 {ef:.3e}"
     assert eg <= tol, f"adjoint rel l2 {eg:.3e}"
+    if M == 0:
+        return ef, eg
+    offs, lens = anova.layout(terms, bw)
+    worst = max(((rel_l2(g[o:o + ln], g_ref[o:o + ln]), u) for u, (o, ln) in enumerate(zip(offs, lens))
+                 if np.any(g_ref[o:o + ln] != 0)), default=(0.0, None))
+    assert worst[0] <= tol, f"adjoint block of term {terms[worst[1]]}: rel l2 {worst[0]:.3e}"
+    orders = sorted({len(u) for u in terms})
+    if len(orders) > 1:
+        for s in orders:
+            part = np.zeros_like(fhat)
+            for u, (o, ln) in enumerate(zip(offs, lens)):
+                if len(terms[u]) == s:
+                    part[o:o + ln] = fhat[o:o + ln]
+            if not np.any(part != 0):
+                continue
+            fs = host(P.trafo(cplx_dev(part)))
+            es = rel_l2(fs, ndft.trafo(xo, terms, bw, part))
+            assert es <= tol, f"forward of the order-{s} terms alone: rel l2 {es:.3e}"
     return ef, eg
 
 
@@ -205,7 +227,8 @@ def test_forward_is_deterministic(gft):
 @pytest.mark.slow
 def test_c2_full_size_sampled(gft):
     """The benchmark workload (M = 1e6, d = 20, 211 terms): forward on 2000
-    sampled nodes and adjoint on three sampled blocks against the oracle, plus
+    sampled nodes and the adjoint blocks of all 20 first-order terms and ten
+    second-order terms against the oracle, each block on its own, plus
     adjointness of the GPU pair over the whole vector."""
     import torch
     w = inputs.c2_scale()
@@ -220,9 +243,14 @@ def test_c2_full_size_sampled(gft):
     f_ref = ndft.trafo(xo[:, idx], terms, bw, w["fhat"])
     assert rel_l2(f[idx], f_ref) <= TOL
     offs, lens = anova.layout(terms, bw)
-    for u in (1, 20, 150):
-        ref = ndft.adjoint(xo, [terms[u]], [bw[u]], w["y"])
-        assert rel_l2(g[offs[u]:offs[u] + lens[u]], ref) <= TOL, f"term {terms[u]}"
+    # every first-order block and ten second-order blocks spread over the schedule
+    blocks = list(range(1, 21)) + list(range(21, len(terms), 19))
+    ref = ndft.adjoint(xo, [terms[u] for u in blocks], [bw[u] for u in blocks], w["y"])
+    pos = 0
+    for u in blocks:
+        ln = lens[u]
+        assert rel_l2(g[offs[u]:offs[u] + ln], ref[pos:pos + ln]) <= TOL, f"term {terms[u]}"
+        pos += ln
     lhs = np.vdot(w["y"], f)
     rhs = np.vdot(g, w["fhat"])
     assert abs(lhs - rhs) / abs(lhs) <= 1e-5
