@@ -159,10 +159,10 @@ def pairs_config(args) -> dict:
             "parallelism": f"replicas x{args.gpus}"}
 
 
-def pairs_method(args) -> dict:
+def pairs_method(args, m_row: int) -> dict:
     """How this library computes the pairs (the GPU arm only)."""
     return {"precision": "fp64 throughout" if args.precision == "f64" else "fp32 grids and accumulation",
-            "window": "Kaiser-Bessel, sigma=2, 6 row x 8 column taps",
+            "window": f"Kaiser-Bessel, sigma=2, {2 * m_row} row x 8 column taps",
             "cell_products": "CUDA cores" if args.cell_kernel else "tensor cores (TF32 split, 3 products)"}
 
 
@@ -313,7 +313,9 @@ def run_mine(args, rank, world, local_rank):
     sms, sl = prof.get("spread", (0.0, 0))
     M, d = args.M, 20
     n_terms2, n_terms1 = 190, 20
-    grid_bytes = 8 * (n_terms2 * 69 * 72 + n_terms1 * 136)
+    m_row = max(P.term_grid(u)[2] for u in range(len(w["terms"])))   # the plan's row half-width
+    # stored grids: order 2 (n + 2 (m_row - 1) + 1) rows of pitch 72, order 1 one row of 136 (n = 64 / 128)
+    grid_bytes = 8 * (n_terms2 * (64 + 2 * (m_row - 1) + 1) * 72 + n_terms1 * 136)
     rs = 8 if f64 else 4
     grid_bytes = grid_bytes * esz // 8
     if gms / max(gl, 1) >= sms / max(sl, 1):
@@ -342,7 +344,6 @@ def run_mine(args, rank, world, local_rank):
     # polynomials (8 column and 2 m_row row taps, degree 7: 7 FMA each by
     # Horner) and the tensor product of the window with y or the grid (2 m_row
     # x 8 taps: the weight product and a complex multiply-add, 3 operations).
-    m_row = 3
     ops2 = (8 + 2 * m_row) * 7 + 2 * m_row * 8 * 3
     ops1 = 8 * 7 + 8 * 2
     alg_flops = 2.0 * M * (n_terms2 * ops2 + n_terms1 * ops1)
@@ -383,7 +384,7 @@ def run_mine(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
                 "data": "synthetic (seeded SplitMix64)",
-                "config": pairs_config(args), "method": pairs_method(args),
+                "config": pairs_config(args), "method": pairs_method(args, m_row),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
                 # algorithmic (node, non-empty term) pairs of both transforms per second, all ranks

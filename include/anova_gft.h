@@ -77,7 +77,8 @@ typedef struct {
     int precision;      /* enum anova_precision */
     double eps;         /* target relative l2 error of F and F^H (0: default for the precision) */
     int window_m_col;   /* window half-width along the fastest grid axis (0: auto) */
-    int window_m_row;   /* window half-width along the other axes (0: auto) */
+    int window_m_row;   /* window half-width along the other axes (0: auto: 4 for eps below
+                           5e-5, which holds every term's block within 1e-5 in FP32; else 3) */
     double sigma;       /* minimal oversampling factor n_u / N_u (0: 2.0) */
     int n_ctas;         /* adjoint: most node chunks (partial grids) per term, <= 64 (0: auto) */
     int node_sort;      /* adjoint: 0 = keep a copy of the nodes sorted by grid cell for every
@@ -224,6 +225,37 @@ int fista_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, const
 int anova_kkt_check(anova_plan_t plan, const void *y_dev, const double *w_dev, const void *fhat_dev,
                     double lambda, double rtol, double *viol_out, int *n_viol);
 
+/*
+ * anova_sobol_indices -- global sensitivity (Sobol) indices of the partial sum
+ * S f = sum_u sum_{k in I_u} fhat_k exp(2 pi i <k, x>) (eq. (gsi), Sec. 2):
+ * rho(u) = sigma^2(f_u) / sigma^2(f) with sigma^2(f_u) = ||fhat_u||^2 (the
+ * blocks are orthogonal on the torus: Parseval) and sigma^2(f) = ||f||^2 -
+ * |c_0|^2, the sum over the non-empty terms; rho(empty set) = 0 (and every
+ * rho is 0 when all non-empty blocks vanish).  With thresholds it also returns
+ * the active set of eq. (activeset), Sec. 4:
+ * U* = {empty set} u {u : rho(u) > eps_|u|} (strict inequality).
+ *   fhat_dev     : [num_coeffs] complex (plan's vector type)
+ *   rho_out      : host [n_terms] (required), in the user's term order
+ *   eps_by_order : host [3] thresholds eps_1, eps_2, eps_3 >= 0, or NULL
+ *   active_out   : host [n_terms], 1 for u in U* (required with eps_by_order)
+ * Block energies and their total are FP64 sums in a fixed order on the device.
+ * Synchronises the plan's stream.
+ */
+int anova_sobol_indices(anova_plan_t plan, const void *fhat_dev, double *rho_out, const double *eps_by_order,
+                        uint8_t *active_out);
+
+/*
+ * anova_l2_error -- relative L2 error of eq. (L2error), Sec. 4, of the partial
+ * sum with coefficients fhat against a function f whose Fourier coefficients
+ * c on I_N(U) and squared norm ||f||^2 are known, through Parseval's identity:
+ *   err = sqrt(max(0, ||f||^2 + sum_I |fhat_k - c_k|^2 - sum_I |c_k|^2) / ||f||^2).
+ *   fhat_dev, c_dev : [num_coeffs] complex (plan's vector type)
+ *   norm2           : ||f||^2 > 0
+ *   err_out         : host
+ * FP64 sums in a fixed order on the device; synchronises the plan's stream.
+ */
+int anova_l2_error(anova_plan_t plan, const void *fhat_dev, const void *c_dev, double norm2, double *err_out);
+
 /* ------------------------------------------------------------------------
  * Many independent problems in one launch per kernel.  A batch holds one
  * plan per problem (same options); its vectors are the concatenation of the
@@ -327,8 +359,9 @@ int anova_profile_read(anova_plan_t plan, double *ms, int64_t *launches, const c
  * oversampling grows, Sec. 3 after eq. (somafm); its cost rises with both).
  * A reference plan (sigma 2.5, 8 x 8 taps) transforms two fixed pseudo-random
  * vectors; every candidate plan transforms the same vectors, its estimated
- * error is max(rel. l2 distance of F fhat, of F^H y) to the reference, and its
- * time is the mean of `reps` timed pairs after one warm-up pair on `stream`.
+ * error is the largest relative l2 distance to the reference of F fhat, of
+ * F^H y and of each coefficient block of F^H y on its own, and its time is
+ * the mean of `reps` timed pairs after one warm-up pair on `stream`.
  * Candidates: sigma in {1.75, 2, 2.5} x row half-width in {3, 4}; then, around
  * the fastest one within eps_target, node chunks per term (n_ctas) in
  * {4, 16, 64}, the original node order (node_sort = -1) and the CUDA-core

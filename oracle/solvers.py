@@ -18,7 +18,8 @@ the algorithm as written, on exact (FP64) matrix-vector products.
 * KKT                stationarity x - y + lam W x / ||x||_W = 0 from the proof of
                      Lemma (ii), and the zero threshold of Lemma (iii)
 * Sobol index        rho(u) = sigma^2(f_u) / sigma^2(f), eq. (gsi), via Parseval on
-                     the coefficient blocks
+                     the coefficient blocks; the active set of eq. (activeset)
+* L2 error           eq. (L2error) through Parseval's identity
 """
 from __future__ import annotations
 
@@ -379,6 +380,16 @@ def sobol_indices(f: np.ndarray, offs, lens) -> np.ndarray:
     if total > 0:
         rho[1:] = e[1:] / total
     return rho
+
+
+def l2_error(fhat: np.ndarray, c: np.ndarray, norm2: float) -> float:
+    """Relative L2 error of eq. (L2error) through Parseval's identity:
+    ||f - S f||^2 = ||f||^2 + sum_{k in I} |fhat_k - c_k|^2 - sum_{k in I} |c_k|^2,
+    with c_k the exact coefficients of f on I and norm2 = ||f||^2; returns
+    ||f - S f|| / ||f||."""
+    d = np.asarray(fhat, dtype=np.complex128) - np.asarray(c, dtype=np.complex128)
+    e2 = norm2 + float(np.sum(d.real ** 2 + d.imag ** 2)) - float(np.sum(np.abs(c) ** 2))
+    return math.sqrt(max(e2, 0.0) / norm2)
 
 
 def active_set(rho: np.ndarray, terms, eps_by_order) -> list:

@@ -53,13 +53,38 @@ __global__ void k_tune_diff(const float2 *a, const float2 *b, long long n, doubl
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
+// per coefficient block u: partial sums of |a - b|^2 and |b|^2 (one block per term)
+__global__ void k_tune_block_diff(const float2 *a, const float2 *b, const long long *off, const long long *len,
+                                  double2 *out) {
+    __shared__ double2 sh[256];
+    const long long o = off[blockIdx.x], m = len[blockIdx.x];
+    double d2 = 0.0, b2 = 0.0;
+    for (long long i = threadIdx.x; i < m; i += blockDim.x) {
+        const float2 u = a[o + i], v = b[o + i];
+        const double dx = (double)u.x - v.x, dy = (double)u.y - v.y;
+        d2 += dx * dx + dy * dy;
+        b2 += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    sh[threadIdx.x] = make_double2(d2, b2);
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sh[threadIdx.x].x += sh[threadIdx.x + s].x;
+            sh[threadIdx.x].y += sh[threadIdx.x + s].y;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
 namespace {
 
 struct TuneBuffers {
     float2 *fhat = nullptr, *y = nullptr, *f = nullptr, *g = nullptr, *f_ref = nullptr, *g_ref = nullptr;
-    double2 *part = nullptr;
+    double2 *part = nullptr, *bpart = nullptr;
+    long long *boff = nullptr, *blen = nullptr;
     ~TuneBuffers() {
-        void *b[] = {fhat, y, f, g, f_ref, g_ref, part};
+        void *b[] = {fhat, y, f, g, f_ref, g_ref, part, bpart, boff, blen};
         for (void *q : b)
             if (q) cudaFree(q);
     }
@@ -79,6 +104,21 @@ double rel_diff(const float2 *a, const float2 *b, long long n, double2 *part, cu
         b2 += v.y;
     }
     return std::sqrt(d2 / std::max(b2, 1e-300));
+}
+
+// the largest relative l2 distance over the coefficient blocks (blocks whose
+// reference is zero are skipped)
+double worst_block(const float2 *a, const float2 *b, const long long *off, const long long *len, int G,
+                   double2 *out, cudaStream_t st) {
+    if (G == 0) return 0.0;
+    k_tune_block_diff<<<G, 256, 0, st>>>(a, b, off, len, out);
+    std::vector<double2> h(G);
+    cudaMemcpyAsync(h.data(), out, sizeof(double2) * G, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return INFINITY;
+    double w = 0.0;
+    for (const double2 &v : h)
+        if (v.y > 0) w = std::max(w, std::sqrt(v.x / v.y));
+    return w;
 }
 
 }  // namespace
@@ -120,6 +160,22 @@ int anova_plan_autotune(anova_plan_options *opts, int d, int64_t M, const void *
     A((void **)&T.f, sizeof(float2) * M);
     A((void **)&T.f_ref, sizeof(float2) * M);
     A((void **)&T.part, sizeof(double2) * TUNE_BLOCKS);
+    A((void **)&T.bpart, sizeof(double2) * n_terms);
+    A((void **)&T.boff, sizeof(long long) * n_terms);
+    A((void **)&T.blen, sizeof(long long) * n_terms);
+    if (e == cudaSuccess) {
+        std::vector<long long> ho(n_terms), hl(n_terms);
+        for (int u = 0; u < n_terms; ++u) {
+            int64_t o = 0, l = 0;
+            anova_term_offset(ref, u, &o, &l);
+            ho[u] = o;
+            hl[u] = l;
+        }
+        e = cudaMemcpyAsync(T.boff, ho.data(), sizeof(long long) * n_terms, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(T.blen, hl.data(), sizeof(long long) * n_terms, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
     if (e != cudaSuccess) {
         anova_plan_destroy(ref);
         return cuda_status(e);
@@ -156,7 +212,8 @@ int anova_plan_autotune(anova_plan_options *opts, int d, int64_t M, const void *
         if (!r) {
             const double ef = rel_diff(T.f, T.f_ref, M, T.part, st);
             const double eg = rel_diff(T.g, T.g_ref, n, T.part, st);
-            c.err = std::max(ef, eg);
+            const double eb = worst_block(T.g, T.g_ref, T.boff, T.blen, n_terms, T.bpart, st);
+            c.err = std::max(ef, std::max(eg, eb));
             cudaEventRecord(e0, st);
             for (int i = 0; i < reps && !r; ++i) {
                 r = grouped_trafo(p, T.fhat, T.f);

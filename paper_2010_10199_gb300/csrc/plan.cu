@@ -338,7 +338,10 @@ static int plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, i
     if (p.sm_count <= 0) p.sm_count = 152;
 
     int mc = o.window_m_col > 0 ? o.window_m_col : 4;
-    int mr = o.window_m_row > 0 ? o.window_m_row : (o.eps >= 5e-6 ? 3 : 4);
+    // 6 row taps (m_row = 3) keep the whole-vector error near 5e-6 but leave
+    // single terms (third-order ones, or any term sampled at few nodes) above
+    // 1e-5; 8 taps hold every term near 3e-6
+    int mr = o.window_m_row > 0 ? o.window_m_row : (o.eps >= 5e-5 ? 3 : 4);
     if (mc != 4) {   // eight column lanes per row segment
         return ANOVA_ERR_UNSUPPORTED;
     }

@@ -28,7 +28,7 @@ namespace agft {
 static void free_work(SolverWork *W) {
     if (!W) return;
     void *b[] = {W->uM, W->tM, W->rM, W->v, W->w, W->x, W->tn, W->h, W->f, W->fp, W->g, W->ws, W->wd,
-                 W->part, W->gnorm, W->goff, W->glen, W->gmask, W->st};
+                 W->part, W->gnorm, W->goff, W->glen, W->gmask, W->grho, W->gact, W->gorder, W->st};
     for (void *q : b)
         if (q) cudaFree(q);
     if (W->e0) cudaEventDestroy(W->e0);
@@ -123,6 +123,9 @@ SolverWork *get_work(Plan &p, int &rc) {
     A((void **)&W->goff, sizeof(long long) * std::max(1, p.n_user_terms));
     A((void **)&W->glen, sizeof(long long) * std::max(1, p.n_user_terms));
     A((void **)&W->gmask, std::max(1, p.n_user_terms));
+    A((void **)&W->grho, sizeof(double) * std::max(1, p.n_user_terms));
+    A((void **)&W->gact, std::max(1, p.n_user_terms));
+    A((void **)&W->gorder, sizeof(int) * std::max(1, p.n_user_terms));
     A((void **)&W->st, sizeof(SolverState));
     if (e == cudaSuccess) e = cudaEventCreate(&W->e0);
     if (e == cudaSuccess) e = cudaEventCreate(&W->e1);
@@ -132,6 +135,8 @@ SolverWork *get_work(Plan &p, int &rc) {
         e = cudaMemcpyAsync(W->goff, p.h_user_off, sizeof(long long) * p.n_user_terms, cudaMemcpyHostToDevice, p.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(W->glen, p.h_user_len, sizeof(long long) * p.n_user_terms, cudaMemcpyHostToDevice, p.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(W->gorder, p.h_user_order, sizeof(int) * p.n_user_terms, cudaMemcpyHostToDevice, p.stream);
     if (e != cudaSuccess) {
         free_work(W);
         cudaGetLastError();

@@ -33,6 +33,9 @@ struct SolverWork {
     double *gnorm = nullptr;      // per-group values
     long long *goff = nullptr, *glen = nullptr;
     unsigned char *gmask = nullptr;
+    double *grho = nullptr;        // per-group Sobol indices (analysis.cu)
+    unsigned char *gact = nullptr; // and the active-set flags
+    int *gorder = nullptr;         // |u| per user term
     SolverState *st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr, join = nullptr;
     cudaStream_t stream = nullptr;   // own non-blocking stream: graph capture needs one

@@ -152,6 +152,11 @@ def load(path: str | None = None):
     lib.anova_kkt_check.restype = ctypes.c_int
     lib.grouped_trafo_noalloc.argtypes = [ctypes.c_int, ctypes.c_int64, vp, ctypes.c_int, i32p, i32p, vp, vp, vp]
     lib.grouped_trafo_noalloc.restype = ctypes.c_int
+    lib.anova_sobol_indices.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_uint8)]
+    lib.anova_sobol_indices.restype = ctypes.c_int
+    lib.anova_l2_error.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.anova_l2_error.restype = ctypes.c_int
     lib.anova_debug_fail_allocation.argtypes = [ctypes.c_int]
     lib.anova_debug_fail_allocation.restype = ctypes.c_int
     lib.anova_status_string.argtypes = [ctypes.c_int]
@@ -315,6 +320,25 @@ def anova_profile_read(h, reset: bool = False) -> dict:
     return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(min(ns.value, n))}
 
 
+def anova_sobol_indices(h, fhat_ptr, n_terms, eps_by_order=None):
+    """Sobol indices rho(u) (eq. (gsi)) of a coefficient vector and, with
+    thresholds (eps_1, eps_2, eps_3), the active-set flags of eq. (activeset)."""
+    rho = (ctypes.c_double * max(1, n_terms))()
+    eps = (ctypes.c_double * 3)(*[float(v) for v in eps_by_order]) if eps_by_order is not None else None
+    act = (ctypes.c_uint8 * max(1, n_terms))() if eps_by_order is not None else None
+    _check("anova_sobol_indices", load().anova_sobol_indices(h, ctypes.c_void_p(int(fhat_ptr) or None), rho, eps, act))
+    return [rho[i] for i in range(n_terms)], (None if act is None else [bool(act[i]) for i in range(n_terms)])
+
+
+def anova_l2_error(h, fhat_ptr, c_ptr, norm2):
+    """Relative L2 error of eq. (L2error) through Parseval's identity."""
+    err = ctypes.c_double()
+    _check("anova_l2_error", load().anova_l2_error(h, ctypes.c_void_p(int(fhat_ptr) or None),
+                                                   ctypes.c_void_p(int(c_ptr) or None), float(norm2),
+                                                   ctypes.byref(err)))
+    return err.value
+
+
 def anova_debug_fail_allocation(k: int):
     """Make the k-th following plan allocation fail (test fault injection; 0 cancels)."""
     return _check("anova_debug_fail_allocation", load().anova_debug_fail_allocation(int(k)))
@@ -422,6 +446,17 @@ class Plan:
         self._vec(fhat, self.n_coeffs, "fhat")
         return anova_kkt_check(self.handle, y.data_ptr(), self._weights(w), fhat.data_ptr(), lam, rtol,
                                len(self.terms))
+
+    def sobol(self, fhat, eps_by_order=None):
+        """Sobol indices of the blocks of fhat (and the active-set flags with thresholds)."""
+        self._vec(fhat, self.n_coeffs, "fhat")
+        return anova_sobol_indices(self.handle, fhat.data_ptr(), len(self.terms), eps_by_order)
+
+    def l2_error(self, fhat, c, norm2):
+        """Relative L2 error of eq. (L2error) for exact coefficients c on this plan's index set."""
+        self._vec(fhat, self.n_coeffs, "fhat")
+        self._vec(c, self.n_coeffs, "c")
+        return anova_l2_error(self.handle, fhat.data_ptr(), c.data_ptr(), norm2)
 
     def profile(self, on: bool = True):
         anova_profile_enable(self.handle, on)

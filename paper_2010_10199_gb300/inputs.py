@@ -258,3 +258,113 @@ def subsample(work: dict, m: int, seed: int = 12345) -> np.ndarray:
     u = uniform(seed, S_META + 7, m)
     idx = np.unique((u * M).astype(np.int64))
     return idx
+
+
+# --------------------------------------------------------------------------
+# the paper's test function (Sec. 4, eq. (testfun)), d = 9:
+#   f(x) = B2(x1) B4(x3) B6(x8) + B2(x2) B4(x5) B6(x6) + B2(x4) B4(x7) B6(x9)
+# with B_j(x) = c_j sum_k sinc^j(pi k / j) cos(pi k) exp(2 pi i k x).  That
+# series is c_j times the periodised B-spline j M_j(j x) on [0, 1) (M_j the
+# cardinal B-spline of order j on [0, j], whose Fourier transform is
+# exp(-i w j / 2) sinc^j(w / 2)), which is how f is evaluated here.  This is
+# data: the sampled values y and, for the error measure of eq. (L2error), the
+# exact coefficients on a grouped index set.
+# --------------------------------------------------------------------------
+
+BSPLINE_C = {2: math.sqrt(3.0 / 4.0), 4: math.sqrt(315.0 / 604.0), 6: math.sqrt(277200.0 / 655177.0)}
+# the three coordinate triples of the test function, 0-based ({1,3,8}, {2,5,6},
+# {4,7,9} in the paper), each listed as (B2 coordinate, B4 coordinate, B6 coordinate)
+BSPLINE_TRIPLES = ((0, 2, 7), (1, 4, 5), (3, 6, 8))
+BSPLINE_ORDER = {c: j for t in BSPLINE_TRIPLES for c, j in zip(t, (2, 4, 6))}
+
+
+def cardinal_bspline(j: int, t: np.ndarray) -> np.ndarray:
+    """M_j(t) = 1/(j-1)! sum_{i=0}^{j} (-1)^i C(j, i) (t - i)_+^{j-1}, supported on [0, j]."""
+    t = np.asarray(t, dtype=np.float64)
+    s = np.zeros_like(t)
+    for i in range(j + 1):
+        s += (-1) ** i * math.comb(j, i) * np.maximum(t - i, 0.0) ** (j - 1)
+    s /= math.factorial(j - 1)
+    return np.where((t >= 0) & (t <= j), s, 0.0)
+
+
+def bspline_B(j: int, x: np.ndarray) -> np.ndarray:
+    """B_j of the test function at x on the torus (any real x)."""
+    u = np.mod(np.asarray(x, dtype=np.float64), 1.0)
+    return BSPLINE_C[j] * j * cardinal_bspline(j, j * u)
+
+
+def bspline_function(x: np.ndarray) -> np.ndarray:
+    """The test function of eq. (testfun) at nodes x [9][M]."""
+    f = np.zeros(x.shape[1])
+    for t in BSPLINE_TRIPLES:
+        f += bspline_B(2, x[t[0]]) * bspline_B(4, x[t[1]]) * bspline_B(6, x[t[2]])
+    return f
+
+
+def bspline_coefficient_1d(j: int, k: np.ndarray) -> np.ndarray:
+    """c_j sinc^j(pi k / j) cos(pi k): the k-th Fourier coefficient of B_j."""
+    k = np.asarray(k, dtype=np.float64)
+    a = np.pi * k / j
+    sinc = np.where(k == 0, 1.0, np.sin(a) / np.where(k == 0, 1.0, a))
+    return BSPLINE_C[j] * sinc ** j * np.cos(np.pi * k)
+
+
+def bspline_coefficients(terms, bandwidths) -> np.ndarray:
+    """Exact Fourier coefficients c_k(f) of the test function on I_N(U), in the
+    block layout (term order; inside a block row-major over the term's sorted
+    coordinates, last fastest, each coordinate -N/2..N/2-1 without 0).  A
+    frequency with support u gets the sum over the triples T containing u of
+    prod_{i in u} c_{o(i)}(k_i) prod_{i in T minus u} c_{o(i)}."""
+    out = []
+    for u, N in zip(terms, bandwidths):
+        s = len(u)
+        if s == 0:
+            out.append(np.array([sum(BSPLINE_C[2] * BSPLINE_C[4] * BSPLINE_C[6] for _ in BSPLINE_TRIPLES)]))
+            continue
+        k1 = np.array([k for k in range(-N // 2, N // 2) if k != 0], dtype=np.float64)
+        block = np.zeros((N - 1) ** s)
+        for t in BSPLINE_TRIPLES:
+            if not set(u) <= set(t):
+                continue
+            const = 1.0
+            for c in t:
+                if c not in u:
+                    const *= BSPLINE_C[BSPLINE_ORDER[c]]
+            grids = np.meshgrid(*[bspline_coefficient_1d(BSPLINE_ORDER[c], k1) for c in u], indexing="ij")
+            prod = np.ones_like(grids[0])
+            for g in grids:
+                prod = prod * g
+            block += const * prod.reshape(-1)
+        out.append(block)
+    return np.concatenate(out).astype(np.complex128)
+
+
+def bspline_norm2() -> float:
+    """||f||^2 = 3 + 6 (c_2 c_4 c_6)^2 (each triple has norm 1; two different
+    triples share no coordinate, so their inner product is the product of
+    their means)."""
+    p = BSPLINE_C[2] * BSPLINE_C[4] * BSPLINE_C[6]
+    return 3.0 + 6.0 * p * p
+
+
+# bandwidths of the LSQR and FISTA experiments (i)/(ii) and (iii)/(iv):
+# eq. (smallbandwidths) and eq. (largebandwidths)
+BSPLINE_SMALL_N = {1: 26, 2: 6, 3: 4}
+BSPLINE_LARGE_N = {1: 352, 2: 20, 3: 8}
+
+
+def bspline_workload(seed: int = 0, M: int = 10_000, bandwidths=None, noise: float = 0.0) -> dict:
+    """The experiments of Sec. 4: M i.i.d. uniform nodes on the torus (here
+    [-1/2, 1/2)^9), y = f(x) + noise * sqrt(mean f(x)^2) * N(0, 1), all terms
+    with |u| <= 3 and the small bandwidths of eq. (smallbandwidths) unless
+    others are given; also the exact coefficients on I_N(U_3) and ||f||^2."""
+    d = 9
+    by_order = BSPLINE_SMALL_N if bandwidths is None else bandwidths
+    terms = terms_up_to(d, 3)
+    bw = bandwidths_by_order(terms, by_order)
+    x = uniform_points(seed, d, M)
+    fx = bspline_function(x)
+    y = fx + noise * math.sqrt(float(np.mean(fx ** 2))) * normal(seed, S_NOISE, M)
+    return dict(name="bspline", d=d, M=M, terms=terms, bandwidths=bw, x=x, y=y.astype(np.complex128),
+                c=bspline_coefficients(terms, bw), norm2=bspline_norm2(), noise=noise)

@@ -128,13 +128,13 @@ def test_long_cell_runs(gft, path):
 @pytest.mark.parametrize("path", ["tensor", "cuda"])
 def test_sparse_cells_and_wide_window(gft, path):
     """Fewer nodes than cells (almost every group of 8 holds 8 cells) and the
-    8 x 8-tap window (eps below 5e-6: m_row = 4, all 8 row taps of the
+    8 x 8-tap window (m_row = 4, the default below eps 5e-5; all 8 row taps of the
     tensor-core tile in use)."""
     x = inputs.uniform_points(19, 3, 777)
     terms = anova.term_set(3, 2)
     bw = [0] + [64] * 3 + [48] * 3
     _pair_check(gft, x, terms, bw, **SPREAD_PATHS[path])
-    _pair_check(gft, x, terms, bw, eps=1e-6, tol=3e-6, **SPREAD_PATHS[path])
+    _pair_check(gft, x, terms, bw, eps=1e-6, tol=5e-6, **SPREAD_PATHS[path])
 
 
 def test_c2_subsample_all_terms(gft):
@@ -159,12 +159,12 @@ def test_third_order_terms(gft, path):
 def test_third_order_dense_cells_and_wide_window(gft, path):
     """A third-order term with hundreds of nodes per cell (long cell runs over
     several steps), a ragged node count, and the 8 x 8 x 8-tap window
-    (eps below 5e-6: m_row = 4)."""
+    (m_row = 4, the default below eps 5e-5)."""
     x = inputs.uniform_points(21, 3, 100003)
     terms = [(), (0,), (1,), (2,), (0, 1, 2)]
     bw = [0, 8, 8, 8, 4]
     _pair_check(gft, x, terms, bw, **SPREAD_PATHS[path])
-    _pair_check(gft, x, terms, bw, eps=1e-6, tol=3e-6, **SPREAD_PATHS[path])
+    _pair_check(gft, x, terms, bw, eps=1e-6, tol=5e-6, **SPREAD_PATHS[path])
 
 
 def test_mixed_bandwidths_and_orders(gft):
