@@ -80,7 +80,7 @@ def parse():
     if a.M <= 0:
         a.M = {"pairs": 1_000_000, "lambda-path": 2_000_000, "lsqr-path": 500_000}.get(a.mode, 1_000_000)
     if a.mode == "lsqr-path" and a.max_it == 5000:
-        a.max_it = 300
+        a.max_it = 200
     return a
 
 
@@ -645,7 +645,7 @@ def run_lsqr_path(args, local_rank):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for lam in w["lambdas"]:
-        fh, info, rc = P.lsqr(y, float(lam), max_it=args.max_it, atol=1e-6, btol=1e-6)
+        fh, info, rc = P.lsqr(y, float(lam), max_it=args.max_it, atol=1e-10, btol=1e-10)
         per.append({"lambda": float(lam), "iterations": info["iterations"], "seconds": info["seconds"],
                     "stop_reason": ["max_it", "breakdown", "residual test", "normal-equation test"][
                         info["stop_reason"]],
@@ -657,7 +657,7 @@ def run_lsqr_path(args, local_rank):
             "higher_is_better": False, "n_gpus": 1, "dtype": "f32 vectors, f64 scalars",
             "data": "synthetic (seeded SplitMix64)",
             "config": {"workload": f"d=10, |u|<=3 (176 terms), N=100 / 24x24 / 10x10x10, M={args.M} Beta(2,2) nodes",
-                       "lsqr": f"atol = btol = 1e-6, at most {args.max_it} iterations per lambda, graph-replayed"},
+                       "lsqr": f"atol = btol = 1e-10, at most {args.max_it} iterations per lambda, graph-replayed"},
             "results": {"iterations": its, "ms_per_iteration": 1e3 * total / max(its, 1),
                         "converged_lambdas": sum(q["stop_reason"] != "max_it" for q in per), "per_lambda": per}}
     print(json.dumps(line), flush=True)

@@ -14,4 +14,7 @@ Contents (each function cites the passage of the paper it follows):
 * ``solvers`` -- LSQR (Tikhonov), the group-lasso prox, FISTA, KKT check,
                  direct normal-equation solve, sensitivity indices
 * ``mlp``     -- FP64 forward/backward of the group-screening MLP
+* ``ndct``    -- direct FP64 sums of the grouped half-period cosine transform
+                 (the orthonormal system of Sec. 5, grouped as in the Remark on
+                 other systems in Sec. 3)
 """
