@@ -61,6 +61,26 @@ enum anova_precision {
     ANOVA_PREC_F64 = 3    /* everything in FP64 */
 };
 
+/* The orthonormal system of the transform (Remark on other systems, Sec. 3):
+ * ANOVA_BASIS_EXP  exp(2 pi i <k, x>) on the torus [-1/2, 1/2)^d, groups
+ *                  k_j in I_N minus {0} = {-N/2, .., -1, 1, .., N/2 - 1} (N even);
+ * ANOVA_BASIS_COS  the half-period cosine system of Sec. 5 on the cube [0, 1]^d,
+ *                  phi_k(x) = sqrt(2)^{|supp k|} prod_{j in supp k} cos(pi k_j x_j),
+ *                  groups 1 <= k_j <= N - 1 (any N >= 2), row-major, last axis
+ *                  fastest; the empty set is phi_0 = 1.  Nodes outside [0, 1]
+ *                  act through the even, 2-periodic extension.  The adjoint is
+ *                  g_k = sum_j y_j phi_k(x_j) (real phi_k: no conjugation).
+ * Cosine terms are computed on the exponential kernels at the halved nodes x/2
+ * with the doubled bandwidth 2N (each cosine coefficient stands for 2^{|u|}
+ * mirrored exponential ones), so their oversampled grids are those of an
+ * exponential term of bandwidth 2N and the grid limits below apply to 2N
+ * (FP32: two-dimensional cosine terms up to N = 24, three-dimensional up to
+ * N = 5 at sigma = 2). */
+enum anova_basis {
+    ANOVA_BASIS_EXP = 0,
+    ANOVA_BASIS_COS = 1
+};
+
 enum anova_status {
     ANOVA_OK = 0,
     ANOVA_ERR_INVALID = -1,      /* bad argument (null pointer, size, term, bandwidth) */
@@ -89,6 +109,7 @@ typedef struct {
                            products, FP32 sums): the adjoint spread of FP32, FP16 and BF16
                            plans, and the forward gather of FP32 plans without third-order
                            terms; 1 = on the CUDA cores (FP32) */
+    int basis;          /* enum anova_basis (0: the exponential system) */
 } anova_plan_options;
 
 /*

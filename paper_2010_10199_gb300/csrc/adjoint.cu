@@ -1170,7 +1170,20 @@ __global__ void adjoint_post_f32(DevPlan single, BatchArgs B, float2 *__restrict
     }
     // crop and deconvolve
     const int Nm = N - 1;
-    for (long long q = threadIdx.x; q < T.coef_len; q += blockDim.x) {
+    for (long long q = threadIdx.x; q < T.coef_len && T.basis == ANOVA_BASIS_COS; q += blockDim.x) {
+        // cosine term: 2^{-s/2} times the sum over its 2^s mirrored frequencies
+        int k[3];
+        cos_decode(q, s, N, k);
+        float sx = 0.f, sy = 0.f;
+        for (int sg = 0; sg < (1 << s); ++sg) {
+            float D = (float)cos_amp(s);
+            const float2 v = cur[cos_mirror(k, s, sg, N, n, P.deconv, T.dc_off, T.dr_off, D)];
+            sx = fmaf(v.x, D, sx);
+            sy = fmaf(v.y, D, sy);
+        }
+        fhat[T.coef_off + q] = make_float2(sx, sy);
+    }
+    for (long long q = threadIdx.x; q < T.coef_len && T.basis != ANOVA_BASIS_COS; q += blockDim.x) {
         long long rr = q;
         int pos = 0, mul = 1;
         float D = 1.f;

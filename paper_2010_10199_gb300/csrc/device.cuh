@@ -34,6 +34,45 @@ struct GridEl<__nv_bfloat162> {
     static __device__ __forceinline__ __nv_bfloat162 store(float a, float b) { return __floats2bfloat162_rn(a, b); }
 };
 
+// ------------------------------------------------------------ cosine terms --
+//
+// A term of the half-period cosine system (Sec. 5) runs on the exponential
+// grids: prod_t cos(pi k_t x_t) = 2^{-s} sum over sign patterns eps of
+// exp(2 pi i <eps k, x / 2>), so with the nodes halved (plan time) its block
+// coefficient fhat_k, k in {1..N/2-1}^s (N the term's doubled bandwidth),
+// stands for 2^{-s/2} fhat_k at each of the 2^s exponential frequencies eps k,
+// and the adjoint's coefficient is 2^{-s/2} times the sum over those
+// frequencies.  cos_decode: block position q -> k (row-major, last axis
+// fastest); cos_mirror: grid position of sign pattern sg (bit t negates axis
+// t; negative frequencies at k + n) and the product of its deconvolution
+// factors (column table on the last axis, row table on the others).
+__device__ __forceinline__ void cos_decode(long long q, int s, int N, int (&k)[3]) {
+    const int nc = N / 2 - 1;
+    for (int t = s - 1; t >= 0; --t) {
+        k[t] = (int)(q % nc) + 1;
+        q /= nc;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ int cos_mirror(const int (&k)[3], int s, int sg, int N, int n, const R *deconv, int dc_off,
+                                          int dr_off, R &D) {
+    int pos = 0, mul = 1;
+    for (int t = s - 1; t >= 0; --t) {
+        const int kt = (sg >> t) & 1 ? -k[t] : k[t];
+        const int it = kt < 0 ? kt + N / 2 : kt + N / 2 - 1;   // index in I_N minus {0}
+        pos += (kt < 0 ? kt + n : kt) * mul;
+        mul *= n;
+        D *= (t == s - 1) ? deconv[dc_off + it] : deconv[dr_off + it];
+    }
+    return pos;
+}
+
+// 2^{-s/2}
+__host__ __device__ __forceinline__ double cos_amp(int s) {
+    return s == 1 ? 0.70710678118654752440 : s == 2 ? 0.5 : 0.35355339059327376220;
+}
+
 // ---------------------------------------------------------------- windows --
 
 // ---- TF32 tensor-core products with FP32-level accuracy ----

@@ -81,7 +81,17 @@ __global__ void trafo_pre_f64(DevPlan P, const double2 *__restrict__ fhat) {
     for (int i = threadIdx.x; i < fe; i += blockDim.x) a[i] = make_double2(0.0, 0.0);
     __syncthreads();
     const int Nm = N - 1;
-    for (long long q = threadIdx.x; q < T.coef_len; q += blockDim.x) {
+    for (long long q = threadIdx.x; q < T.coef_len && T.basis == ANOVA_BASIS_COS; q += blockDim.x) {
+        int k[3];
+        cos_decode(q, s, N, k);
+        const double2 c = fhat[T.coef_off + q];
+        for (int sg = 0; sg < (1 << s); ++sg) {
+            double D = cos_amp(s);
+            const int pos = cos_mirror(k, s, sg, N, n, P.deconvd, T.dc_off, T.dr_off, D);
+            a[pos] = make_double2(c.x * D, c.y * D);
+        }
+    }
+    for (long long q = threadIdx.x; q < T.coef_len && T.basis != ANOVA_BASIS_COS; q += blockDim.x) {
         long long r = q;
         int pos = 0, mul = 1;
         double D = 1.0;
@@ -455,7 +465,19 @@ __global__ void adjoint_post_f64(DevPlan P, double2 *__restrict__ fhat) {
     __syncthreads();
     const double2 *cur = grid_fft<double2, double>(a, b, n, s, -1);
     const int Nm = N - 1;
-    for (long long q = threadIdx.x; q < T.coef_len; q += blockDim.x) {
+    for (long long q = threadIdx.x; q < T.coef_len && T.basis == ANOVA_BASIS_COS; q += blockDim.x) {
+        int k[3];
+        cos_decode(q, s, N, k);
+        double sx = 0.0, sy = 0.0;
+        for (int sg = 0; sg < (1 << s); ++sg) {
+            double D = cos_amp(s);
+            const double2 v = cur[cos_mirror(k, s, sg, N, n, P.deconvd, T.dc_off, T.dr_off, D)];
+            sx = fma(v.x, D, sx);
+            sy = fma(v.y, D, sy);
+        }
+        fhat[T.coef_off + q] = make_double2(sx, sy);
+    }
+    for (long long q = threadIdx.x; q < T.coef_len && T.basis != ANOVA_BASIS_COS; q += blockDim.x) {
         long long rr = q;
         int pos = 0, mul = 1;
         double D = 1.0;

@@ -72,7 +72,9 @@ __global__ void k_fixed_point_exponent(DevPlan single, BatchArgs B, const double
     double s = 0.0;
     for (int b = 0; b < FPE_BLOCKS; ++b) s += part[b];
     int e = 100;
-    if (s > 0) e = 61 - (int)ceil(log2(s));
+    // a cosine coefficient stands for 2^s exponential ones of 2^{-s/2} its size
+    // (s <= 3): their absolute sum is at most 2^{3/2} = 2.83 times larger
+    if (s > 0) e = 61 - (int)ceil(log2(s)) - (P.basis == ANOVA_BASIS_COS ? 2 : 0);
     *P.fexp = max(-100, min(100, e));
 }
 

@@ -69,7 +69,7 @@ struct Term {
     int user_index;
     int slot_c;           // FP64 plans: window-table slots of the column and row coordinates
     int slot_r0, slot_r1;
-    int pad2_;
+    int basis;            // ANOVA_BASIS_EXP, or ANOVA_BASIS_COS (N above is then the doubled bandwidth)
 };
 
 // What the forward gather needs of an active term, in one 48-byte record
@@ -135,6 +135,7 @@ struct DevPlan {
     long long n_coeffs;
     long long vec_node_off;   // offset of this problem's nodes in batched node vectors
     long long vec_coef_off;   // offset of this problem's coefficients in batched coefficient vectors
+    int basis;                // ANOVA_BASIS_EXP or ANOVA_BASIS_COS
 };
 
 // Work lists of a launch over several problems (a batch).  With plans == null
@@ -158,6 +159,7 @@ struct Plan {
     int device;
     cudaStream_t stream;
     int precision;
+    int basis;              // ANOVA_BASIS_EXP or ANOVA_BASIS_COS
     double eps;             // target relative error of the transforms
     int d;
     long long M;
@@ -246,7 +248,8 @@ double deconv_factor(int k, int n, int m, double b);
 void window_polys(Window &w, int m, double b);
 int fft_size(int N, double sigma);
 int row_stride(int n);
-__global__ void wrap_nodes_f32(const float *in, float *out, long long total);
+// out = in * scale wrapped into [-1/2, 1/2) (scale 1/2 for cosine plans: x in [0, 1] -> x / 2)
+__global__ void wrap_nodes_f32(const float *in, float *out, long long total, float scale);
 
 // stage timing: call stage_begin before and stage_end after a kernel launch
 void stage_begin(Plan &p, int stage);

@@ -241,7 +241,7 @@ extern "C" int grouped_trafo_noalloc(int d, int64_t M, const float *x_dev, int n
     if (e != cudaSuccess) return cuda_status(e);
     const long long total_x = (long long)d * M;
     wrap_nodes_f32<<<(int)std::min<long long>(4096, (total_x + 255) / 256), 256, 0, st>>>(
-        x_dev, (float *)(base + o_x), total_x);
+        x_dev, (float *)(base + o_x), total_x, 1.0f);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
 

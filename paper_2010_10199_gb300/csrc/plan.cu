@@ -122,20 +122,20 @@ int row_stride(int n) {
     return s;
 }
 
-__global__ void wrap_nodes_f32(const float *in, float *out, long long total) {
+__global__ void wrap_nodes_f32(const float *in, float *out, long long total, float scale) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        float v = in[i];
+        float v = in[i] * scale;
         v = v - floorf(v + 0.5f);   // into [-1/2, 1/2)
         if (v >= 0.5f) v -= 1.0f;
         out[i] = v;
     }
 }
 
-__global__ void wrap_nodes_f64(const double *in, double *out, long long total) {
+__global__ void wrap_nodes_f64(const double *in, double *out, long long total, double scale) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        double v = in[i];
+        double v = in[i] * scale;
         v = v - floor(v + 0.5);
         if (v >= 0.5) v -= 1.0;
         out[i] = v;
@@ -212,6 +212,7 @@ DevPlan dev_view(const Plan &p) {
     v.n_coeffs = p.n_coeffs;
     v.vec_node_off = 0;
     v.vec_coef_off = 0;
+    v.basis = p.basis;
     return v;
 }
 
@@ -289,6 +290,8 @@ static int plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, i
     if (opts) o = *opts;
     if (o.precision < ANOVA_PREC_F32 || o.precision > ANOVA_PREC_F64) return ANOVA_ERR_INVALID;
     if (o.cell_kernel < 0 || o.cell_kernel > 1) return ANOVA_ERR_INVALID;
+    if (o.basis != ANOVA_BASIS_EXP && o.basis != ANOVA_BASIS_COS) return ANOVA_ERR_INVALID;
+    const bool cosine = o.basis == ANOVA_BASIS_COS;
 
     if (o.eps <= 0) o.eps = 1e-5;
     if (o.sigma <= 0) o.sigma = 2.0;
@@ -308,8 +311,10 @@ static int plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, i
             if (j > 0 && t[j] <= t[j - 1]) return ANOVA_ERR_INVALID;
             ++ord;
         }
-        if (ord > 0 && (bandwidth[i] < 2 || bandwidth[i] % 2)) return ANOVA_ERR_INVALID;
-        if (ord > 0 && bandwidth[i] > 4096) return ANOVA_ERR_UNSUPPORTED;
+        // exponential groups need an even N (I_N = [-N/2, N/2)); cosine groups
+        // 1 <= k <= N - 1 take any N >= 2 and run at the doubled bandwidth
+        if (ord > 0 && (bandwidth[i] < 2 || (!cosine && bandwidth[i] % 2))) return ANOVA_ERR_INVALID;
+        if (ord > 0 && bandwidth[i] * (cosine ? 2 : 1) > 4096) return ANOVA_ERR_UNSUPPORTED;
     }
 
     anova_plan_s *h = alloc_fault() ? nullptr : new (std::nothrow) anova_plan_s;
@@ -329,6 +334,7 @@ static int plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, i
     Plan &p = h->p;
     p.stream = (cudaStream_t)stream;
     p.precision = o.precision;
+    p.basis = o.basis;
     p.eps = o.eps;
     p.d = d;
     p.M = M;
@@ -369,7 +375,7 @@ static int plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, i
         for (int j = 0; j < ord; ++j) len *= (bandwidth[i] - 1);
         p.h_user_off[i] = off;
         p.h_user_len[i] = len;
-        p.h_user_n[i] = ord ? fft_size(bandwidth[i], o.sigma) : 0;
+        p.h_user_n[i] = ord ? fft_size(bandwidth[i] * (cosine ? 2 : 1), o.sigma) : 0;
         p.h_user_mc[i] = ord ? mc : 0;
         p.h_user_mr[i] = ord > 1 ? mr : 0;
         p.h_user_order[i] = ord;
@@ -418,7 +424,7 @@ static int plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, i
     p.pitch2 = 8;
     for (int s = 0; s < p.n_terms; ++s)
         if (order[sched[s]] == 2)
-            p.pitch2 = std::max(p.pitch2, row_stride(p.h_user_n[sched[s]] + 2 * (mc - 1) + 1));
+            p.pitch2 = std::max(p.pitch2, row_stride(p.h_user_n[sched[s]] + 2 * (mc - 1) + 1));   // n already doubled
     for (int s = 0; s < p.n_terms; ++s) {
         int i = sched[s];
         const int32_t *t = term_dims + 3 * i;
@@ -428,7 +434,8 @@ static int plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, i
         T.col = t[T.order - 1];
         T.row0 = T.order >= 2 ? t[0] : -1;
         T.row1 = T.order >= 3 ? t[1] : -1;
-        T.N = bandwidth[i];
+        T.N = bandwidth[i] * (cosine ? 2 : 1);   // cosine terms: the mirrored exponential set
+        T.basis = o.basis;
         T.n = p.h_user_n[i];
         T.rows = 1;
         for (int j = 1; j < T.order; ++j) T.rows *= T.n;
@@ -620,9 +627,11 @@ static int plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, i
         long long total = (long long)d * M;
         int blocks = (int)std::min<long long>(4096, (total + 255) / 256);
         if (p.precision == ANOVA_PREC_F64)
-            wrap_nodes_f64<<<blocks, 256, 0, p.stream>>>((const double *)x_dev, (double *)p.x, total);
+            wrap_nodes_f64<<<blocks, 256, 0, p.stream>>>((const double *)x_dev, (double *)p.x, total,
+                                                          cosine ? 0.5 : 1.0);
         else
-            wrap_nodes_f32<<<blocks, 256, 0, p.stream>>>((const float *)x_dev, (float *)p.x, total);
+            wrap_nodes_f32<<<blocks, 256, 0, p.stream>>>((const float *)x_dev, (float *)p.x, total,
+                                                          cosine ? 0.5f : 1.0f);
         chk(cudaGetLastError());
     }
     p.mma_step = spread_step_for(p);

@@ -44,7 +44,18 @@ __device__ __forceinline__ void trafo_pre_body(const DevPlan &single, const Batc
     __syncthreads();
     // zero-extended, deconvolved coefficients at k mod n
     const int Nm = N - 1;
-    for (long long q = threadIdx.x; q < T.coef_len; q += blockDim.x) {
+    for (long long q = threadIdx.x; q < T.coef_len && T.basis == ANOVA_BASIS_COS; q += blockDim.x) {
+        // cosine term: the coefficient at its 2^s mirrored frequencies
+        int k[3];
+        cos_decode(q, s, N, k);
+        const float2 c = fhat[T.coef_off + q];
+        for (int sg = 0; sg < (1 << s); ++sg) {
+            float D = (float)cos_amp(s);
+            const int pos = cos_mirror(k, s, sg, N, n, P.deconv, T.dc_off, T.dr_off, D);
+            a[pos] = make_float2(c.x * D, c.y * D);
+        }
+    }
+    for (long long q = threadIdx.x; q < T.coef_len && T.basis != ANOVA_BASIS_COS; q += blockDim.x) {
         long long r = q;
         int pos = 0, mul = 1;
         float D = 1.f;

@@ -18,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libanova_gft.so")
 
 PREC_F32, PREC_BF16, PREC_F16, PREC_F64 = 0, 1, 2, 3
+BASIS_EXP, BASIS_COS = 0, 1
 
 _lib = None
 
@@ -31,7 +32,7 @@ class AnovaError(RuntimeError):
 class PlanOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eps", ctypes.c_double), ("window_m_col", ctypes.c_int),
                 ("window_m_row", ctypes.c_int), ("sigma", ctypes.c_double), ("n_ctas", ctypes.c_int),
-                ("node_sort", ctypes.c_int), ("cell_kernel", ctypes.c_int)]
+                ("node_sort", ctypes.c_int), ("cell_kernel", ctypes.c_int), ("basis", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -211,7 +212,7 @@ def autotune(x, terms, bandwidths, eps: float = 1e-5, reps: int = 3, stream=None
             td[3 * i + j] = u[j] if j < len(u) else -1
         bw[i] = int(bandwidths[i]) if len(u) else 0
     opts = PlanOptions(precision=PREC_F32, eps=0.0, window_m_col=0, window_m_row=0, sigma=0.0, n_ctas=0,
-                       node_sort=0, cell_kernel=0)
+                       node_sort=0, cell_kernel=0, basis=BASIS_EXP)
     trials = (TuneTrial * 32)()
     nt = ctypes.c_int(0)
     st = stream if stream is not None else torch.cuda.current_stream()
@@ -359,7 +360,7 @@ class Plan:
 
     def __init__(self, x, terms, bandwidths, precision: int = PREC_F32, eps: float = 0.0, sigma: float = 0.0,
                  window_m_row: int = 0, n_ctas: int = 0, node_sort: int = 0, cell_kernel: int = 0,
-                 stream=None):
+                 basis: int = BASIS_EXP, stream=None):
         import torch
         if not (isinstance(x, torch.Tensor) and x.is_cuda):
             raise TypeError("x must be a CUDA tensor [d, M]")
@@ -369,9 +370,10 @@ class Plan:
         self.d, self.M = int(x.shape[0]), int(x.shape[1])
         self.terms = [tuple(u) for u in terms]
         self.bandwidths = [int(b) for b in bandwidths]
+        self.basis = int(basis)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opts = PlanOptions(precision=precision, eps=eps, window_m_col=0, window_m_row=window_m_row, sigma=sigma,
-                           n_ctas=n_ctas, node_sort=node_sort, cell_kernel=cell_kernel)
+                           n_ctas=n_ctas, node_sort=node_sort, cell_kernel=cell_kernel, basis=basis)
         self.handle = anova_plan_create(self.d, self.M, x.data_ptr() if self.M else 0, self.terms,
                                         self.bandwidths, opts, self.stream.cuda_stream)
         self.n_coeffs = anova_num_coeffs(self.handle)

@@ -368,3 +368,35 @@ def bspline_workload(seed: int = 0, M: int = 10_000, bandwidths=None, noise: flo
     y = fx + noise * math.sqrt(float(np.mean(fx ** 2))) * normal(seed, S_NOISE, M)
     return dict(name="bspline", d=d, M=M, terms=terms, bandwidths=bw, x=x, y=y.astype(np.complex128),
                 c=bspline_coefficients(terms, bw), norm2=bspline_norm2(), noise=noise)
+
+
+# --------------------------------------------------------------------------
+# the cosine (non-periodic) workload: the shape of the application of Sec. 5
+# (d = 12 attributes min-max normalised into [0, 1], all terms with |u| <= 2,
+# N = 82 / 10 as in eq. (appl:bandwidths): 79 terms, 6 319 coefficients,
+# 36 160 training nodes, labels y in {0, 1}).  The census data are not here;
+# synthetic attributes stand in: six continuous ones (Beta(2,5)-skewed and
+# uniform) and six categorical ones with 2..16 levels spread over [0, 1], and
+# a label that thresholds a sparse low-order function of them plus noise.
+# --------------------------------------------------------------------------
+
+def cosine_workload(seed: int = 0, M: int = 36_160, bandwidths=None) -> dict:
+    d = 12
+    by_order = {1: 82, 2: 10} if bandwidths is None else bandwidths
+    terms = terms_up_to(d, 2)
+    bw = bandwidths_by_order(terms, by_order)
+    u = uniform(seed, S_POINTS, 3 * d * M).reshape(3, d, M)
+    x = np.empty((d, M))
+    for t in range(d):
+        if t < 3:       # skewed continuous attribute: the median-of-3 order statistic of u^2
+            x[t] = np.median(u[:, t, :] ** 2, axis=0)
+        elif t < 6:     # uniform continuous attribute
+            x[t] = u[0, t]
+        else:           # categorical attribute with 2..16 levels, normalised to [0, 1]
+            levels = 2 + (t * 5) % 15
+            x[t] = np.floor(u[0, t] * levels) / (levels - 1)
+    score = (np.sin(np.pi * x[0]) * x[7] + 0.8 * np.exp(-6 * (x[3] - 0.3) ** 2) + 0.5 * x[1] * x[9]
+             + 0.3 * np.cos(2 * np.pi * x[4]) + 0.2 * normal(seed, S_NOISE, M))
+    y = (score > np.median(score)).astype(np.float64)
+    return dict(name="cosine_adult_shape", d=d, M=M, terms=terms, bandwidths=bw, x=x,
+                y=y.astype(np.complex128))
