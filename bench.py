@@ -10,13 +10,16 @@ grouped_adjoint through the C ABI.  Inputs are resident in HBM for ``value``;
 both results) inside the timed region.  L2 is flushed (256 MB write) before
 every timed step, outside the step's events.
 
-The default line also carries ``lambda_path``: the group-lasso lambda path of
+The default line also carries ``precision_study`` (the same pairs with FP16 and
+BF16 grid storage), ``batch`` (64 independent problems of uneven size in one
+launch per kernel against one plan after the other, transform pairs and 30
+LSQR iterations) and ``lambda_path``: the group-lasso lambda path of
 the d = 30 workload (466 terms, M = 2e6, 20 lambda values) solved three ways
 -- FP32 with the learned group screen, FP32 on all groups, FP64 on all groups
 (the plain path) -- with their times, iterations, active groups and KKT
 residuals per lambda, the agreement of the screened FP32 path with the FP64
 path, and the SM clocks sampled over that region (``--no-lambda-path`` leaves
-it out).
+these three out).
 
 ``--impl reference`` times the FP64 oracle (direct summation on the host
 cores): every step is one pair on a bounded node sample of the same workload,
@@ -75,7 +78,7 @@ def parse():
     ap.add_argument("--max-it", type=int, default=5000, help="lambda-path mode: FISTA iterations per lambda")
     ap.add_argument("--tol", type=float, default=1e-6, help="lambda-path mode: FISTA relative-change stop")
     ap.add_argument("--skip-f64", action="store_true", help="lambda-path mode: leave out the FP64 path")
-    ap.add_argument("--no-lambda-path", action="store_true", help="pairs mode: leave out the lambda-path object")
+    ap.add_argument("--no-lambda-path", action="store_true", help="pairs mode: leave out the precision, batch and lambda-path objects")
     a = ap.parse_args()
     if a.M <= 0:
         a.M = {"pairs": 1_000_000, "lambda-path": 2_000_000, "lsqr-path": 500_000}.get(a.mode, 1_000_000)
@@ -395,6 +398,10 @@ def run_mine(args, rank, world, local_rank):
     if rank == 0:
         if world == 1 and not args.no_lambda_path and args.precision == "f32":
             torch.cuda.empty_cache()
+            line["precision_study"] = precision_result(args, local_rank)
+            torch.cuda.empty_cache()
+            line["batch"] = batch_result(args, local_rank)
+            torch.cuda.empty_cache()
             line["lambda_path"] = lambda_path_result(args, local_rank, 2_000_000, 20)
         print(json.dumps(line), flush=True)
 
@@ -558,9 +565,10 @@ def run_lambda_path(args, local_rank):
 
 # ------------------------------------------------------------------ batch ---
 
-def run_batch(args, local_rank):
+def batch_result(args, local_rank) -> dict:
     """64 problems, M log-uniform in [1e4, 2e5], d in 5..15, |u| <= 2: one
-    launch per kernel for all of them vs one plan after the other."""
+    launch per kernel for all of them vs one plan after the other, with the SM
+    clocks sampled over the timed regions."""
     import numpy as np
     import torch
 
@@ -579,9 +587,10 @@ def run_batch(args, local_rank):
     y_all = torch.from_numpy(np.concatenate([w["y"] for w in probs]).astype(np.complex64)).to(dev)
     fh_p = [fh_all[B.coef_off[p]:B.coef_off[p + 1]] for p in range(64)]
     y_p = [y_all[B.node_off[p]:B.node_off[p + 1]] for p in range(64)]
+    steps = max(3, args.steps)
 
     def timed(fn, reps):
-        for _ in range(args.warmup):
+        for _ in range(max(3, args.warmup)):
             fn()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -601,9 +610,6 @@ def run_batch(args, local_rank):
             plans[p].trafo(fh_p[p])
             plans[p].adjoint(y_p[p])
 
-    t_bp = timed(batched_pair, args.steps)
-    t_sp = timed(sequential_pair, args.steps)
-
     def batched_lsqr():
         B.lsqr(y_all, 1e-3, max_it=30)
 
@@ -611,16 +617,77 @@ def run_batch(args, local_rank):
         for p in range(64):
             plans[p].lsqr(y_p[p], 1e-3, max_it=30)
 
-    t_bl = timed(batched_lsqr, max(1, args.steps // 3))
-    t_sl = timed(sequential_lsqr, max(1, args.steps // 3))
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t_bp = timed(batched_pair, steps)
+    t_sp = timed(sequential_pair, steps)
+    t_bl = timed(batched_lsqr, max(1, steps // 3))
+    t_sl = timed(sequential_lsqr, max(1, steps // 3))
+    clk = clocks.stop()
     Ms = [w["M"] for w in probs]
-    line = {"metric": "many problems in one launch: sequential time / batched time", "value": t_sl / t_bl,
-            "unit": "x", "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic (seeded SplitMix64)",
-            "config": {"workload": f"64 problems, M {min(Ms)}..{max(Ms)} (total {sum(Ms)}), d 5..15, |u|<=2, "
-                                   "N=32 (1D) / 16x16 (2D)", "lsqr": "lambda 1e-3, 30 iterations"},
+    B.close()
+    for P in plans:
+        P.close()
+    return {"metric": "many problems in one launch: sequential time / batched time (30 LSQR iterations)",
+            "value": t_sl / t_bl, "unit": "x", "higher_is_better": True,
+            "workload": f"64 problems, M {min(Ms)}..{max(Ms)} (total {sum(Ms)}), d 5..15, |u|<=2, N=32 (1D) / 16x16 (2D)",
+            "lsqr": "lambda 1e-3, 30 iterations, one LSQR per problem with its own FP64 scalars",
+            "kernels": "per launch all problems: trafo_pre, fixed-point passes around gather_mma_f32, spread_mma_f32, "
+                       "reduce_partials, adjoint_post (cell-sorted records per problem)",
             "results": {"batched_pair_s": t_bp, "sequential_pair_s": t_sp, "pair_speedup": t_sp / t_bp,
-                        "batched_lsqr_s": t_bl, "sequential_lsqr_s": t_sl, "lsqr_speedup": t_sl / t_bl}}
+                        "batched_lsqr_s": t_bl, "sequential_lsqr_s": t_sl, "lsqr_speedup": t_sl / t_bl,
+                        "batched_pairs_per_s": 1.0 / t_bp},
+            "clocks": clk}
+
+
+def run_batch(args, local_rank):
+    r = batch_result(args, local_rank)
+    line = {"metric": r["metric"], "value": r["value"], "unit": "x", "higher_is_better": True, "n_gpus": 1,
+            "dtype": "f32", "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": r["workload"], "lsqr": r["lsqr"]}, "results": r["results"], "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
+
+
+def precision_result(args, local_rank) -> dict:
+    """The d = 20 pairs with the oversampled grids stored in FP32, FP16 or BF16
+    (FP32 arithmetic throughout): pairs per second, L2 flushed between pairs.
+    Their errors against the FP64 oracle are measured by the parity tests."""
+    import numpy as np
+    import torch
+
+    from paper_2010_10199_gb300 import gft, inputs
+
+    dev = torch.device("cuda", local_rank)
+    w = inputs.c2_scale(M=args.M)
+    xd = torch.from_numpy(w["x"].astype(np.float32)).to(dev)
+    fhat = torch.from_numpy(w["fhat"].astype(np.complex64)).to(dev)
+    y = torch.from_numpy(w["y"].astype(np.complex64)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for name, prec in (("f32", gft.PREC_F32), ("f16", gft.PREC_F16), ("bf16", gft.PREC_BF16)):
+        P = gft.Plan(xd, w["terms"], w["bandwidths"], precision=prec)
+        f = torch.empty(args.M, dtype=torch.complex64, device=dev)
+        g = torch.empty(P.n_coeffs, dtype=torch.complex64, device=dev)
+        for _ in range(max(3, args.warmup)):
+            P.trafo(fhat, out=f)
+            P.adjoint(y, out=g)
+        ms = []
+        for _ in range(max(5, args.steps)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.trafo(fhat, out=f)
+            P.adjoint(y, out=g)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        out[name] = {"pairs_per_s": 1e3 / (sum(ms) / len(ms)), "ms_per_pair": sum(ms) / len(ms)}
+        P.close()
+    out["clocks"] = clocks.stop()
+    out["workload"] = WORKLOAD
+    return out
 
 
 # ------------------------------------------------------------- lsqr path ---

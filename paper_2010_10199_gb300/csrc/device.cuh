@@ -109,6 +109,18 @@ __device__ __forceinline__ float horner8(const float c[NCOEF], float v) {
     return s;
 }
 
+// The same polynomial at v and at -v from its even and odd parts,
+// p(+-v) = E(v^2) +- v O(v^2): 9 operations instead of two Horner chains of 7.
+// Tap 2m - 1 - j of the (even) window at v is tap j at -v.
+__device__ __forceinline__ void horner8_pm(const float c[NCOEF], float v, float &p, float &m) {
+    static_assert(NCOEF == 8, "even/odd split of a degree-7 polynomial");
+    const float v2 = v * v;
+    const float e = fmaf(fmaf(fmaf(c[6], v2, c[4]), v2, c[2]), v2, c[0]);
+    const float o = fmaf(fmaf(fmaf(c[7], v2, c[5]), v2, c[3]), v2, c[1]);
+    p = fmaf(v, o, e);
+    m = fmaf(-v, o, e);
+}
+
 // Direct evaluation of the normalised Kaiser--Bessel window at distance d
 // (grid units); used where no per-tap polynomial is kept in registers.
 __device__ __forceinline__ float kb_direct(float d, int m, float b, float inv_psi0) {

@@ -324,28 +324,42 @@ __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, i
                                                bool ord2, const float4 *coef, unsigned long long *__restrict__ acc,
                                                float sc) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    float ca[NCOEF], cb[NCOEF], ra[NCOEF], rb[NCOEF];   // column taps t, t + 4; row taps 2t, 2t + 1
+    // With 8 row taps (MR = 4) the contraction index k of the mma and the
+    // output index (grid row) are permuted so that every lane needs mirrored
+    // tap pairs of its own nodes: k = t and k = t + 4 are column taps t and
+    // 7 - t, outputs 2t and 2t + 1 are rows t and 7 - t.  The window is even,
+    // so tap 7 - t at v is tap t at -v: one even/odd evaluation gives both
+    // (horner8_pm), from the coefficients of taps t only.  With 6 row taps the
+    // natural order stays: column taps t, t + 4, rows 2t, 2t + 1.
+    constexpr bool MIRROR = MR == 4;
+    float ca[NCOEF], cb[NCOEF], ra[NCOEF], rb[NCOEF];   // column taps t, t + 4; row taps 2t, 2t + 1 (MIRROR: ca, ra)
     auto fetch = [&](const float4 *c, float (&dst)[NCOEF]) {
         const float4 lo = c[0], hi = c[1];
         dst[0] = lo.x, dst[1] = lo.y, dst[2] = lo.z, dst[3] = lo.w;
         dst[4] = hi.x, dst[5] = hi.y, dst[6] = hi.z, dst[7] = hi.w;
     };
     fetch(coef + 2 * t, ca);
-    fetch(coef + 2 * (t + 4), cb);
-    fetch(coef + 16 + 2 * (2 * t), ra);
-    fetch(coef + 16 + 2 * (2 * t + 1), rb);
+    if constexpr (MIRROR) {
+        fetch(coef + 16 + 2 * t, ra);
+    } else {
+        fetch(coef + 2 * (t + 4), cb);
+        fetch(coef + 16 + 2 * (2 * t), ra);
+        fetch(coef + 16 + 2 * (2 * t + 1), rb);
+    }
     const int nstep = (n + 2 * GM_TILE - 1) / (2 * GM_TILE);
     // record u of step i; past the end the last record is read again (not written back)
     auto ld = [&](int i, int u) { return __ldg(rec + min(2 * GM_TILE * i + u, n - 1)); };
     float4 q[4] = {ld(0, g), ld(0, g + 8), ld(0, g + 16), ld(0, g + 24)};
     int cur = -1;            // cell whose window is in bh, bl
     unsigned bh[4], bl[4];   // B fragments: real part (b0, b1), imaginary part (b0, b1)
-    const bool row_ok = ord2 ? g < 2 * MR : g == 0;   // grid row g of the window exists
+    // output index g holds grid row grow (mirrored: 2s -> row s, 2s + 1 -> row 7 - s)
+    const int grow = MIRROR ? ((g & 1) ? 7 - (g >> 1) : (g >> 1)) : g;
+    const bool row_ok = ord2 ? grow < 2 * MR : grow == 0;   // that grid row of the window exists
     auto load_b = [&](int off) {
         float2 v0 = make_float2(0.f, 0.f), v1 = v0;
         if (row_ok) {
-            v0 = S[off + g * stride + t];
-            v1 = S[off + g * stride + t + 4];
+            v0 = S[off + grow * stride + t];
+            v1 = S[off + grow * stride + (MIRROR ? 7 - t : t + 4)];
         }
         split_tf32(v0.x, bh[0], bl[0]);
         split_tf32(v1.x, bh[1], bl[1]);
@@ -382,10 +396,20 @@ __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, i
         unsigned ah[2][4], al[2][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            split_tf32(horner8(ca, q[2 * h].y), ah[h][0], al[h][0]);
-            split_tf32(horner8(ca, q[2 * h + 1].y), ah[h][1], al[h][1]);
-            split_tf32(horner8(cb, q[2 * h].y), ah[h][2], al[h][2]);
-            split_tf32(horner8(cb, q[2 * h + 1].y), ah[h][3], al[h][3]);
+            if constexpr (MIRROR) {
+                float w0, w0m, w1, w1m;   // taps t and 7 - t of nodes g, g + 8
+                horner8_pm(ca, q[2 * h].y, w0, w0m);
+                horner8_pm(ca, q[2 * h + 1].y, w1, w1m);
+                split_tf32(w0, ah[h][0], al[h][0]);
+                split_tf32(w1, ah[h][1], al[h][1]);
+                split_tf32(w0m, ah[h][2], al[h][2]);
+                split_tf32(w1m, ah[h][3], al[h][3]);
+            } else {
+                split_tf32(horner8(ca, q[2 * h].y), ah[h][0], al[h][0]);
+                split_tf32(horner8(ca, q[2 * h + 1].y), ah[h][1], al[h][1]);
+                split_tf32(horner8(cb, q[2 * h].y), ah[h][2], al[h][2]);
+                split_tf32(horner8(cb, q[2 * h + 1].y), ah[h][3], al[h][3]);
+            }
         }
         float dre[2][4] = {}, dim[2][4] = {};
         const int o[4] = {__float_as_int(q[0].z), __float_as_int(q[1].z), __float_as_int(q[2].z),
@@ -405,7 +429,10 @@ __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, i
             const float4 &q0 = q[2 * h], &q1 = q[2 * h + 1];
             // row weights: taps 2t (r0: node g, r1: node g + 8) and 2t + 1 (r2, r3)
             float r[4];
-            if (ord2) {
+            if (ord2 && MIRROR) {   // rows t, 7 - t of nodes g (r0, r2) and g + 8 (r1, r3)
+                horner8_pm(ra, q0.x, r[0], r[2]);
+                horner8_pm(ra, q1.x, r[1], r[3]);
+            } else if (ord2) {
                 r[0] = horner8(ra, q0.x);
                 r[1] = horner8(ra, q1.x);
                 r[2] = horner8(rb, q0.x);
