@@ -582,8 +582,8 @@ static size_t spread_mma_smem_bytes(long long max_grid_bytes, int step) {
 
 template <int MR, bool ORD2, int MMA_STEP>
 __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, const float2 *__restrict__ y, int n,
-                                               float2 *S, int stride, const float ccf[NCOEF], const float rcf[NCOEF],
-                                               float4 *rring, float2 *yring) {
+                                               float2 *S, int stride, const f32x2 rcp[NCOEF], float4 *rring,
+                                               float2 *yring) {
     using R = MmaRing<MMA_STEP>;
     constexpr unsigned MMA_RING = R::RING, MMA_YRING = R::YRING;
     constexpr int MMA_DR = R::DR, MMA_DY = R::DY;
@@ -659,11 +659,14 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
             const int sl = sl0 + 8 * h, yl = yl0 + 8 * h;
             const float4 r0 = rring[sl + t], r1 = rring[sl + t + 4];
             const float2 y0 = yring[yl + t], y1 = yring[yl + t + 4];
-            const float wc0 = horner8(ccf, r0.y), wc1 = horner8(ccf, r1.y);
+            // row and column weights of nodes t, t + 4: one packed Horner per node
+            float wr0, wc0, wr1, wc1;
+            horner8_x2(rcp, r0.x, r0.y, wr0, wc0);
+            horner8_x2(rcp, r1.x, r1.y, wr1, wc1);
             unsigned bh0, bl0, bh1, bl1;
             if (ORD2) {
-                split_tf32(g < 2 * MR ? horner8(rcf, r0.x) : 0.f, bh0, bl0);
-                split_tf32(g < 2 * MR ? horner8(rcf, r1.x) : 0.f, bh1, bl1);
+                split_tf32(g < 2 * MR ? wr0 : 0.f, bh0, bl0);
+                split_tf32(g < 2 * MR ? wr1 : 0.f, bh1, bl1);
             } else {
                 bh0 = bh1 = g == 0 ? 0x3f800000u : 0u;
                 bl0 = bl1 = 0u;
@@ -712,15 +715,14 @@ template <int MR, int STEP>
 __device__ __forceinline__ void spread_mma_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                 long long j0, long long j1, float2 *S, unsigned char *stg_raw) {
     const int warp = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
-    float ccf[NCOEF], rcf[NCOEF];
+    // coefficient pairs (row tap g, column tap g) for the packed Horner; order-1
+    // terms have no row window (their row weight is unused)
+    f32x2 rcp[NCOEF];
     {
         const float *cs = P.windows[T.wc].c[g];
         const float *rs = P.windows[T.wr].c[min(g, 2 * MR - 1)];
 #pragma unroll
-        for (int q = 0; q < NCOEF; ++q) {
-            ccf[q] = __ldg(cs + q);
-            rcf[q] = __ldg(rs + q);
-        }
+        for (int q = 0; q < NCOEF; ++q) rcp[q] = pk2(__ldg(rs + q), __ldg(cs + q));
     }
     constexpr int NW = SPREAD_THREADS / 32;
     const long long len = j1 - j0, per = (len + 8 * NW - 1) / (8 * NW) * 8;
@@ -731,9 +733,9 @@ __device__ __forceinline__ void spread_mma_item(const DevPlan &P, const Term &T,
     float4 *rring = (float4 *)ring;
     float2 *yring = (float2 *)(ring + MmaRing<STEP>::REC_BYTES);
     if (T.order == 2)
-        spread_mma_run<MR, true, STEP>(rec, y, (int)(b - a), S, T.stride, ccf, rcf, rring, yring);
+        spread_mma_run<MR, true, STEP>(rec, y, (int)(b - a), S, T.stride, rcp, rring, yring);
     else
-        spread_mma_run<MR, false, STEP>(rec, y, (int)(b - a), S, T.stride, ccf, rcf, rring, yring);
+        spread_mma_run<MR, false, STEP>(rec, y, (int)(b - a), S, T.stride, rcp, rring, yring);
 }
 
 // ---- Third-order cell sums on the tensor cores ----
@@ -763,9 +765,8 @@ static size_t spread3_mma_smem_bytes(long long max_grid_bytes) {
 
 template <int MR>
 __device__ __forceinline__ void spread3_mma_run(const float4 *__restrict__ rec, const float2 *__restrict__ y, int n,
-                                                float2 *S, const Term &T, const float ccf[NCOEF],
-                                                const float rcf[NCOEF], const float bcf[NCOEF], float4 *rring,
-                                                float2 *yring) {
+                                                float2 *S, const Term &T, const f32x2 cbp[NCOEF],
+                                                const float rcf[NCOEF], float4 *rring, float2 *yring) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int ib_g = (g >> 1) + 4 * (g & 1);   // second-row tap of B column g
     const int nn = T.n, stride = T.stride, mc = T.mc;
@@ -822,11 +823,15 @@ __device__ __forceinline__ void spread3_mma_run(const float4 *__restrict__ rec, 
             const float4 q0 = rring[2 * (sl + t)], c0 = rring[2 * (sl + t) + 1];
             const float4 q1 = rring[2 * (sl + t + 4)], c1 = rring[2 * (sl + t + 4) + 1];
             const float2 y0 = yring[sl + t], y1 = yring[sl + t + 4];
-            const float wc0 = horner8(ccf, q0.z), wc1 = horner8(ccf, q1.z);
-            // second row coordinate: tap g of nodes t, t + 4 (the B column);
-            // first row coordinate: tap g here, handed round below
+            // column tap g and second-row tap ib(g) (the B column) of nodes t,
+            // t + 4, one packed Horner per node; first-row tap g here, handed
+            // round below
             const bool gok = ib_g < 2 * MR;
-            const float wb0 = gok ? horner8(bcf, q0.y) : 0.f, wb1 = gok ? horner8(bcf, q1.y) : 0.f;
+            float wc0, wc1, wb0, wb1;
+            horner8_x2(cbp, q0.z, q0.y, wc0, wb0);
+            horner8_x2(cbp, q1.z, q1.y, wc1, wb1);
+            wb0 = gok ? wb0 : 0.f;
+            wb1 = gok ? wb1 : 0.f;
             const float wa0 = horner8(rcf, q0.x), wa1 = horner8(rcf, q1.x);
             const int key0 = __float_as_int(c0.w), key1 = __float_as_int(c1.w);
             bool p0 = base + t < n, p1 = base + t + 4 < n;   // nodes t, t + 4 not yet added
@@ -885,8 +890,9 @@ template <int MR>
 __device__ __forceinline__ void spread3_mma_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                  long long j0, long long j1, float2 *S, unsigned char *stg_raw) {
     const int warp = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
-    // column tap g, first-row tap g, second-row tap of B column g
-    float ccf[NCOEF], rcf[NCOEF], bcf[NCOEF];
+    // (column tap g, second-row tap of B column g) pairs, first-row tap g
+    f32x2 cbp[NCOEF];
+    float rcf[NCOEF];
     {
         const int ib = (g >> 1) + 4 * (g & 1);
         const float *cs = P.windows[T.wc].c[g];
@@ -894,9 +900,8 @@ __device__ __forceinline__ void spread3_mma_item(const DevPlan &P, const Term &T
         const float *bs = P.windows[T.wr].c[min(ib, 2 * MR - 1)];
 #pragma unroll
         for (int q = 0; q < NCOEF; ++q) {
-            ccf[q] = __ldg(cs + q);
+            cbp[q] = pk2(__ldg(cs + q), __ldg(bs + q));
             rcf[q] = __ldg(rs + q);
-            bcf[q] = __ldg(bs + q);
         }
     }
     constexpr int NW = SPREAD_THREADS / 32;
@@ -904,7 +909,7 @@ __device__ __forceinline__ void spread3_mma_item(const DevPlan &P, const Term &T
     const long long a = j0 + warp * per, b = min(j1, a + per);
     if (a >= b) return;
     unsigned char *ring = stg_raw + warp * MMA3_RING_BYTES;
-    spread3_mma_run<MR>(P.srec + (long long)T.sort_slot * P.M + 2 * a, y, (int)(b - a), S, T, ccf, rcf, bcf,
+    spread3_mma_run<MR>(P.srec + (long long)T.sort_slot * P.M + 2 * a, y, (int)(b - a), S, T, cbp, rcf,
                         (float4 *)ring, (float2 *)(ring + MMA3_REC_BYTES));
 }
 

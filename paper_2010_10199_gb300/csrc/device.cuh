@@ -121,6 +121,35 @@ __device__ __forceinline__ void horner8_pm(const float c[NCOEF], float v, float 
     m = fmaf(-v, o, e);
 }
 
+// ---- packed FP32 pairs ----
+//
+// sm_100-class GPUs execute two FP32 fused multiply-adds of one lane in one
+// instruction (fma.rn.f32x2 on a 64-bit register pair) at the same FMA rate,
+// which halves the issue slots of independent pairs of operations; each half
+// rounds exactly as the scalar fmaf does.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Two degree-7 polynomials at once: coefficient pairs cp[i] = (a_i, b_i),
+// arguments (va, vb); the same operations as horner8 on each half.
+__device__ __forceinline__ void horner8_x2(const f32x2 cp[NCOEF], float va, float vb, float &pa, float &pb) {
+    const f32x2 v = pk2(va, vb);
+    f32x2 s = cp[NCOEF - 1];
+#pragma unroll
+    for (int i = NCOEF - 2; i >= 0; --i) s = fma2(s, v, cp[i]);
+    upk2(s, pa, pb);
+}
+
 // Direct evaluation of the normalised Kaiser--Bessel window at distance d
 // (grid units); used where no per-tap polynomial is kept in registers.
 __device__ __forceinline__ float kb_direct(float d, int m, float b, float inv_psi0) {
