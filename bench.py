@@ -82,6 +82,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6, help="lambda-path mode: FISTA relative-change stop")
     ap.add_argument("--skip-f64", action="store_true", help="lambda-path mode: leave out the FP64 path")
     ap.add_argument("--no-lambda-path", action="store_true", help="pairs mode: leave out the precision, batch and lambda-path objects")
+    ap.add_argument("--no-tune", action="store_true", help="pairs mode: the default plan options instead of the autotuner's")
     a = ap.parse_args()
     if a.M <= 0:
         a.M = {"pairs": 1_000_000, "lambda-path": 2_000_000, "lsqr-path": 500_000}.get(a.mode, 1_000_000)
@@ -168,7 +169,7 @@ def pairs_config(args) -> dict:
 def pairs_method(args, m_row: int) -> dict:
     """How this library computes the pairs (the GPU arm only)."""
     return {"precision": "fp64 throughout" if args.precision == "f64" else "fp32 grids and accumulation",
-            "window": f"Kaiser-Bessel, sigma=2, {2 * m_row} row x 8 column taps",
+            "window": f"Kaiser-Bessel, {2 * m_row} row x 8 column taps",
             "cell_products": "CUDA cores" if args.cell_kernel else "tensor cores (TF32 split, 3 products)"}
 
 
@@ -249,8 +250,21 @@ def run_mine(args, rank, world, local_rank):
     tcdt = torch.complex128 if f64 else torch.complex64
     esz = 16 if f64 else 8
     xd = torch.from_numpy(w["x"].astype(rdt)).to(dev)
-    P = gft.Plan(xd, w["terms"], w["bandwidths"], precision=gft.PREC_F64 if f64 else gft.PREC_F32,
-                 cell_kernel=args.cell_kernel)
+    # the plan's options come from the library's autotuner (FP32, error target
+    # 1e-5 judged on the whole vectors and on every coefficient block) unless
+    # fixed by --no-tune / --cell-kernel / --precision f64
+    tune = None
+    opts = {"cell_kernel": args.cell_kernel}
+    if not f64 and not args.no_tune and args.cell_kernel == 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        chosen, trials = gft.autotune(xd, w["terms"], w["bandwidths"], eps=1e-5, reps=3)
+        torch.cuda.synchronize()
+        opts = chosen
+        tune = {"chosen": chosen, "seconds": time.perf_counter() - t0, "candidates": len(trials),
+                "trials": [{k: (None if isinstance(v, float) and not math.isfinite(v) else v) for k, v in t.items()}
+                           for t in trials]}
+    P = gft.Plan(xd, w["terms"], w["bandwidths"], precision=gft.PREC_F64 if f64 else gft.PREC_F32, **opts)
     n = P.n_coeffs
     fhat_h = torch.from_numpy(w["fhat"].astype(cdt)).pin_memory()
     y_h = torch.from_numpy(w["y"].astype(cdt)).pin_memory()
@@ -320,8 +334,15 @@ def run_mine(args, rank, world, local_rank):
     M, d = args.M, 20
     n_terms2, n_terms1 = 190, 20
     m_row = max(P.term_grid(u)[2] for u in range(len(w["terms"])))   # the plan's row half-width
-    # stored grids: order 2 (n + 2 (m_row - 1) + 1) rows of pitch 72, order 1 one row of 136 (n = 64 / 128)
-    grid_bytes = 8 * (n_terms2 * (64 + 2 * (m_row - 1) + 1) * 72 + n_terms1 * 136)
+    n2 = P.term_grid(len(w["terms"]) - 1)[0]   # oversampled sizes of the 2-D and 1-D terms
+    n1 = P.term_grid(1)[0]
+
+    def pitch(v):   # stored row pitch: v rounded up to 8 (mod 16) complex elements
+        while v % 16 != 8:
+            v += 1
+        return v
+    # stored grids: order 2 (n + 2 (m_row - 1) + 1) rows, order 1 one row, each with 3 + 4 column halo
+    grid_bytes = 8 * (n_terms2 * (n2 + 2 * (m_row - 1) + 1) * pitch(n2 + 7) + n_terms1 * pitch(n1 + 7))
     rs = 8 if f64 else 4
     grid_bytes = grid_bytes * esz // 8
     if gms / max(gl, 1) >= sms / max(sl, 1):
@@ -390,7 +411,9 @@ def run_mine(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
                 "data": "synthetic (seeded SplitMix64)",
-                "config": pairs_config(args), "method": pairs_method(args, m_row),
+                "config": pairs_config(args), "method": dict(pairs_method(args, m_row), plan_options=opts,
+                                                             oversampled_n={"1d": n1, "2d": n2}),
+                "autotune": tune,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
                 # algorithmic (node, non-empty term) pairs of both transforms per second, all ranks
