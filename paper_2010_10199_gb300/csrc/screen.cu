@@ -215,6 +215,11 @@ int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, c
     std::vector<double> pairs;
     std::vector<float> prob(G);
     std::vector<uint8_t> mask(G);
+    // the step bound of a small proposal depends only on its group set: kept
+    // for the next solve on the same set (consecutive sparse lambdas mostly
+    // propose the same groups), which saves its Lanczos estimate
+    std::vector<uint8_t> bound_mask;
+    double bound_L = 0.0;
     long long proposed_total = 0, readmitted_total = 0, rounds_total = 0, term_iters = 0, full_term_iters = 0;
     for (int li = 0; li < n_lambda; ++li) {
         const int idx = ord[li];
@@ -250,11 +255,17 @@ int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, c
             // a large one the path's bound, which costs no extra transforms
             int prop_terms = 0;
             for (int u = 0; u < G; ++u) prop_terms += mask[u] && p.h_user_order[u] > 0;
-            const double L0 = 4 * prop_terms <= p.n_terms ? 0.0 : Lpath;
+            const bool small = 4 * prop_terms <= p.n_terms;
+            double L0 = small ? 0.0 : Lpath;
+            if (small && bound_L > 0.0 && bound_mask == mask) L0 = bound_L;
             double L = 0.0;
             rc = fista_impl(p, y, w_dev, &lam, 1, max_it, tol, 0, L0, 2.0, mask.data(), S.fprev,
                             path + (long long)idx * n, &I, &L);
             if (rc) return rc;
+            if (small) {
+                bound_mask = mask;
+                bound_L = L;
+            }
             int act_terms = 0;
             for (int u = 0; u < G; ++u) act_terms += mask[u] && p.h_user_order[u] > 0;
             term_iters += (long long)I.iterations * act_terms;
