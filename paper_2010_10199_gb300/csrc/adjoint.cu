@@ -31,7 +31,10 @@ __device__ __forceinline__ void red_add(float *addr, float v) {
 __device__ __forceinline__ int freq_index_a(int q, int N) { return q < N / 2 ? q - N / 2 : q - N / 2 + 1; }
 
 enum { SK_STAGED = 0, SK_ORDER3 = 1, SK_MMA = 2, SK_MMA3 = 3 };
-constexpr int SPREAD_MMA_CTAS_PER_SM = 3;   // 80 registers
+// the order-1/2 tensor-core spread: 12 warps per CTA, 2 CTAs per SM (80
+// registers); two grid copies per SM leave each warp room for deep rings
+constexpr int SPREAD_MMA_THREADS = 384;
+constexpr int SPREAD_MMA_CTAS_PER_SM = 2;
 
 constexpr int SP_CH = 512;   // nodes staged per block of a work item (order 1/2: SP_CH or SP_CH / 2)
 
@@ -55,6 +58,11 @@ __device__ __forceinline__ void cp_async_wait_n() {
 __host__ __device__ constexpr size_t sp_stage_bytes(int sp) { return (size_t)sp * (3 * 16 + 2 * 8); }
 // third-order items (spread3_f32): 8 warp runs of 32 nodes, two records each
 constexpr size_t SP3_STAGE_BYTES = 3 * 256 * 32 + 2 * 256 * 8;
+
+// L2 prefetch of bytes (a multiple of 16) at a 16-byte aligned global address
+__device__ __forceinline__ void prefetch_l2_bulk(const void *src, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
@@ -88,30 +96,19 @@ int spread_block_nodes(long long max_grid_bytes) {
     return smem_bound && ctas_for(max_grid_bytes, SP_CH / 2) > ctas_for(max_grid_bytes, SP_CH) ? SP_CH / 2 : SP_CH;
 }
 
-// the tensor-core kernel with STEP-node steps: grid, one ring per warp, item slot
-static size_t spread_mma_smem_bytes(long long max_grid_bytes, int step);
+// the tensor-core kernel: grid, one ring per warp, item slot
+static size_t spread_mma_smem_bytes(long long max_grid_bytes);
 
-int spread_ctas_per_sm(long long max_grid_bytes, bool tc, int step) {
+int spread_ctas_per_sm(long long max_grid_bytes, bool tc) {
     if (tc) {
-        const size_t per = spread_mma_smem_bytes(max_grid_bytes, step) + 1024;
+        const size_t per = spread_mma_smem_bytes(max_grid_bytes) + 1024;
         return (int)std::max<size_t>(1, std::min<size_t>(SPREAD_MMA_CTAS_PER_SM, (size_t)(MAX_SMEM + 1024) / per));
     }
     return ctas_for(max_grid_bytes, spread_block_nodes(max_grid_bytes));
 }
 
-int spread_step_for(const Plan &p) {
-    long long cells = 1;
-    for (int s = 0; s < p.n_terms; ++s) {
-        const Term &T = p.h_terms[s];
-        if (T.order == 2) cells = std::max(cells, (long long)T.n * T.n);
-        if (T.order == 1) cells = std::max(cells, (long long)T.n);
-    }
-    return p.M >= 1000 * cells ? 64 : 32;
-}
-
-int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc,
-                      int step) {
-    const long long resident = (long long)spread_ctas_per_sm(max_grid_bytes, tc, step) * sm_count;
+int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc) {
+    const long long resident = (long long)spread_ctas_per_sm(max_grid_bytes, tc) * sm_count;
     long long K = (3 * resident + std::max(1, n_act_total) - 1) / std::max(1, n_act_total);
     K = std::min<long long>(K, (M + 2047) / 2048);
     K = std::min<long long>(K, kmax);
@@ -542,83 +539,125 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
 
 // ---- Tensor-core cell sums (order 1/2 terms with cell-sorted records) ----
 //
-// For the nodes j of one cell the contributions to its m_row x 8 window are
-//     G[r][k] += sum_j y_j psi_row,r(j) psi_col,k(j),
-// a product A B with A[(k, re/im)][j] = y_j psi_col,k(j) (16 x n) and
-// B[j][r] = psi_row,r(j) (n x 8).  A warp runs mma.m16n8k8 over groups of 8
-// cell-sorted nodes: lane (g, t) = (lane / 4, lane % 4) evaluates column tap g
-// and row tap g of nodes t and t + 4 (the fragment layout of the PTX ISA for
-// tf32 m16n8k8), so weights never leave the registers that feed the tensor
-// core.  Each operand is split x = hi + lo into TF32 parts and the product is
-// hi*hi + hi*lo + lo*hi (relative error near 2^-21); the three products of a
-// group are summed by the tensor core, the groups in FP32 registers.  A
-// group holding nodes of several cells is run once per cell with the other
-// nodes masked; the 16 x 8 accumulator goes to the shared grid by
-// shared-memory additions whenever the cell changes.
+// For the nodes j of one cell the contributions to its window block are
+//     G[r][k] += sum_j y_j psi_row,r(j) psi_col,k(j)   (r < 2 m_row, k < 8).
+// Every tap weight is a degree-7 polynomial in the node's cell offset v, kept
+// in the Chebyshev basis X_i (Window::ch): psi_k = sum_i C[k][i] X_i.  So
+//     G = C_col Mo C_row^T,   Mo[(re/im, i)][l] = sum_j y_j X_i(v_col,j) X_l(v_row,j),
+// and the nodes of a cell only build the 16 x 8 moment matrix Mo: a product
+// A B with A[(re/im, i)][j] = y_j X_i(v_col,j) (16 x n) and B[j][l] =
+// X_l(v_row,j) (n x 8), one mma.m16n8k8 per group of 8 cell-sorted nodes.  A
+// node's 2 x 8 basis values come from one lane (the recurrence: 8 packed FP32
+// operations for both coordinates) through shared memory, where lane (g, t) =
+// (lane / 4, lane % 4) picks up X_g of nodes t and t + 4 (the fragment layout
+// of the PTX ISA for tf32 m16n8k8).  Instead of 16 polynomial evaluations
+// per node (one per lane that holds a tap of it), each node's basis is
+// computed once.  When the cell changes, two more products turn Mo into G,
+// with the contraction index permuted (2t, 2t + 1 -> t, t + 4) so that each
+// D fragment is the next product's operand as it stands, and G goes to the
+// shared grid by shared-memory additions.  Each operand is split x = hi + lo
+// into TF32 parts and a product is hi*hi + hi*lo + lo*hi (relative error near
+// 2^-21); the three products of a group are summed by the tensor core, the
+// groups in FP32 registers.  A group holding nodes of several cells is run
+// once per cell with the other nodes masked.
 
-// Records rec[0, n) of one term for one warp, in steps of STEP nodes (STEP / 8
-// groups of 8 for the tensor core): 32 where cells hold a few hundred nodes,
-// 64 where they hold thousands (half the step overheads; the one-test-per-step
-// fast path below needs the whole step in one cell).  The warp's own rings in
-// shared memory (RING steps of records, YRING steps of values y) are filled by
-// its lanes with cp.async: the records DR steps ahead, the values y[index] DY
-// steps ahead (their addresses come from the records already in the ring).
+// Records rec[0, n) of one term for one warp, in steps of STEP = 32 nodes (4
+// groups of 8 for the tensor core; a step lying in one cell takes one test).
+// The warp's own rings in shared memory (RING steps of records, YRING steps
+// of values y) are filled by its lanes with cp.async: the records DR steps
+// ahead, the values y[index] DY steps ahead (their addresses come from the
+// records already in the ring).  Records PF steps ahead are prefetched into
+// L2 (one bulk prefetch per step), so that the ring's copies find them there.
+// The basis rows X_0..X_7 of the current step follow, XROW words apart
+// (= 8 mod 32: the four rows a half-warp reads lie in distinct banks).
 // Order 1: B = e_0 (the single grid row), exact in TF32.
 template <int STEP>
 struct MmaRing {
-    static constexpr int RING = STEP == 32 ? 4 : 3, YRING = STEP == 32 ? 4 : 2, DR = STEP == 32 ? 3 : 2, DY = 1;
-    static constexpr size_t REC_BYTES = (size_t)RING * STEP * 16;           // float4 records
-    static constexpr size_t BYTES = REC_BYTES + (size_t)YRING * STEP * 8;   // + float2 values, per warp
-    static_assert(DY < DR && DR < RING && DY < YRING && STEP % 32 == 0, "ring depths");
+    // records DR = DY + 2 steps ahead: the wait for the records that address
+    // step i + DY's values leaves the values of step i + DY - 1 in flight
+    static constexpr int RING = 5, YRING = 4, DR = 4, DY = 2, PF = 7;   // PF: L2 prefetch distance
+    static constexpr int XROW = 2 * STEP + 8;   // words per basis row (STEP float2 + pad)
+    static constexpr size_t REC_BYTES = (size_t)RING * STEP * 16;                    // float4 records
+    static constexpr size_t X_OFF = REC_BYTES + (size_t)YRING * STEP * 8;            // + float2 values
+    static constexpr size_t BYTES = X_OFF + (size_t)NCOEF * XROW * 4;                // + basis rows, per warp
+    static_assert(DY < DR && DR < RING && DY < YRING && STEP % 32 == 0 && XROW % 32 == 8, "ring layout");
 };
 
-__host__ __device__ constexpr size_t mma_ring_bytes(int step) {
-    return step == 64 ? MmaRing<64>::BYTES : MmaRing<32>::BYTES;
+constexpr int MMA_STEP = 32;   // nodes per ring step of the order-1/2 tensor-core spread
+
+static size_t spread_mma_smem_bytes(long long max_grid_bytes) {
+    return (size_t)max_grid_bytes + MmaRing<MMA_STEP>::BYTES * (SPREAD_MMA_THREADS / 32) + 16;
 }
 
-static size_t spread_mma_smem_bytes(long long max_grid_bytes, int step) {
-    return (size_t)max_grid_bytes + mma_ring_bytes(step) * (SPREAD_THREADS / 32) + 16;
-}
+// Per-lane window coefficients of the two products that turn Mo into G, split
+// into TF32 parts: the row window's C_row[g][2t], C_row[g][2t + 1] (zero for
+// g >= 2 m_row; order 1: e_0 e_0^T) and the column window's C_col[g][2t],
+// C_col[g][2t + 1].
+struct MomentCoef {
+    unsigned rh0, rl0, rh1, rl1;
+    unsigned ch0, cl0, ch1, cl1;
+};
 
-template <int MR, bool ORD2, int MMA_STEP>
+template <int MR, bool ORD2>
 __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, const float2 *__restrict__ y, int n,
-                                               float2 *S, int stride, const f32x2 rcp[NCOEF], float4 *rring,
-                                               float2 *yring) {
+                                               float2 *S, int stride, const MomentCoef &C, float4 *rring,
+                                               float2 *yring, float2 *xs) {
     using R = MmaRing<MMA_STEP>;
     constexpr unsigned MMA_RING = R::RING, MMA_YRING = R::YRING;
-    constexpr int MMA_DR = R::DR, MMA_DY = R::DY;
+    constexpr int MMA_DR = R::DR, MMA_DY = R::DY, XR = R::XROW / 2;   // basis row stride in float2
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int ns = (n + MMA_STEP - 1) / MMA_STEP;
     int cur = -1;   // grid offset of the cell being summed
     float d[4] = {0.f, 0.f, 0.f, 0.f};
-    // d = (re row 2t, re row 2t + 1, im row 2t, im row 2t + 1) of column g
+    // d = Mo (re i = g, l = 2t), (re g, 2t + 1), (im g, 2t), (im g, 2t + 1)
     auto flush = [&]() {
-        float *c = (float *)(S + cur + g);
-        if (ORD2) {
-            if (2 * t < 2 * MR) {
-                red_add(c + 4 * t * stride, d[0]);
-                red_add(c + 4 * t * stride + 1, d[2]);
-                red_add(c + (4 * t + 2) * stride, d[1]);
-                red_add(c + (4 * t + 2) * stride + 1, d[3]);
-            }
-        } else if (t == 0) {
-            red_add(c, d[0]);
-            red_add(c + 1, d[2]);
+        // Q_x[j][i] = sum_l C_row[j][l] Mo_x[i][l]: A = C_row (rows 8..15 zero),
+        // B[k][i] = Mo_x[i][l(k)] with l(t) = 2t, l(t + 4) = 2t + 1
+        unsigned mh[4], ml[4];
+        split_tf32_x2(pk2(d[0], d[1]), mh[0], ml[0], mh[1], ml[1]);
+        split_tf32_x2(pk2(d[2], d[3]), mh[2], ml[2], mh[3], ml[3]);
+        const unsigned ah[4] = {C.rh0, 0u, C.rh1, 0u}, al[4] = {C.rl0, 0u, C.rl1, 0u};
+        float qr[4] = {0.f, 0.f, 0.f, 0.f}, qi[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_tf32(qr, al, mh[0], mh[1]);
+        mma_tf32(qr, ah, ml[0], ml[1]);
+        mma_tf32(qr, ah, mh[0], mh[1]);
+        mma_tf32(qi, al, mh[2], mh[3]);
+        mma_tf32(qi, ah, ml[2], ml[3]);
+        mma_tf32(qi, ah, mh[2], mh[3]);
+        // q = Q_x[j = g][i = 2t], Q_x[g][2t + 1] (entries 2, 3: zero rows).
+        // G_x^T[j][k] = sum_i Q_x[j][i] C_col[k][i]: A[(x, j)][k'] = Q_x[j][i(k')],
+        // B[k'][k] = C_col[k][i(k')]
+        unsigned qh[4], ql[4];
+        split_tf32_x2(pk2(qr[0], qi[0]), qh[0], ql[0], qh[1], ql[1]);
+        split_tf32_x2(pk2(qr[1], qi[1]), qh[2], ql[2], qh[3], ql[3]);
+        float G[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_tf32(G, ql, C.ch0, C.ch1);
+        mma_tf32(G, qh, C.cl0, C.cl1);
+        mma_tf32(G, qh, C.ch0, C.ch1);
+        // G = (re, row tap g, column tap 2t), (re, g, 2t + 1), (im, g, 2t), (im, g, 2t + 1)
+        if (ORD2 ? g < 2 * MR : g == 0) {
+            float *c = (float *)(S + cur + g * stride + 2 * t);
+            red_add(c, G[0]);
+            red_add(c + 1, G[2]);
+            red_add(c + 2, G[1]);
+            red_add(c + 3, G[3]);
         }
         d[0] = d[1] = d[2] = d[3] = 0.f;
     };
-    // tensor-core products of one group added to e (hi*lo terms first)
-    auto group_mma = [&](float (&e)[4], float a0, float a1, float a2, float a3, unsigned bh0, unsigned bl0,
-                         unsigned bh1, unsigned bl1) {
+    // tensor-core products of one group added to e (hi*lo terms first); a01 =
+    // (A[g][t], A[g + 8][t]), a23 = (A[g][t + 4], A[g + 8][t + 4])
+    auto group_mma = [&](float (&e)[4], f32x2 a01, f32x2 a23, unsigned bh0, unsigned bl0, unsigned bh1,
+                         unsigned bl1) {
         unsigned ah[4], al[4];
-        split_tf32(a0, ah[0], al[0]);
-        split_tf32(a1, ah[1], al[1]);
-        split_tf32(a2, ah[2], al[2]);
-        split_tf32(a3, ah[3], al[3]);
+        split_tf32_x2(a01, ah[0], al[0], ah[1], al[1]);
+        split_tf32_x2(a23, ah[2], al[2], ah[3], al[3]);
         mma_tf32(e, al, bh0, bh1);
         if (ORD2) mma_tf32(e, ah, bl0, bl1);
         mma_tf32(e, ah, bh0, bh1);
     };
+    // basis row 0 is X_0 = 1 for every node
+#pragma unroll
+    for (int u = lane; u < MMA_STEP; u += 32) xs[u] = make_float2(1.f, 1.f);
     // A fresh tensor-core sum per step (at most eight groups), added to d in
     // FP32 with rounding to nearest: the tensor core's own accumulation is
     // not rounded to nearest, and its bias would grow with the cell's node
@@ -627,7 +666,10 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         // iteration i commits one cp.async group: the records of step
         // i + MMA_DR and the values of step i + MMA_DY; steps i < 0 fill the ring
         {
-            const int qr = i + MMA_DR, qy = i + MMA_DY;
+            const int qr = i + MMA_DR, qy = i + MMA_DY, qp = i + R::PF;
+            // the records of step qp into L2 (whole records of the run only)
+            if (lane == 0 && qp < ns && qp >= MMA_DR)
+                prefetch_l2_bulk(rec + MMA_STEP * qp, 16u * (unsigned)min(MMA_STEP, n - MMA_STEP * qp));
             if (qr < ns)
 #pragma unroll
                 for (int u = lane; u < MMA_STEP; u += 32)
@@ -645,37 +687,74 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         cp_async_commit();
         if (i < 0) continue;
         cp_async_wait_n<MMA_DY>();   // values of step i (and its records) have landed
-        __syncwarp();
-        float e[4] = {0.f, 0.f, 0.f, 0.f};
+        const int sl0 = ((unsigned)i % MMA_RING) * MMA_STEP, yl0 = ((unsigned)i % MMA_YRING) * MMA_STEP;
+        // basis values X_1..X_7 of the step's nodes, (row, column) coordinate
+        // pairs, from the lane that loaded the node's record: X_{k+1} =
+        // X_{k-1} + (-1)^k 2 v X_k
+#pragma unroll
+        for (int u = lane; u < MMA_STEP; u += 32) {
+            const float4 r = rring[sl0 + u];
+            const f32x2 v = pk2(r.x, r.y);
+            const f32x2 up = mul2(v, pk2(2.f, 2.f)), um = mul2(v, pk2(-2.f, -2.f));
+            f32x2 xm = pk2(1.f, 1.f), x = v;
+            f32x2 *row = (f32x2 *)(xs + u);
+            row[XR] = x;
+#pragma unroll
+            for (int k = 2; k < NCOEF; ++k) {
+                const f32x2 xn = fma2((k & 1) ? up : um, x, xm);
+                row[k * XR] = xn;
+                xm = x;
+                x = xn;
+            }
+        }
+        __syncwarp();   // records, values and basis rows of step i visible to the warp
+        // two tensor-core sums (even and odd groups), so that two chains of
+        // dependent products are in flight
+        float e[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
         const bool whole = MMA_STEP * (i + 1) <= n;   // no group of this step runs past the end
         // the records are in cell order: if the step's first and last nodes lie in
         // the cell being summed, all of them do (the same test in every lane)
-        const int sl0 = ((unsigned)i % MMA_RING) * MMA_STEP, yl0 = ((unsigned)i % MMA_YRING) * MMA_STEP;
         const bool step_in_cell = whole && __float_as_int(rring[sl0].z) == cur &&
                                   __float_as_int(rring[sl0 + MMA_STEP - 1].z) == cur;
-#pragma unroll
-        for (int h = 0; h < MMA_STEP / 8; ++h) {
-            const int base = MMA_STEP * i + 8 * h;   // first node of this group (may be past the end)
-            const int sl = sl0 + 8 * h, yl = yl0 + 8 * h;
-            const float4 r0 = rring[sl + t], r1 = rring[sl + t + 4];
-            const float2 y0 = yring[yl + t], y1 = yring[yl + t + 4];
-            // row and column weights of nodes t, t + 4: one packed Horner per node
-            float wr0, wc0, wr1, wc1;
-            horner8_x2(rcp, r0.x, r0.y, wr0, wc0);
-            horner8_x2(rcp, r1.x, r1.y, wr1, wc1);
+        // operands of group h: A = y times X_g of the column coordinate of nodes
+        // t, t + 4, B = X_g of their row coordinate
+        struct GroupOp {
+            f32x2 a01, a23;
             unsigned bh0, bl0, bh1, bl1;
+        };
+        auto operands = [&](int h) {
+            GroupOp o;
+            const float2 x0 = xs[g * XR + 8 * h + t], x1 = xs[g * XR + 8 * h + t + 4];
+            const float2 y0 = yring[yl0 + 8 * h + t], y1 = yring[yl0 + 8 * h + t + 4];
+            o.a01 = pk2(y0.x * x0.y, y0.y * x0.y);
+            o.a23 = pk2(y1.x * x1.y, y1.y * x1.y);
             if (ORD2) {
-                split_tf32(g < 2 * MR ? wr0 : 0.f, bh0, bl0);
-                split_tf32(g < 2 * MR ? wr1 : 0.f, bh1, bl1);
+                split_tf32_x2(pk2(x0.x, x1.x), o.bh0, o.bl0, o.bh1, o.bl1);
             } else {
-                bh0 = bh1 = g == 0 ? 0x3f800000u : 0u;
-                bl0 = bl1 = 0u;
+                o.bh0 = o.bh1 = g == 0 ? 0x3f800000u : 0u;
+                o.bl0 = o.bl1 = 0u;
             }
-            const int off0 = __float_as_int(r0.z), off1 = __float_as_int(r1.z);
-            if (step_in_cell || __all_sync(0xffffffffu, (whole || base + 8 <= n) && off0 == cur && off1 == cur)) {
-                // the whole group lies in the cell being summed
-                group_mma(e, y0.x * wc0, y0.y * wc0, y1.x * wc1, y1.y * wc1, bh0, bl0, bh1, bl1);
-            } else {
+            return o;
+        };
+        if (step_in_cell) {
+            // every group of the step lies in the cell being summed
+#pragma unroll
+            for (int h = 0; h < MMA_STEP / 8; ++h) {
+                const GroupOp o = operands(h);
+                group_mma((h & 1) ? e2 : e, o.a01, o.a23, o.bh0, o.bl0, o.bh1, o.bl1);
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < MMA_STEP / 8; ++h) {
+                const int base = MMA_STEP * i + 8 * h;   // first node of this group (may be past the end)
+                const GroupOp o = operands(h);
+                const int off0 = __float_as_int(rring[sl0 + 8 * h + t].z);
+                const int off1 = __float_as_int(rring[sl0 + 8 * h + t + 4].z);
+                if (__all_sync(0xffffffffu, (whole || base + 8 <= n) && off0 == cur && off1 == cur)) {
+                    // the whole group lies in the cell being summed
+                    group_mma((h & 1) ? e2 : e, o.a01, o.a23, o.bh0, o.bl0, o.bh1, o.bl1);
+                    continue;
+                }
                 // past the end the ring holds the last record again: masked here
                 bool p0 = base + t < n, p1 = base + t + 4 < n;   // nodes t, t + 4 not yet added
                 for (;;) {
@@ -688,22 +767,22 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
                     if (oc != cur) {
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            d[q] += e[q];
-                            e[q] = 0.f;
+                            d[q] += e[q] + e2[q];
+                            e[q] = e2[q] = 0.f;
                         }
                         if (cur >= 0) flush();
                         cur = oc;
                     }
-                    group_mma(e, e0 ? y0.x * wc0 : 0.f, e0 ? y0.y * wc0 : 0.f, e1 ? y1.x * wc1 : 0.f,
-                              e1 ? y1.y * wc1 : 0.f, bh0, bl0, bh1, bl1);
+                    group_mma(e, e0 ? o.a01 : pk2(0.f, 0.f), e1 ? o.a23 : pk2(0.f, 0.f), o.bh0, o.bl0, o.bh1,
+                              o.bl1);
                     p0 = p0 && !e0;
                     p1 = p1 && !e1;
                 }
             }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) d[q] += e[q];
-        __syncwarp();   // ring slot i is read before a later iteration refills it
+        for (int q = 0; q < 4; ++q) d[q] += e[q] + e2[q];
+        __syncwarp();   // ring slot i and the basis rows are read before later iterations refill them
     }
     cp_async_wait0();
     if (cur >= 0) flush();
@@ -711,31 +790,39 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
 
 // Sorted item of order 1/2 on the tensor cores: the item's records are cut
 // into 8 contiguous runs (multiples of 8 nodes), one per warp.
-template <int MR, int STEP>
+template <int MR>
 __device__ __forceinline__ void spread_mma_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                 long long j0, long long j1, float2 *S, unsigned char *stg_raw) {
-    const int warp = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
-    // coefficient pairs (row tap g, column tap g) for the packed Horner; order-1
-    // terms have no row window (their row weight is unused)
-    f32x2 rcp[NCOEF];
+    const int warp = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+    MomentCoef C;
     {
-        const float *cs = P.windows[T.wc].c[g];
-        const float *rs = P.windows[T.wr].c[min(g, 2 * MR - 1)];
-#pragma unroll
-        for (int q = 0; q < NCOEF; ++q) rcp[q] = pk2(__ldg(rs + q), __ldg(cs + q));
+        float r0, r1;
+        if (T.order == 2) {
+            const float *rs = P.windows[T.wr].ch[min(g, 2 * MR - 1)];
+            r0 = g < 2 * MR ? __ldg(rs + 2 * t) : 0.f;
+            r1 = g < 2 * MR ? __ldg(rs + 2 * t + 1) : 0.f;
+        } else {
+            r0 = g == 0 && t == 0 ? 1.f : 0.f;
+            r1 = 0.f;
+        }
+        split_tf32_x2(pk2(r0, r1), C.rh0, C.rl0, C.rh1, C.rl1);
+        const float *cs = P.windows[T.wc].ch[g];
+        split_tf32_x2(pk2(__ldg(cs + 2 * t), __ldg(cs + 2 * t + 1)), C.ch0, C.cl0, C.ch1, C.cl1);
     }
-    constexpr int NW = SPREAD_THREADS / 32;
+    constexpr int NW = SPREAD_MMA_THREADS / 32;
     const long long len = j1 - j0, per = (len + 8 * NW - 1) / (8 * NW) * 8;
     const long long a = j0 + warp * per, b = min(j1, a + per);
     if (a >= b) return;
     const float4 *rec = P.srec + (long long)T.sort_slot * P.M + a;
-    unsigned char *ring = stg_raw + warp * MmaRing<STEP>::BYTES;
+    using R = MmaRing<MMA_STEP>;
+    unsigned char *ring = stg_raw + warp * R::BYTES;
     float4 *rring = (float4 *)ring;
-    float2 *yring = (float2 *)(ring + MmaRing<STEP>::REC_BYTES);
+    float2 *yring = (float2 *)(ring + R::REC_BYTES);
+    float2 *xs = (float2 *)(ring + R::X_OFF);
     if (T.order == 2)
-        spread_mma_run<MR, true, STEP>(rec, y, (int)(b - a), S, T.stride, rcp, rring, yring);
+        spread_mma_run<MR, true>(rec, y, (int)(b - a), S, T.stride, C, rring, yring, xs);
     else
-        spread_mma_run<MR, false, STEP>(rec, y, (int)(b - a), S, T.stride, rcp, rring, yring);
+        spread_mma_run<MR, false>(rec, y, (int)(b - a), S, T.stride, C, rring, yring, xs);
 }
 
 // ---- Third-order cell sums on the tensor cores ----
@@ -857,18 +944,16 @@ __device__ __forceinline__ void spread3_mma_run(const float4 *__restrict__ rec, 
                     }
                 }
                 unsigned ah[4], al[4];
-                split_tf32(e0 ? y0.x * wc0 : 0.f, ah[0], al[0]);
-                split_tf32(e0 ? y0.y * wc0 : 0.f, ah[1], al[1]);
-                split_tf32(e1 ? y1.x * wc1 : 0.f, ah[2], al[2]);
-                split_tf32(e1 ? y1.y * wc1 : 0.f, ah[3], al[3]);
+                split_tf32_x2(e0 ? mul2(pk2(y0.x, y0.y), pk2(wc0, wc0)) : pk2(0.f, 0.f), ah[0], al[0], ah[1], al[1]);
+                split_tf32_x2(e1 ? mul2(pk2(y1.x, y1.y), pk2(wc1, wc1)) : pk2(0.f, 0.f), ah[2], al[2], ah[3], al[3]);
+                const f32x2 wb = pk2(wb0, wb1);
 #pragma unroll
                 for (int a = 0; a < 2 * MR; ++a) {
                     // first coordinate's tap a of nodes t, t + 4 from lane (a, t)
                     const float va0 = __shfl_sync(0xffffffffu, wa0, 4 * a + t);
                     const float va1 = __shfl_sync(0xffffffffu, wa1, 4 * a + t);
                     unsigned bh0, bl0, bh1, bl1;
-                    split_tf32(va0 * wb0, bh0, bl0);
-                    split_tf32(va1 * wb1, bh1, bl1);
+                    split_tf32_x2(mul2(pk2(va0, va1), wb), bh0, bl0, bh1, bl1);
                     mma_tf32(d[a], al, bh0, bh1);
                     mma_tf32(d[a], ah, bl0, bl1);
                     mma_tf32(d[a], ah, bh0, bh1);
@@ -921,7 +1006,7 @@ __device__ __forceinline__ void spread3_mma_item(const DevPlan &P, const Term &T
 // items from a global counter.
 // KIND: SK_STAGED (order 1/2 on the CUDA cores), SK_ORDER3, SK_MMA (order 1/2
 // with records on the tensor cores; no staging area)
-template <int MR, typename G, int KIND, int SP>
+template <int MR, typename G, int KIND, int SP, int NT = SPREAD_THREADS>
 __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchArgs &B,
                                              const float2 *__restrict__ y_base, int item_begin, int item_end,
                                              int *counter, long long max_grid_bytes) {
@@ -929,8 +1014,8 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
     float2 *S = (float2 *)smem_raw;
     unsigned char *stg_raw = smem_raw + max_grid_bytes;
     constexpr bool O3 = KIND == SK_ORDER3;
-    int &s_item = *(int *)(stg_raw + (KIND == SK_MMA    ? mma_ring_bytes(SP) * (SPREAD_THREADS / 32)
-                                      : KIND == SK_MMA3 ? MMA3_RING_BYTES * (SPREAD_THREADS / 32)
+    int &s_item = *(int *)(stg_raw + (KIND == SK_MMA    ? MmaRing<MMA_STEP>::BYTES * (NT / 32)
+                                      : KIND == SK_MMA3 ? MMA3_RING_BYTES * (NT / 32)
                                       : O3              ? SP3_STAGE_BYTES
                                                         : sp_stage_bytes(SP)));
     const int tid = threadIdx.x;
@@ -949,7 +1034,7 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
         const long long j0 = M * itm.z / itm.w, j1 = M * (itm.z + 1) / itm.w;
         const long long elems = T.grid_bytes / (long long)sizeof(G);   // shared copy is FP32 complex
         float4 *S4 = (float4 *)S;
-        for (long long e = tid; e < elems / 2; e += SPREAD_THREADS) S4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (long long e = tid; e < elems / 2; e += NT) S4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 *y = y_base + P.vec_node_off;
         // window coefficients of this lane: row tap k for lanes r = 1 of an
         // order-2 term (see node_weights), column tap k otherwise
@@ -962,7 +1047,7 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
         }
         __syncthreads();   // grid zeroed before any addition
         if constexpr (KIND == SK_MMA) {
-            spread_mma_item<MR, SP>(P, T, y, j0, j1, S, stg_raw);
+            spread_mma_item<MR>(P, T, y, j0, j1, S, stg_raw);
         } else if constexpr (KIND == SK_MMA3) {
             spread3_mma_item<MR>(P, T, y, j0, j1, S, stg_raw);
         } else if constexpr (O3) {
@@ -979,10 +1064,10 @@ __device__ __forceinline__ void spread_items(const DevPlan &single, const BatchA
         __syncthreads();
         if constexpr (std::is_same<G, float2>::value) {
             float4 *dst = (float4 *)(P.partials + (long long)itm.z * P.grid_elems + T.grid_off);
-            for (long long e = tid; e < elems / 2; e += SPREAD_THREADS) dst[e] = S4[e];
+            for (long long e = tid; e < elems / 2; e += NT) dst[e] = S4[e];
         } else {
             G *dst = (G *)P.partials + (long long)itm.z * P.grid_elems + T.grid_off;
-            for (long long e = tid; e < elems; e += SPREAD_THREADS) dst[e] = GridEl<G>::store(S[e].x, S[e].y);
+            for (long long e = tid; e < elems; e += NT) dst[e] = GridEl<G>::store(S[e].x, S[e].y);
         }
         __syncthreads();
     }
@@ -999,11 +1084,12 @@ spread_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int i
 
 // order-1/2 items of plans with cell-sorted records, on the tensor cores, in
 // steps of STEP nodes
-template <int MR, typename G, int STEP>
-__global__ void __launch_bounds__(SPREAD_THREADS, SPREAD_MMA_CTAS_PER_SM)
+template <int MR, typename G>
+__global__ void __launch_bounds__(SPREAD_MMA_THREADS, SPREAD_MMA_CTAS_PER_SM)
 spread_mma_f32(DevPlan single, BatchArgs B, const float2 *__restrict__ y_base, int item_begin, int item_end,
                int *counter, long long max_grid_bytes) {
-    spread_items<MR, G, SK_MMA, STEP>(single, B, y_base, item_begin, item_end, counter, max_grid_bytes);
+    spread_items<MR, G, SK_MMA, MMA_STEP, SPREAD_MMA_THREADS>(single, B, y_base, item_begin, item_end, counter,
+                                                              max_grid_bytes);
 }
 
 // third-order items of plans with cell-sorted records, on the tensor cores
@@ -1259,10 +1345,8 @@ static void adjoint_attrs() {
         cudaFuncSetAttribute(spread3_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_mma_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_mma_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        cudaFuncSetAttribute(spread_mma_f32<3, G, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        cudaFuncSetAttribute(spread_mma_f32<4, G, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        cudaFuncSetAttribute(spread_mma_f32<3, G, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
-        cudaFuncSetAttribute(spread_mma_f32<4, G, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_mma_f32<3, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        cudaFuncSetAttribute(spread_mma_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
         cudaFuncSetAttribute(spread3_f32<4, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
     });
 }
@@ -1273,11 +1357,11 @@ template <typename G>
 static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P,
                             const float2 *y, float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks,
                             int mr, long long sgrid, int max_fft_elems, int sm_count, long long max_grid_elems,
-                            bool tc, int mma_step) {
+                            bool tc) {
     adjoint_attrs<G>();
     const int sp = spread_block_nodes(sgrid);
     const size_t ssm = spread_smem_bytes(sgrid, false, sp), ssm3 = spread_smem_bytes(sgrid, true, sp);
-    const int per_sm = spread_ctas_per_sm(sgrid, false, mma_step);
+    const int per_sm = spread_ctas_per_sm(sgrid, false);
     if (prof) stage_begin(*prof, ST_SPREAD);
     cudaMemsetAsync(counter, 0, 2 * sizeof(int), st);
     if (n_items3 > 0 && tc) {
@@ -1294,13 +1378,12 @@ static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const
             spread3_f32<4, G><<<c3, SPREAD_THREADS, ssm3, st>>>(v, B, y, 0, n_items3, counter, sgrid);
     }
     if (n_items > n_items3 && tc) {
-        const size_t sm = spread_mma_smem_bytes(sgrid, mma_step);
+        const size_t sm = spread_mma_smem_bytes(sgrid);
         const int per = (int)std::max<size_t>(
             1, std::min<size_t>(SPREAD_MMA_CTAS_PER_SM, (size_t)(MAX_SMEM + 1024) / (sm + 1024)));
         const int c = std::max(1, std::min(n_items - n_items3, per * sm_count));
-        auto k = mr <= 3 ? (mma_step == 64 ? spread_mma_f32<3, G, 64> : spread_mma_f32<3, G, 32>)
-                         : (mma_step == 64 ? spread_mma_f32<4, G, 64> : spread_mma_f32<4, G, 32>);
-        k<<<c, SPREAD_THREADS, sm, st>>>(v, B, y, n_items3, n_items, counter + 1, sgrid);
+        auto k = mr <= 3 ? spread_mma_f32<3, G> : spread_mma_f32<4, G>;
+        k<<<c, SPREAD_MMA_THREADS, sm, st>>>(v, B, y, n_items3, n_items, counter + 1, sgrid);
     } else if (n_items > n_items3) {
         const int c = std::max(1, std::min(n_items - n_items3, per_sm * sm_count));
         auto k = mr <= 3 ? (sp == SP_CH ? spread_f32<3, G, SP_CH> : spread_f32<3, G, SP_CH / 2>)
@@ -1323,7 +1406,7 @@ static void adjoint_kernels(Plan *prof, cudaStream_t st, const DevPlan &v, const
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
                    float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks, int mr,
                    long long max_grid_bytes, int max_fft_elems, int sm_count, long long max_grid_elems,
-                   bool any_empty, double2 *scratch, int prec, bool tc, int mma_step) {
+                   bool any_empty, double2 *scratch, int prec, bool tc) {
     if (any_empty) {
         const int nb = 256;
         if (prof) stage_begin(*prof, ST_SUMY);
@@ -1334,13 +1417,13 @@ int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArg
     if (n_blocks == 0) return cuda_status(cudaGetLastError());
     if (prec == ANOVA_PREC_F16)
         adjoint_kernels<__half2>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
-                                 2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc, mma_step);
+                                 2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc);
     else if (prec == ANOVA_PREC_BF16)
         adjoint_kernels<__nv_bfloat162>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
-                                        2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc, mma_step);
+                                        2 * max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc);
     else
         adjoint_kernels<float2>(prof, st, v, B, P, y, fhat, n_items, n_items3, counter, n_blocks, mr,
-                                max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc, mma_step);
+                                max_grid_bytes, max_fft_elems, sm_count, max_grid_elems, tc);
     return cuda_status(cudaGetLastError());
 }
 
@@ -1355,13 +1438,9 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat) {
     }
     int mr = 3;
     for (int s = 0; s < p.n_terms; ++s) mr = p.h_terms[s].mr > 0 ? p.h_terms[s].mr : mr;
-    // spread steps of 64 nodes where the order-1/2 cells hold a thousand nodes
-    // or more on average (d = 30 workload: 1950), else 32 (d = 20: 244); the
-    // plan chose it, and sized its node chunks for it
-    const int mma_step = p.mma_step == 64 ? 64 : 32;
     return adjoint_launch(&p, p.stream, v, B, 1, y, fhat, p.n_items, p.n_items3, p.counter, p.n_act, mr,
                           p.max_grid_bytes, p.max_fft_elems, p.sm_count, p.grid_elems, p.n_empty > 0,
-                          (double2 *)p.scratch, p.precision, p.srec && p.cell_tc, mma_step);
+                          (double2 *)p.scratch, p.precision, p.srec && p.cell_tc);
 }
 
 }  // namespace agft

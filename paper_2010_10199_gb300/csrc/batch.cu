@@ -96,7 +96,7 @@ static int batch_trafo(Batch &b, cudaStream_t st, const float2 *fhat, float2 *f)
 static int batch_adjoint(Batch &b, cudaStream_t st, const float2 *y, float2 *fhat) {
     return adjoint_launch(nullptr, st, b.views[0], b.args, b.P, y, fhat, b.n_items, b.n_items3, b.counter,
                           b.n_blocks, b.mr, b.max_grid_bytes, b.max_fft, b.sm_count, b.max_grid_elems, b.any_empty,
-                          b.scratch, ANOVA_PREC_F32, b.cell_tc, 32);
+                          b.scratch, ANOVA_PREC_F32, b.cell_tc);
 }
 
 // ----------------------------------------------------- segmented kernels --
@@ -302,7 +302,7 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
     std::vector<int> Ks(n_problems);
     for (int p = 0; p < n_problems; ++p) {
         Plan &pl = b->plans[p]->p;
-        Ks[p] = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count, b->cell_tc, 32);
+        Ks[p] = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count, b->cell_tc);
         b->views[p].spread_chunks = Ks[p];
     }
     // third-order items of every problem first, then the others

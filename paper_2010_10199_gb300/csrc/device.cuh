@@ -73,6 +73,36 @@ __host__ __device__ __forceinline__ double cos_amp(int s) {
     return s == 1 ? 0.70710678118654752440 : s == 2 ? 0.5 : 0.35355339059327376220;
 }
 
+// ---- packed FP32 pairs ----
+//
+// sm_100-class GPUs execute two FP32 fused multiply-adds of one lane in one
+// instruction (fma.rn.f32x2 on a 64-bit register pair) at the same FMA rate,
+// which halves the issue slots of independent pairs of operations; each half
+// rounds exactly as the scalar fmaf does.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // ---------------------------------------------------------------- windows --
 
 // ---- TF32 tensor-core products with FP32-level accuracy ----
@@ -91,6 +121,29 @@ __host__ __device__ __forceinline__ double cos_amp(int s) {
 __device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
     hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
     lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+// The same split for two values at once in three packed operations (instead
+// of two integer and one FP32 operation per value): c = fl(x + 2^13 x) =
+// fl(8193 x), hi = c - 2^13 x (exact: one fma), lo = x - hi (exact: the
+// rounding error of c).  ulp(c) >= 2^13 ulp(x), so hi is a multiple of
+// 2^13 ulp(x) no larger than 2 |x| in magnitude: at most 11 significant
+// bits, exact in TF32.  |lo| <= ulp(c) / 2 <= 2^-10 |x| (2^-11 |x| unless the
+// mantissa of x is within 2^-13 of 2), and the tensor core's truncation of lo
+// errs by less than 2^-20 |x|.  Finite |x| below 2^114 (c must not overflow).
+// Written with fma rather than as Veltkamp's c - (c - x): in a probe of the
+// packed subtraction form the compiled code returned hi = x.
+__device__ __forceinline__ void split_tf32_x2(f32x2 x, unsigned &h0, unsigned &l0, unsigned &h1, unsigned &l1) {
+    const f32x2 c = fma2(x, pk2(8192.0f, 8192.0f), x);
+    const f32x2 hi = fma2(x, pk2(-8192.0f, -8192.0f), c);
+    const f32x2 lo = sub2(x, hi);
+    float a, b;
+    upk2(hi, a, b);
+    h0 = __float_as_uint(a);
+    h1 = __float_as_uint(b);
+    upk2(lo, a, b);
+    l0 = __float_as_uint(a);
+    l1 = __float_as_uint(b);
 }
 
 // d += a b on the tensor core (mma.m16n8k8, TF32 operands, FP32 sums)
@@ -119,25 +172,6 @@ __device__ __forceinline__ void horner8_pm(const float c[NCOEF], float v, float 
     const float o = fmaf(fmaf(fmaf(c[7], v2, c[5]), v2, c[3]), v2, c[1]);
     p = fmaf(v, o, e);
     m = fmaf(-v, o, e);
-}
-
-// ---- packed FP32 pairs ----
-//
-// sm_100-class GPUs execute two FP32 fused multiply-adds of one lane in one
-// instruction (fma.rn.f32x2 on a 64-bit register pair) at the same FMA rate,
-// which halves the issue slots of independent pairs of operations; each half
-// rounds exactly as the scalar fmaf does.
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pk2(float a, float b) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(f32x2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
 }
 
 // Two degree-7 polynomials at once: coefficient pairs cp[i] = (a_i, b_i),

@@ -33,8 +33,12 @@ constexpr int MAX_SMEM = 227 * 1024;
 // grid position t = n x sits at grid index floor(t) - m + 1 + j and has weight
 // psi(tau + m - 1 - j) / psi(0), tau = t - floor(t); the weight is stored as a
 // degree-7 polynomial in v = 2 tau - 1 (Chebyshev interpolation, monomial form).
+// The same polynomial in the Chebyshev basis: tap j = sum_i ch[j][i] X_i(v) with
+// X_i = s_i T_i, signs s = (+, +, -, -, +, +, -, -), which turn the three-term
+// recurrence into X_{i+1} = X_{i-1} + (-1)^i 2 v X_i (one fma per step).
 struct Window {
     float c[2 * MAXM][NCOEF];
+    float ch[2 * MAXM][NCOEF];
     int m;
     float b;          // shape parameter pi (2 - 1/sigma)
     float inv_psi0;   // 1 / psi(0)
@@ -203,7 +207,6 @@ struct Plan {
     int *counter;           // work-queue counter of the spread
     float4 *srec;           // cell-sorted node records (null: none), n_sorted slots of M
     bool cell_tc;           // order-1/2 spread of sorted records on the tensor cores
-    int mma_step;           // ring step (nodes) of that spread, see spread_step_for
     int n_sorted;
     unsigned long long *facc;   // sorted forward: fixed-point accumulators [M][2]
     int *fexp;              // and their exponent
@@ -275,7 +278,7 @@ int launch_adjoint_f32(Plan &p, const float2 *y, float2 *fhat);
 int adjoint_launch(Plan *prof, cudaStream_t st, const DevPlan &v, const BatchArgs &B, int P, const float2 *y,
                    float2 *fhat, int n_items, int n_items3, int *counter, int n_blocks, int mr,
                    long long max_grid_bytes, int max_fft_elems, int sm_count, long long max_grid_elems,
-                   bool any_empty, double2 *scratch, int prec, bool tc, int mma_step);
+                   bool any_empty, double2 *scratch, int prec, bool tc);
 size_t spread_smem_bytes(long long max_grid_bytes, bool o3, int sp);
 int spread_block_nodes(long long max_grid_bytes);
 // Sorts the nodes by grid cell for every term with sort_slot >= 0 (sort.cu).
@@ -284,17 +287,12 @@ int sort_nodes_by_cell(Plan &p);
 int build_window_tables_f64(Plan &p);
 int launch_trafo_f64(Plan &p, const double2 *fhat, double2 *f);
 int launch_adjoint_f64(Plan &p, const double2 *y, double2 *fhat);
-// CTAs per SM of the order-1/2 spread kernel (tc: the tensor-core one with
-// `step`-node ring steps)
-int spread_ctas_per_sm(long long max_grid_bytes, bool tc, int step);
-// Ring step of the tensor-core spread for a plan: 64 nodes where its
-// order-1/2 cells hold a thousand nodes or more on average, else 32.
-int spread_step_for(const Plan &p);
+// CTAs per SM of the order-1/2 spread kernel (tc: the tensor-core one)
+int spread_ctas_per_sm(long long max_grid_bytes, bool tc);
 // Node chunks per term for a spread over n_act_total active terms (all
 // problems of a launch) on sm_count SMs: about three items per resident CTA,
 // at most kmax, at least 2048 nodes per chunk.
-int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc,
-                      int step);
+int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc);
 // Appends the spread work items of one problem, K chunks per active term:
 // those of the third-order terms (sel = 3) or of the others, order 2 before
 // order 1 (sel = 0).  Returns the count.

@@ -58,7 +58,7 @@ void window_polys(Window &w, int m, double b) {
     const int P = NCOEF;
     double psi0 = kb_window(0.0, m, b);
     for (int j = 0; j < 2 * MAXM; ++j)
-        for (int i = 0; i < P; ++i) w.c[j][i] = 0.0f;
+        for (int i = 0; i < P; ++i) w.c[j][i] = w.ch[j][i] = 0.0f;
     for (int j = 0; j < 2 * m; ++j) {
         double fv[NCOEF], a[NCOEF];
         for (int i = 0; i < P; ++i) {
@@ -70,6 +70,7 @@ void window_polys(Window &w, int m, double b) {
             double s = 0;
             for (int i = 0; i < P; ++i) s += fv[i] * std::cos(M_PI * k * (i + 0.5) / P);
             a[k] = (k == 0 ? 1.0 : 2.0) * s / P;
+            w.ch[j][k] = (float)(((k >> 1) & 1) ? -a[k] : a[k]);   // s_k a_k
         }
         // sum a_k T_k(v) -> monomials, T_{k+1} = 2 v T_k - T_{k-1}
         double Tm1[NCOEF] = {0}, T0[NCOEF] = {0}, mono[NCOEF] = {0};
@@ -167,7 +168,7 @@ int set_active_terms(Plan &p, const unsigned char *user_mask) {
     p.n_items = 0;
     p.n_items3 = 0;
     if (n == 0) return ANOVA_OK;
-    p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count, p.cell_tc, p.mma_step);
+    p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count, p.cell_tc);
     if (p.h_items) {
         p.n_items3 = append_spread_items(p, 0, p.spread_K, p.h_items, 3);
         p.n_items = p.n_items3 + append_spread_items(p, 0, p.spread_K, p.h_items + p.n_items3, 0);
@@ -634,7 +635,6 @@ static int plan_create(anova_plan_t *out, int d, int64_t M, const void *x_dev, i
                                                           cosine ? 0.5f : 1.0f);
         chk(cudaGetLastError());
     }
-    p.mma_step = spread_step_for(p);
     if (e == cudaSuccess && p.precision == ANOVA_PREC_F64) chk(cuda_err_of(build_window_tables_f64(p)));
     if (e == cudaSuccess) chk(cuda_err_of(sort_nodes_by_cell(p)));
     if (e == cudaSuccess) chk(cuda_err_of(set_active_terms(p, nullptr)));
