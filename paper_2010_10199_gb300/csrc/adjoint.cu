@@ -564,23 +564,29 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
 // Records rec[0, n) of one term for one warp, in steps of STEP = 32 nodes (4
 // groups of 8 for the tensor core; a step lying in one cell takes one test).
 // The warp's own rings in shared memory (RING steps of records, YRING steps
-// of values y) are filled by its lanes with cp.async: the records DR steps
-// ahead, the values y[index] DY steps ahead (their addresses come from the
-// records already in the ring).  Records PF steps ahead are prefetched into
-// L2 (one bulk prefetch per step), so that the ring's copies find them there.
-// The basis rows X_0..X_7 of the current step follow, XROW words apart
-// (= 8 mod 32: the four rows a half-warp reads lie in distinct banks).
+// of values) are filled by its lanes with cp.async, in two groups per step:
+// the records DR steps ahead, then the values DY steps ahead (their
+// addresses come from the records already in the ring; with DR = DY + 1 the
+// wait for those records leaves the previous step's values in flight).
+// Records PF steps ahead are prefetched into L2 (one bulk prefetch per step),
+// so that the ring's copies find them there.  A value y[index] arrives as the
+// aligned 16-byte block that holds it (cp.async.cg: the scattered reads do not
+// allocate L1 lines, whose few hundred per SM would otherwise bound the reads
+// in flight; the block lies within the allocation of y, whose granularity
+// is at least 16 bytes); the lane that computes the node's basis moves the
+// right half to the step's value array.  The basis rows X_0..X_7 of the
+// current step follow, XROW words apart (= 8 mod 32: the four rows a
+// half-warp reads lie in distinct banks), then the step's values.
 // Order 1: B = e_0 (the single grid row), exact in TF32.
 template <int STEP>
 struct MmaRing {
-    // records DR = DY + 2 steps ahead: the wait for the records that address
-    // step i + DY's values leaves the values of step i + DY - 1 in flight
-    static constexpr int RING = 5, YRING = 4, DR = 4, DY = 2, PF = 7;   // PF: L2 prefetch distance
+    static constexpr int RING = 4, YRING = 3, DR = 3, DY = 2, PF = 7;   // PF: L2 prefetch distance
     static constexpr int XROW = 2 * STEP + 8;   // words per basis row (STEP float2 + pad)
     static constexpr size_t REC_BYTES = (size_t)RING * STEP * 16;                    // float4 records
-    static constexpr size_t X_OFF = REC_BYTES + (size_t)YRING * STEP * 8;            // + float2 values
-    static constexpr size_t BYTES = X_OFF + (size_t)NCOEF * XROW * 4;                // + basis rows, per warp
-    static_assert(DY < DR && DR < RING && DY < YRING && STEP % 32 == 0 && XROW % 32 == 8, "ring layout");
+    static constexpr size_t X_OFF = REC_BYTES + (size_t)YRING * STEP * 16;           // + 16-byte value blocks
+    static constexpr size_t YC_OFF = X_OFF + (size_t)NCOEF * XROW * 4;               // + basis rows
+    static constexpr size_t BYTES = YC_OFF + (size_t)STEP * 8;                       // + values, per warp
+    static_assert(DR == DY + 1 && DR < RING && DY < YRING && STEP % 32 == 0 && XROW % 32 == 8, "ring layout");
 };
 
 constexpr int MMA_STEP = 32;   // nodes per ring step of the order-1/2 tensor-core spread
@@ -601,7 +607,7 @@ struct MomentCoef {
 template <int MR, bool ORD2>
 __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, const float2 *__restrict__ y, int n,
                                                float2 *S, int stride, const MomentCoef &C, float4 *rring,
-                                               float2 *yring, float2 *xs) {
+                                               float4 *yring, float2 *xs, float2 *yc) {
     using R = MmaRing<MMA_STEP>;
     constexpr unsigned MMA_RING = R::RING, MMA_YRING = R::YRING;
     constexpr int MMA_DR = R::DR, MMA_DY = R::DY, XR = R::XROW / 2;   // basis row stride in float2
@@ -663,37 +669,41 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
     // not rounded to nearest, and its bias would grow with the cell's node
     // count.
     for (int i = -MMA_DR; i < ns; ++i) {
-        // iteration i commits one cp.async group: the records of step
-        // i + MMA_DR and the values of step i + MMA_DY; steps i < 0 fill the ring
-        {
-            const int qr = i + MMA_DR, qy = i + MMA_DY, qp = i + R::PF;
-            // the records of step qp into L2 (whole records of the run only)
-            if (lane == 0 && qp < ns && qp >= MMA_DR)
-                prefetch_l2_bulk(rec + MMA_STEP * qp, 16u * (unsigned)min(MMA_STEP, n - MMA_STEP * qp));
-            if (qr < ns)
+        // iteration i commits two cp.async groups: A(i), the records of step
+        // i + MMA_DR, and B(i), the values of step i + MMA_DY; steps i < 0 fill
+        // the rings
+        const int qr = i + MMA_DR, qy = i + MMA_DY, qp = i + R::PF;
+        // the records of step qp into L2 (whole records of the run only)
+        if (lane == 0 && qp < ns && qp >= MMA_DR)
+            prefetch_l2_bulk(rec + MMA_STEP * qp, 16u * (unsigned)min(MMA_STEP, n - MMA_STEP * qp));
+        if (qr < ns)
 #pragma unroll
-                for (int u = lane; u < MMA_STEP; u += 32)
-                    cp_async16(&rring[((unsigned)qr % MMA_RING) * MMA_STEP + u], rec + min(MMA_STEP * qr + u, n - 1));
-            if (qy >= 0 && qy < ns) {
-                // the records of step qy were committed MMA_DR - MMA_DY iterations ago
-                cp_async_wait_n<MMA_DR - MMA_DY - 1>();
+            for (int u = lane; u < MMA_STEP; u += 32)
+                cp_async16(&rring[((unsigned)qr % MMA_RING) * MMA_STEP + u], rec + min(MMA_STEP * qr + u, n - 1));
+        cp_async_commit();
+        if (qy >= 0 && qy < ns) {
+            // the records of step qy are A(i - 1); B(i - 1) and A(i) may stay in flight
+            cp_async_wait_n<2>();
 #pragma unroll
-                for (int u = lane; u < MMA_STEP; u += 32) {
-                    const int j = __float_as_int(rring[((unsigned)qy % MMA_RING) * MMA_STEP + u].w);
-                    cp_async8(&yring[((unsigned)qy % MMA_YRING) * MMA_STEP + u], y + j);
-                }
+            for (int u = lane; u < MMA_STEP; u += 32) {
+                const int j = __float_as_int(rring[((unsigned)qy % MMA_RING) * MMA_STEP + u].w);
+                cp_async16(&yring[((unsigned)qy % MMA_YRING) * MMA_STEP + u],
+                           (const void *)((size_t)(y + j) & ~(size_t)15));
             }
         }
         cp_async_commit();
         if (i < 0) continue;
-        cp_async_wait_n<MMA_DY>();   // values of step i (and its records) have landed
+        // the values of step i are B(i - MMA_DY) (its records are older)
+        cp_async_wait_n<2 * MMA_DY>();
         const int sl0 = ((unsigned)i % MMA_RING) * MMA_STEP, yl0 = ((unsigned)i % MMA_YRING) * MMA_STEP;
-        // basis values X_1..X_7 of the step's nodes, (row, column) coordinate
-        // pairs, from the lane that loaded the node's record: X_{k+1} =
-        // X_{k-1} + (-1)^k 2 v X_k
+        // value and basis values X_1..X_7 of the step's nodes, (row, column)
+        // coordinate pairs, from the lane that loaded the node's record:
+        // X_{k+1} = X_{k-1} + (-1)^k 2 v X_k
 #pragma unroll
         for (int u = lane; u < MMA_STEP; u += 32) {
             const float4 r = rring[sl0 + u];
+            const float4 yb = yring[yl0 + u];
+            yc[u] = ((size_t)(y + __float_as_int(r.w)) & 8) ? make_float2(yb.z, yb.w) : make_float2(yb.x, yb.y);
             const f32x2 v = pk2(r.x, r.y);
             const f32x2 up = mul2(v, pk2(2.f, 2.f)), um = mul2(v, pk2(-2.f, -2.f));
             f32x2 xm = pk2(1.f, 1.f), x = v;
@@ -725,7 +735,7 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         auto operands = [&](int h) {
             GroupOp o;
             const float2 x0 = xs[g * XR + 8 * h + t], x1 = xs[g * XR + 8 * h + t + 4];
-            const float2 y0 = yring[yl0 + 8 * h + t], y1 = yring[yl0 + 8 * h + t + 4];
+            const float2 y0 = yc[8 * h + t], y1 = yc[8 * h + t + 4];
             o.a01 = pk2(y0.x * x0.y, y0.y * x0.y);
             o.a23 = pk2(y1.x * x1.y, y1.y * x1.y);
             if (ORD2) {
@@ -817,12 +827,13 @@ __device__ __forceinline__ void spread_mma_item(const DevPlan &P, const Term &T,
     using R = MmaRing<MMA_STEP>;
     unsigned char *ring = stg_raw + warp * R::BYTES;
     float4 *rring = (float4 *)ring;
-    float2 *yring = (float2 *)(ring + R::REC_BYTES);
+    float4 *yring = (float4 *)(ring + R::REC_BYTES);
     float2 *xs = (float2 *)(ring + R::X_OFF);
+    float2 *yc = (float2 *)(ring + R::YC_OFF);
     if (T.order == 2)
-        spread_mma_run<MR, true>(rec, y, (int)(b - a), S, T.stride, C, rring, yring, xs);
+        spread_mma_run<MR, true>(rec, y, (int)(b - a), S, T.stride, C, rring, yring, xs, yc);
     else
-        spread_mma_run<MR, false>(rec, y, (int)(b - a), S, T.stride, C, rring, yring, xs);
+        spread_mma_run<MR, false>(rec, y, (int)(b - a), S, T.stride, C, rring, yring, xs, yc);
 }
 
 // ---- Third-order cell sums on the tensor cores ----
