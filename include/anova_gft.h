@@ -217,7 +217,10 @@ int lsqr_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, double
  *   y_dev        : [M] complex
  *   w_dev        : [num_coeffs] double weights, or NULL for W = I
  *   lambdas      : host [n_lambda], any order (solved largest first)
- *   max_it, tol  : per lambda; stop when ||f_k - f_{k-1}|| <= tol ||f_k||
+ *   max_it, tol  : per lambda; stop when ||f_k - f_{k-1}|| <= tol ||f_k||.  FP32 plans
+ *                  resolve relative changes down to about 1e-7 (their rounding
+ *                  level); below that the iterates may cycle at the rounding level
+ *                  and a smaller tol then runs to max_it
  *   step_mode    : 0 constant step L (Remark after the Algorithm), 1 backtracking
  *   L0, eta      : step constant (constant mode: L; backtracking: L_0) and eta > 1;
  *                  L0 <= 0 asks for 1.05 times a Lanczos (Golub-Kahan) estimate of ||F||^2
@@ -354,7 +357,7 @@ typedef struct {
  * groups nonzero at the previous lambda and the empty set), run constant-step
  * FISTA with the transforms restricted to them, then re-admit every held-out
  * group whose KKT score ||W^{-1/2} (F^H r)_u|| exceeds lambda (1 + kkt_tol) and
- * re-solve until none does.  Output layout as fista_solve. */
+ * re-solve until none does.  Output layout and tol as fista_solve. */
 int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, const double *w_dev,
                         const double *lambdas, int n_lambda, int max_it, double tol, double threshold,
                         double kkt_tol, void *fhat_path_dev, anova_solve_info *info, anova_screen_stats *stats);

@@ -44,13 +44,7 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_n() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 // staging area after the grid: the larger of the unsorted layout
 // (float4 [2][SP]) and the sorted one (float4 [3][SP] node records, float2
@@ -59,14 +53,6 @@ __host__ __device__ constexpr size_t sp_stage_bytes(int sp) { return (size_t)sp 
 // third-order items (spread3_f32): 8 warp runs of 32 nodes, two records each
 constexpr size_t SP3_STAGE_BYTES = 3 * 256 * 32 + 2 * 256 * 8;
 
-// L2 prefetch of bytes (a multiple of 16) at a 16-byte aligned global address
-__device__ __forceinline__ void prefetch_l2_bulk(const void *src, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
 
 // shared memory of spread_f32 (o3 = false, sp nodes per block) or spread3_f32:
 // grid, node blocks, item slot

@@ -295,22 +295,39 @@ gather_sorted_f32(DevPlan single, BatchArgs B, const int4 *__restrict__ items, i
 
 // ---- Forward gather of order-1/2 terms on the tensor cores ----
 //
-// For the nodes j of one cell, H[j][r] = sum_k psi_col,k(j) G[r][k] (G the
-// m_row x 8 grid window of the cell, complex) is the product of the 16 x 8
-// matrix of column weights of 16 nodes with the 8 x 8 window (real and
-// imaginary parts one mma.m16n8k8 each, TF32 operands split into two parts);
-// f_j = sum_r psi_row,r(j) H[j][r] then takes two FMAs per lane and a
-// butterfly over the 4 lanes that hold node j's rows.  Lane (g, t) evaluates
-// column taps t, t + 4 and row taps 2t, 2t + 1 of nodes g and g + 8 of a tile
-// of 16 cell-sorted nodes, from coefficients held in registers (a table in
-// shared memory read at 4 taps at once would saturate its data path).  A
-// warp takes two tiles per step.  A tile holding nodes of several cells is
-// run once per cell with the other nodes' rows of A zeroed.  The sums go to
-// the 64-bit fixed-point accumulators as in gather_sorted_f32, one (node,
-// real or imaginary part) per lane.  Grid values are read from shared memory
-// only when the cell changes, so the data path carries the records and the
-// accumulator additions.
-constexpr int GM_TILE = 16;
+// Every tap weight is a degree-7 polynomial in the node's cell offset v, kept
+// in the Chebyshev basis X_i (Window::ch): psi_k = sum_i C[k][i] X_i.  For the
+// nodes j of one cell with grid window G (m_row x 8, complex)
+//     f_j = sum_{r,k} G[r][k] psi_row,r(j) psi_col,k(j)
+//         = sum_{l,i} X_l(v_row,j) H[l][i] X_i(v_col,j),   H = C_row^T G C_col,
+// so a cell change costs two small products that turn G into H (8 x 8,
+// complex), and each node only needs its 2 x 8 basis values: one lane
+// computes them (the recurrence, 8 packed FP32 operations) and leaves them in
+// shared memory.  A tile of 16 cell-sorted nodes takes P = X_col H^T (16 x 8,
+// real and imaginary parts one mma.m16n8k8 each, three TF32 products) and
+// f_j = sum_l X_l(v_row,j) P[j][l]: two FMAs per lane and a butterfly over
+// the 4 lanes that hold node j's columns.  The contraction index of every
+// product is permuted (2t, 2t + 1 -> t, t + 4), so that lane (g, t) needs
+// X_2t and X_2t+1 of both coordinates of nodes g, g + 8, one 16-byte read per
+// node, and so that each accumulator fragment is the next product's operand
+// as it stands.  A warp takes two tiles per step.  A tile holding nodes of
+// several cells is run once per cell with the other nodes' rows of A zeroed.
+// The sums go to the 64-bit fixed-point accumulators as in gather_sorted_f32,
+// one (node, real or imaginary part) per lane.
+//
+// Records arrive in a per-warp ring (cp.async, DR steps ahead; L2 bulk
+// prefetch PF steps ahead); the basis of a node lies in 4 chunks of 16 bytes
+// (X_2c(v_row), X_2c+1(v_row), X_2c(v_col), X_2c+1(v_col)), chunk c of node
+// u at position c ^ ((u / 2) mod 4), which keeps the writes (a lane per node)
+// and the reads (a lane per chunk) free of bank conflicts.
+constexpr int GM_TILE = 16, GM_STEP = 2 * GM_TILE;
+struct GmRing {
+    static constexpr int RING = 4, DR = 3, PF = 7;
+    static constexpr size_t REC_BYTES = (size_t)RING * GM_STEP * 16;
+    static constexpr size_t BYTES = REC_BYTES + (size_t)GM_STEP * 64;   // + basis chunks, per warp
+    static_assert(DR < RING, "ring depth");
+};
+constexpr int GM_CTAS_PER_SM = 3;
 
 __device__ __forceinline__ void mma3_tf32(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
                                           unsigned bh0, unsigned bh1, unsigned bl0, unsigned bl1) {
@@ -321,52 +338,55 @@ __device__ __forceinline__ void mma3_tf32(float (&d)[4], const unsigned (&ah)[4]
 
 template <int MR>
 __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, int n, const float2 *S, int stride,
-                                               bool ord2, const float4 *coef, unsigned long long *__restrict__ acc,
-                                               float sc) {
+                                               bool ord2, const float *__restrict__ chr, const float *__restrict__ chc,
+                                               unsigned long long *__restrict__ acc, float sc, float4 *rring,
+                                               float4 *xs) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    // With 8 row taps (MR = 4) the contraction index k of the mma and the
-    // output index (grid row) are permuted so that every lane needs mirrored
-    // tap pairs of its own nodes: k = t and k = t + 4 are column taps t and
-    // 7 - t, outputs 2t and 2t + 1 are rows t and 7 - t.  The window is even,
-    // so tap 7 - t at v is tap t at -v: one even/odd evaluation gives both
-    // (horner8_pm), from the coefficients of taps t only.  With 6 row taps the
-    // natural order stays: column taps t, t + 4, rows 2t, 2t + 1.
-    constexpr bool MIRROR = MR == 4;
-    float ca[NCOEF], cb[NCOEF], ra[NCOEF], rb[NCOEF];   // column taps t, t + 4; row taps 2t, 2t + 1 (MIRROR: ca, ra)
-    auto fetch = [&](const float4 *c, float (&dst)[NCOEF]) {
-        const float4 lo = c[0], hi = c[1];
-        dst[0] = lo.x, dst[1] = lo.y, dst[2] = lo.z, dst[3] = lo.w;
-        dst[4] = hi.x, dst[5] = hi.y, dst[6] = hi.z, dst[7] = hi.w;
-    };
-    fetch(coef + 2 * t, ca);
-    if constexpr (MIRROR) {
-        fetch(coef + 16 + 2 * t, ra);
-    } else {
-        fetch(coef + 2 * (t + 4), cb);
-        fetch(coef + 16 + 2 * (2 * t), ra);
-        fetch(coef + 16 + 2 * (2 * t + 1), rb);
-    }
-    const int nstep = (n + 2 * GM_TILE - 1) / (2 * GM_TILE);
-    // record u of step i; past the end the last record is read again (not written back)
-    auto ld = [&](int i, int u) { return __ldg(rec + min(2 * GM_TILE * i + u, n - 1)); };
-    float4 q[4] = {ld(0, g), ld(0, g + 8), ld(0, g + 16), ld(0, g + 24)};
-    int cur = -1;            // cell whose window is in bh, bl
-    unsigned bh[4], bl[4];   // B fragments: real part (b0, b1), imaginary part (b0, b1)
-    // output index g holds grid row grow (mirrored: 2s -> row s, 2s + 1 -> row 7 - s)
-    const int grow = MIRROR ? ((g & 1) ? 7 - (g >> 1) : (g >> 1)) : g;
-    const bool row_ok = ord2 ? grow < 2 * MR : grow == 0;   // that grid row of the window exists
-    auto load_b = [&](int off) {
-        float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+    const int ns = (n + GM_STEP - 1) / GM_STEP;
+    int cur = -1;            // cell whose H is in bh, bl
+    unsigned bh[4], bl[4];   // B fragments of H: real part (b0, b1), imaginary part (b0, b1)
+    // H = C_row^T G C_col for the cell at grid offset off.  Stage 1: D1_x[i][r]
+    // = sum_k C_col[k][i] G_x[r][k] (A = C_col^T, rows 8..15 zero; B[k][r] =
+    // G_x[r][k]); stage 2: H_x[l][i] = sum_r C_row[r][l] D1_x[i][r] (A[l][k] =
+    // C_row[r(k)][l], B[k][i] = D1_x[i][r(k)], r(t) = 2t, r(t + 4) = 2t + 1).
+    // Order 1: C_row = e_0 e_0^T and only grid row 0 exists.
+    auto load_h = [&](int off) {
+        const bool row_ok = ord2 ? g < 2 * MR : g == 0;   // grid row g of the window exists
+        float2 g0 = make_float2(0.f, 0.f), g1 = g0;
         if (row_ok) {
-            v0 = S[off + grow * stride + t];
-            v1 = S[off + grow * stride + (MIRROR ? 7 - t : t + 4)];
+            g0 = S[off + g * stride + t];
+            g1 = S[off + g * stride + t + 4];
         }
-        split_tf32(v0.x, bh[0], bl[0]);
-        split_tf32(v1.x, bh[1], bl[1]);
-        split_tf32(v0.y, bh[2], bl[2]);
-        split_tf32(v1.y, bh[3], bl[3]);
+        unsigned c1h[4], c1l[4], c2h[4], c2l[4];
+        split_tf32_x2(pk2(__ldg(chc + t * NCOEF + g), __ldg(chc + (t + 4) * NCOEF + g)), c1h[0], c1l[0], c1h[2],
+                      c1l[2]);
+        float r0 = 0.f, r1 = 0.f;
+        if (ord2) {
+            r0 = __ldg(chr + 2 * t * NCOEF + g);
+            r1 = __ldg(chr + (2 * t + 1) * NCOEF + g);
+        } else {
+            r0 = g == 0 && t == 0 ? 1.f : 0.f;
+        }
+        split_tf32_x2(pk2(r0, r1), c2h[0], c2l[0], c2h[2], c2l[2]);
+        c1h[1] = c1h[3] = c1l[1] = c1l[3] = c2h[1] = c2h[3] = c2l[1] = c2l[3] = 0u;
+        unsigned gh[4], gl[4];   // B of stage 1: (re k = t, re k = t + 4, im t, im t + 4)
+        split_tf32_x2(pk2(g0.x, g1.x), gh[0], gl[0], gh[1], gl[1]);
+        split_tf32_x2(pk2(g0.y, g1.y), gh[2], gl[2], gh[3], gl[3]);
+        float ur[4] = {0.f, 0.f, 0.f, 0.f}, ui[4] = {0.f, 0.f, 0.f, 0.f};
+        mma3_tf32(ur, c1h, c1l, gh[0], gh[1], gl[0], gl[1]);
+        mma3_tf32(ui, c1h, c1l, gh[2], gh[3], gl[2], gl[3]);
+        // ur = (D1_re[i = g][r = 2t], D1_re[g][2t + 1], 0, 0): the B fragment of stage 2
+        unsigned uh[4], ul[4];
+        split_tf32_x2(pk2(ur[0], ur[1]), uh[0], ul[0], uh[1], ul[1]);
+        split_tf32_x2(pk2(ui[0], ui[1]), uh[2], ul[2], uh[3], ul[3]);
+        float hr[4] = {0.f, 0.f, 0.f, 0.f}, hi[4] = {0.f, 0.f, 0.f, 0.f};
+        mma3_tf32(hr, c2h, c2l, uh[0], uh[1], ul[0], ul[1]);
+        mma3_tf32(hi, c2h, c2l, uh[2], uh[3], ul[2], ul[3]);
+        // hr = (H_re[l = g][i = 2t], H_re[g][2t + 1], 0, 0): B of the tile product
+        split_tf32_x2(pk2(hr[0], hr[1]), bh[0], bl[0], bh[1], bl[1]);
+        split_tf32_x2(pk2(hi[0], hi[1]), bh[2], bl[2], bh[3], bl[3]);
     };
-    // tile h of the step: rows of A from records q[2h] (node g) and q[2h + 1] (node g + 8)
+    // tile h: A rows from the basis of nodes g, g + 8 (q0, q1 = their chunk t)
     auto tile_slow = [&](const unsigned (&ah)[4], const unsigned (&al)[4], int off0, int off1, float (&dre)[4],
                          float (&dim)[4]) {
         bool p0 = true, p1 = true;   // nodes g, g + 8 not yet covered
@@ -379,7 +399,7 @@ __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, i
             const int oc = __shfl_sync(0xffffffffu, m0 ? off0 : off1, src);
             const bool e0 = p0 && off0 == oc, e1 = p1 && off1 == oc;
             if (oc != cur) {
-                load_b(oc);
+                load_h(oc);
                 cur = oc;
             }
             const unsigned mh[4] = {e0 ? ah[0] : 0u, e1 ? ah[1] : 0u, e0 ? ah[2] : 0u, e1 ? ah[3] : 0u};
@@ -390,87 +410,88 @@ __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, i
             p1 = p1 && !e1;
         }
     };
-    for (int i = 0; i < nstep; ++i) {
-        const float4 nq[4] = {ld(i + 1, g), ld(i + 1, g + 8), ld(i + 1, g + 16), ld(i + 1, g + 24)};
-        // A of both tiles: column weights, taps t (a0: node g, a1: node g + 8) and t + 4 (a2, a3)
-        unsigned ah[2][4], al[2][4];
+    const int sw = (g >> 1) & 3;   // chunk swizzle of nodes g, g + 8 (of every tile)
+    for (int i = -GmRing::DR; i < ns; ++i) {
+        {
+            const int qr = i + GmRing::DR, qp = i + GmRing::PF;
+            // the records of step qp into L2 (whole records of the run only)
+            if (lane == 0 && qp < ns && qp >= GmRing::DR)
+                prefetch_l2_bulk(rec + GM_STEP * qp, 16u * (unsigned)min(GM_STEP, n - GM_STEP * qp));
+            // record u of step qr; past the end the last record again (not written back)
+            if (qr < ns) cp_async16(&rring[(qr % GmRing::RING) * GM_STEP + lane], rec + min(GM_STEP * qr + lane, n - 1));
+            cp_async_commit();
+        }
+        if (i < 0) continue;
+        cp_async_wait_n<GmRing::DR>();   // the records of step i (this lane's own copy) have landed
+        // the basis of node `lane`, (row, column) pairs: X_{k+1} = X_{k-1} + (-1)^k 2 v X_k
+        const float4 r = rring[(i % GmRing::RING) * GM_STEP + lane];
+        const int my_cell = __float_as_int(r.z), my_j = __float_as_int(r.w);
+        {
+            const f32x2 v = pk2(r.x, r.y);
+            const f32x2 up = mul2(v, pk2(2.f, 2.f)), um = mul2(v, pk2(-2.f, -2.f));
+            f32x2 x[NCOEF];
+            x[0] = pk2(1.f, 1.f);
+            x[1] = v;
+#pragma unroll
+            for (int k = 2; k < NCOEF; ++k) x[k] = fma2((k & 1) ? up : um, x[k - 1], x[k - 2]);
+            const int msw = (lane >> 1) & 3;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float a0, b0, a1, b1;   // (row, column) of X_2c and X_2c+1
+                upk2(x[2 * c], a0, b0);
+                upk2(x[2 * c + 1], a1, b1);
+                xs[lane * 4 + (c ^ msw)] = make_float4(a0, a1, b0, b1);
+            }
+        }
+        __syncwarp();   // the step's basis chunks visible to the warp
+        const bool fast = __all_sync(0xffffffffu, my_cell == cur);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            if constexpr (MIRROR) {
-                float w0, w0m, w1, w1m;   // taps t and 7 - t of nodes g, g + 8
-                horner8_pm(ca, q[2 * h].y, w0, w0m);
-                horner8_pm(ca, q[2 * h + 1].y, w1, w1m);
-                split_tf32(w0, ah[h][0], al[h][0]);
-                split_tf32(w1, ah[h][1], al[h][1]);
-                split_tf32(w0m, ah[h][2], al[h][2]);
-                split_tf32(w1m, ah[h][3], al[h][3]);
+            const int n0 = GM_TILE * h + g, n1 = n0 + 8;   // nodes of this lane's A rows
+            const float4 q0 = xs[n0 * 4 + (t ^ sw)], q1 = xs[n1 * 4 + (t ^ sw)];
+            // A: a0 = X_2t(v_col) of node g, a1 = of node g + 8, a2 = X_2t+1(v_col) of g, a3 = of g + 8
+            unsigned ah[4], al[4];
+            split_tf32_x2(pk2(q0.z, q0.w), ah[0], al[0], ah[2], al[2]);
+            split_tf32_x2(pk2(q1.z, q1.w), ah[1], al[1], ah[3], al[3]);
+            float dre[4] = {0.f, 0.f, 0.f, 0.f}, dim[4] = {0.f, 0.f, 0.f, 0.f};
+            if (fast) {
+                mma3_tf32(dre, ah, al, bh[0], bh[1], bl[0], bl[1]);
+                mma3_tf32(dim, ah, al, bh[2], bh[3], bl[2], bl[3]);
             } else {
-                split_tf32(horner8(ca, q[2 * h].y), ah[h][0], al[h][0]);
-                split_tf32(horner8(ca, q[2 * h + 1].y), ah[h][1], al[h][1]);
-                split_tf32(horner8(cb, q[2 * h].y), ah[h][2], al[h][2]);
-                split_tf32(horner8(cb, q[2 * h + 1].y), ah[h][3], al[h][3]);
+                tile_slow(ah, al, __shfl_sync(0xffffffffu, my_cell, n0), __shfl_sync(0xffffffffu, my_cell, n1), dre,
+                          dim);
             }
+            // d0, d1: node g, l = 2t, 2t + 1; d2, d3: node g + 8.  Row basis X_2t, X_2t+1 = q.x, q.y
+            const float fx0 = fmaf(q0.y, dre[1], q0.x * dre[0]), fy0 = fmaf(q0.y, dim[1], q0.x * dim[0]);
+            const float fx1 = fmaf(q1.y, dre[3], q1.x * dre[2]), fy1 = fmaf(q1.y, dim[3], q1.x * dim[2]);
+            // reduce-scatter over the 4 lanes of nodes g, g + 8: lane t ends with
+            // value t of (node g: re, im; node g + 8: re, im) summed over the lanes
+            const bool hi2 = t & 2, hi1 = t & 1;
+            float k0 = hi2 ? fx1 : fx0, k1 = hi2 ? fy1 : fy0;   // the pair this lane keeps
+            k0 += __shfl_xor_sync(0xffffffffu, hi2 ? fx0 : fx1, 2);
+            k1 += __shfl_xor_sync(0xffffffffu, hi2 ? fy0 : fy1, 2);
+            const float v = (hi1 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, hi1 ? k0 : k1, 1);
+            const int nl = t < 2 ? n0 : n1;
+            const int j = __shfl_sync(0xffffffffu, my_j, nl);
+            if (GM_STEP * i + nl < n) red_add_u64(acc + 2 * (long long)j + (t & 1), __float2ll_rn(v * sc));
         }
-        float dre[2][4] = {}, dim[2][4] = {};
-        const int o[4] = {__float_as_int(q[0].z), __float_as_int(q[1].z), __float_as_int(q[2].z),
-                          __float_as_int(q[3].z)};
-        if (__all_sync(0xffffffffu, o[0] == cur && o[1] == cur && o[2] == cur && o[3] == cur)) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                mma3_tf32(dre[h], ah[h], al[h], bh[0], bh[1], bl[0], bl[1]);
-                mma3_tf32(dim[h], ah[h], al[h], bh[2], bh[3], bl[2], bl[3]);
-            }
-        } else {
-            tile_slow(ah[0], al[0], o[0], o[1], dre[0], dim[0]);
-            tile_slow(ah[1], al[1], o[2], o[3], dre[1], dim[1]);
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float4 &q0 = q[2 * h], &q1 = q[2 * h + 1];
-            // row weights: taps 2t (r0: node g, r1: node g + 8) and 2t + 1 (r2, r3)
-            float r[4];
-            if (ord2 && MIRROR) {   // rows t, 7 - t of nodes g (r0, r2) and g + 8 (r1, r3)
-                horner8_pm(ra, q0.x, r[0], r[2]);
-                horner8_pm(ra, q1.x, r[1], r[3]);
-            } else if (ord2) {
-                r[0] = horner8(ra, q0.x);
-                r[1] = horner8(ra, q1.x);
-                r[2] = horner8(rb, q0.x);
-                r[3] = horner8(rb, q1.x);
-            } else {
-                r[0] = r[1] = t == 0 ? 1.f : 0.f;
-                r[2] = r[3] = 0.f;
-            }
-            // d0, d1: node g, rows 2t, 2t + 1; d2, d3: node g + 8
-            float fx0 = fmaf(r[2], dre[h][1], r[0] * dre[h][0]), fy0 = fmaf(r[2], dim[h][1], r[0] * dim[h][0]);
-            float fx1 = fmaf(r[3], dre[h][3], r[1] * dre[h][2]), fy1 = fmaf(r[3], dim[h][3], r[1] * dim[h][2]);
-#pragma unroll
-            for (int m = 1; m <= 2; m <<= 1) {
-                fx0 += __shfl_xor_sync(0xffffffffu, fx0, m);
-                fy0 += __shfl_xor_sync(0xffffffffu, fy0, m);
-                fx1 += __shfl_xor_sync(0xffffffffu, fx1, m);
-                fy1 += __shfl_xor_sync(0xffffffffu, fy1, m);
-            }
-            // lane t writes (node g: re, im; node g + 8: re, im)[t]
-            const float v = t == 0 ? fx0 : t == 1 ? fy0 : t == 2 ? fx1 : fy1;
-            const int node = 2 * GM_TILE * i + GM_TILE * h + (t < 2 ? g : g + 8);
-            const int j = __float_as_int(t < 2 ? q0.w : q1.w);
-            if (node < n) red_add_u64(acc + 2 * (long long)j + (t & 1), __float2ll_rn(v * sc));
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] = nq[k];
+        __syncwarp();   // ring slot i and the basis chunks are read before later steps refill them
     }
+    cp_async_wait0();
 }
 
 template <int MR>
-__global__ void __launch_bounds__(GS_THREADS, 2)
+__global__ void __launch_bounds__(GS_THREADS, GM_CTAS_PER_SM)
 gather_mma_f32(DevPlan single, BatchArgs B, const int4 *__restrict__ items, int item_begin, int item_end,
                int *counter, long long max_grid_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *S = (float2 *)smem;
-    float4 *coef = (float4 *)(smem + max_grid_bytes);   // [8 column taps + 8 row taps][2]
-    int &s_item = *(int *)(coef + 32);
+    unsigned char *rings = smem + max_grid_bytes;
+    constexpr int NW = GS_THREADS / 32;
+    int &s_item = *(int *)(rings + NW * GmRing::BYTES);
     const int tid = threadIdx.x, warp = tid >> 5;
+    float4 *rring = (float4 *)(rings + warp * GmRing::BYTES);
+    float4 *xs = (float4 *)(rings + warp * GmRing::BYTES + GmRing::REC_BYTES);
     for (;;) {
         if (tid == 0) s_item = item_begin + atomicAdd(counter, 1);
         __syncthreads();
@@ -489,21 +510,15 @@ gather_mma_f32(DevPlan single, BatchArgs B, const int4 *__restrict__ items, int 
             float4 *S4 = (float4 *)S;
             const long long n4 = T.grid_bytes / 16;
             for (long long e = tid; e < n4; e += GS_THREADS) S4[e] = __ldg(gsrc + e);
-            if (tid < 32) {
-                const int tap = tid >> 1, h = tid & 1;
-                const float *src = tap < 8 ? P.windows[T.wc].c[tap] : P.windows[T.wr].c[min(tap - 8, 2 * MR - 1)];
-                coef[tid] = make_float4(__ldg(src + 4 * h), __ldg(src + 4 * h + 1), __ldg(src + 4 * h + 2),
-                                        __ldg(src + 4 * h + 3));
-            }
         }
         __syncthreads();
         // warp w takes a contiguous run of the item's records (whole steps of two tiles)
-        constexpr int NW = GS_THREADS / 32;
-        const long long len = j1 - j0, per = (len + 2 * GM_TILE * NW - 1) / (2 * GM_TILE * NW) * (2 * GM_TILE);
+        const long long len = j1 - j0, per = (len + GM_STEP * NW - 1) / (GM_STEP * NW) * GM_STEP;
         const long long a = j0 + warp * per, b = min(j1, a + per);
         if (a < b)
             gather_mma_run<MR>(P.srec + (long long)T.sort_slot * M + a, (int)(b - a), S, T.stride, T.order == 2,
-                               coef, P.facc, sc);
+                               T.order == 2 ? &P.windows[T.wr].ch[0][0] : nullptr, &P.windows[T.wc].ch[0][0],
+                               P.facc, sc, rring, xs);
         __syncthreads();   // the grid is read by every warp before the next item replaces it
     }
 }
@@ -531,6 +546,9 @@ int gather_sorted_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, 
     k_sorted_forward_init<<<dim3(nb, P), 256, 0, st>>>(v, B, fhat, f);
     const size_t smem = (size_t)max_grid_bytes + 32 * sizeof(float4) + 16;
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(3, (size_t)(MAX_SMEM + 1024) / (smem + 1024)));
+    const size_t smem_mma = (size_t)max_grid_bytes + (GS_THREADS / 32) * GmRing::BYTES + 16;
+    const int per_sm_mma = (int)std::max<size_t>(
+        1, std::min<size_t>(GM_CTAS_PER_SM, (size_t)(MAX_SMEM + 1024) / (smem_mma + 1024)));
     if (item_end > item_begin) cudaMemsetAsync(counter, 0, 2 * sizeof(int), st);
     if (cuda_end > item_begin) {
         const int ctas = std::max(1, std::min(cuda_end - item_begin, per_sm * sm_count));
@@ -542,13 +560,13 @@ int gather_sorted_launch(cudaStream_t st, const DevPlan &v, const BatchArgs &B, 
                                                                  max_grid_bytes);
     }
     if (item_end > cuda_end) {
-        const int ctas = std::max(1, std::min(item_end - cuda_end, std::min(per_sm, 2) * sm_count));
+        const int ctas = std::max(1, std::min(item_end - cuda_end, per_sm_mma * sm_count));
         if (mr <= 3)
-            gather_mma_f32<3><<<ctas, GS_THREADS, smem, st>>>(v, B, items, cuda_end, item_end, counter + 1,
-                                                              max_grid_bytes);
+            gather_mma_f32<3><<<ctas, GS_THREADS, smem_mma, st>>>(v, B, items, cuda_end, item_end, counter + 1,
+                                                                  max_grid_bytes);
         else
-            gather_mma_f32<4><<<ctas, GS_THREADS, smem, st>>>(v, B, items, cuda_end, item_end, counter + 1,
-                                                              max_grid_bytes);
+            gather_mma_f32<4><<<ctas, GS_THREADS, smem_mma, st>>>(v, B, items, cuda_end, item_end, counter + 1,
+                                                                  max_grid_bytes);
     }
     k_fixed_point_finish<<<dim3(nb, P), 256, 0, st>>>(v, B, f);
     return cuda_status(cudaGetLastError());

@@ -119,8 +119,12 @@ def test_screened_path_equals_full_path(gft):
 
 
 def test_trained_screen_saves_transform_work(gft):
-    """Train on the paths of four problems, screen a fifth: the screened path
-    transforms a fraction of the terms the full path does, with equal results."""
+    """Train on the paths of four problems, screen three others: the screened
+    paths transform a fraction of the terms the full paths do, with equal
+    results.  Both paths stop at a relative change of 1e-6: an FP32 plan cannot
+    resolve a relative change much below its resolution (2^-24, 6e-8), and at
+    such a tolerance the iteration counts measure cycles at the rounding level
+    (which differ between two paths of equal solutions) rather than work."""
     import torch
     Xs, ys = [], []
     for seed in (11, 12, 13, 14):
@@ -138,17 +142,21 @@ def test_trained_screen_saves_transform_work(gft):
     net = gft.Mlp(gft.mlp_init_params(21))
     hist = net.train(X, lab, batch=256, epochs=150, lr=2e-3, pos_weight=max(1.0, (1 - pos) / max(pos, 1e-3)))
     assert hist[-1] < hist[0]
-    x, terms, bw, y = _problem(2)
-    P = gft.Plan(to_dev(x, torch.float32), terms, bw)
-    yd = cplx_dev(y)
-    full, finfo, _ = P.fista(yd, LAMS, max_it=20000, tol=1e-8)
-    scr, _, stats = gft.fista_screened_path(P, net, yd, LAMS, max_it=20000, tol=1e-8, threshold=0.5)
-    for i in range(len(LAMS)):
-        assert rel_l2(host(scr[i]), host(full[i])) <= 1e-4
-    # transform work: terms transformed per iteration, summed over the path
-    full_work = sum(fi["iterations"] for fi in finfo) * (len(terms) - 1)
-    active = [int(a.sum()) for a in _active(full, terms, bw)]
-    frac = stats["term_iterations"] / full_work
-    print("active groups per lambda", active, "screen stats", stats, "full work", full_work, "fraction", frac)
-    assert frac < 0.6, (frac, stats, active)
+    fracs = []
+    for seed in (2, 3, 4):
+        x, terms, bw, y = _problem(seed)
+        P = gft.Plan(to_dev(x, torch.float32), terms, bw)
+        yd = cplx_dev(y)
+        full, finfo, _ = P.fista(yd, LAMS, max_it=20000, tol=1e-6)
+        scr, _, stats = gft.fista_screened_path(P, net, yd, LAMS, max_it=20000, tol=1e-6, threshold=0.5)
+        for i in range(len(LAMS)):
+            assert rel_l2(host(scr[i]), host(full[i])) <= 1e-4
+        # transform work: terms transformed per iteration, summed over the path
+        full_work = sum(fi["iterations"] for fi in finfo) * (len(terms) - 1)
+        active = [int(a.sum()) for a in _active(full, terms, bw)]
+        fracs.append(stats["term_iterations"] / full_work)
+        print("problem", seed, "active groups per lambda", active, "screen stats", stats, "full work", full_work,
+              "fraction", fracs[-1])
+        P.close()
+    assert np.mean(fracs) < 0.6 and max(fracs) < 0.7, fracs
     net.close()
