@@ -361,10 +361,12 @@ def run_mine(args, rank, world, local_rank):
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tf):
-        tj = json.load(open(tf))
-        src = [os.path.join(ROOT, "paper_2010_10199_gb300", "csrc", s) for s in tj.get("sources", [])]
-        if tj.get("kernel") == kname and all(os.path.exists(s) for s in src) and source_hash(src) == tj.get("hash"):
-            traffic = tj.get("dram_bytes_per_launch")
+        # one entry per kernel; an entry counts while its kernel's sources are unchanged
+        for tj in json.load(open(tf)).get("entries", []):
+            src = [os.path.join(ROOT, "paper_2010_10199_gb300", "csrc", s) for s in tj.get("sources", [])]
+            if tj.get("kernel") == kname and all(os.path.exists(s) for s in src) and \
+                    source_hash(src) == tj.get("hash"):
+                traffic = tj.get("dram_bytes_per_launch")
     # Arithmetic roofline: both kernels are bound by instruction issue, far from
     # HBM (the HBM figures are kept beside it).  Algorithmic work per node and
     # term, as FMA-equivalent operations of the direct evaluation: the window

@@ -548,31 +548,28 @@ __device__ __forceinline__ void spread_unsorted_item(const DevPlan &P, const Ter
 // once per cell with the other nodes masked.
 
 // Records rec[0, n) of one term for one warp, in steps of STEP = 32 nodes (4
-// groups of 8 for the tensor core; a step lying in one cell takes one test).
-// The warp's own rings in shared memory (RING steps of records, YRING steps
-// of values) are filled by its lanes with cp.async, in two groups per step:
-// the records DR steps ahead, then the values DY steps ahead (their
-// addresses come from the records already in the ring; with DR = DY + 1 the
-// wait for those records leaves the previous step's values in flight).
-// Records PF steps ahead are prefetched into L2 (one bulk prefetch per step),
-// so that the ring's copies find them there.  A value y[index] arrives as the
-// aligned 16-byte block that holds it (cp.async.cg: the scattered reads do not
-// allocate L1 lines, whose few hundred per SM would otherwise bound the reads
-// in flight; the block lies within the allocation of y, whose granularity
-// is at least 16 bytes); the lane that computes the node's basis moves the
-// right half to the step's value array.  The basis rows X_0..X_7 of the
-// current step follow, XROW words apart (= 8 mod 32: the four rows a
-// half-warp reads lie in distinct banks), then the step's values.
+// groups of 8 for the tensor core; a step lying in one cell takes one test),
+// lane u holding node u of a step.  The warp's ring in shared memory (RING
+// steps of records) is filled by its lanes with cp.async DR steps ahead, and
+// records PF steps ahead are prefetched into L2 (one bulk prefetch per step),
+// so that the ring's copies find them there.  The value y[index] of a node is
+// loaded by its lane into registers DY steps ahead, through L2 only
+// (ld.global.cg: the scattered reads allocate no L1 lines, whose few hundred
+// per SM would otherwise bound the reads in flight, and they cost no
+// shared-memory writes); the lane then computes the node's basis and leaves
+// it, with the value, in shared memory: the basis rows X_0..X_7 of the
+// current step XROW words apart (= 8 mod 32: the four rows a half-warp reads
+// lie in distinct banks), then the step's values.
 // Order 1: B = e_0 (the single grid row), exact in TF32.
 template <int STEP>
 struct MmaRing {
-    static constexpr int RING = 4, YRING = 3, DR = 3, DY = 2, PF = 7;   // PF: L2 prefetch distance
+    static constexpr int RING = 4, DR = 3, DY = 2, PF = 7;   // PF: L2 prefetch distance
     static constexpr int XROW = 2 * STEP + 8;   // words per basis row (STEP float2 + pad)
     static constexpr size_t REC_BYTES = (size_t)RING * STEP * 16;                    // float4 records
-    static constexpr size_t X_OFF = REC_BYTES + (size_t)YRING * STEP * 16;           // + 16-byte value blocks
-    static constexpr size_t YC_OFF = X_OFF + (size_t)NCOEF * XROW * 4;               // + basis rows
-    static constexpr size_t BYTES = YC_OFF + (size_t)STEP * 8;                       // + values, per warp
-    static_assert(DR == DY + 1 && DR < RING && DY < YRING && STEP % 32 == 0 && XROW % 32 == 8, "ring layout");
+    static constexpr size_t X_OFF = REC_BYTES;                                       // basis rows
+    static constexpr size_t YC_OFF = X_OFF + (size_t)NCOEF * XROW * 4;               // + values
+    static constexpr size_t BYTES = YC_OFF + (size_t)STEP * 8;                       // per warp
+    static_assert(DY < DR && DR < RING && STEP == 32 && XROW % 32 == 8, "ring layout");
 };
 
 constexpr int MMA_STEP = 32;   // nodes per ring step of the order-1/2 tensor-core spread
@@ -581,21 +578,13 @@ static size_t spread_mma_smem_bytes(long long max_grid_bytes) {
     return (size_t)max_grid_bytes + MmaRing<MMA_STEP>::BYTES * (SPREAD_MMA_THREADS / 32) + 16;
 }
 
-// Per-lane window coefficients of the two products that turn Mo into G, split
-// into TF32 parts: the row window's C_row[g][2t], C_row[g][2t + 1] (zero for
-// g >= 2 m_row; order 1: e_0 e_0^T) and the column window's C_col[g][2t],
-// C_col[g][2t + 1].
-struct MomentCoef {
-    unsigned rh0, rl0, rh1, rl1;
-    unsigned ch0, cl0, ch1, cl1;
-};
-
 template <int MR, bool ORD2>
 __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, const float2 *__restrict__ y, int n,
-                                               float2 *S, int stride, const MomentCoef &C, float4 *rring,
-                                               float4 *yring, float2 *xs, float2 *yc) {
+                                               float2 *S, int stride, const float *__restrict__ chr,
+                                               const float *__restrict__ chc, float4 *rring, float2 *xs,
+                                               float2 *yc) {
     using R = MmaRing<MMA_STEP>;
-    constexpr unsigned MMA_RING = R::RING, MMA_YRING = R::YRING;
+    constexpr unsigned MMA_RING = R::RING;
     constexpr int MMA_DR = R::DR, MMA_DY = R::DY, XR = R::XROW / 2;   // basis row stride in float2
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int ns = (n + MMA_STEP - 1) / MMA_STEP;
@@ -603,12 +592,31 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
     float d[4] = {0.f, 0.f, 0.f, 0.f};
     // d = Mo (re i = g, l = 2t), (re g, 2t + 1), (im g, 2t), (im g, 2t + 1)
     auto flush = [&]() {
+        // this lane's window coefficients of the two products, split into TF32
+        // parts: the row window's C_row[g][2t], C_row[g][2t + 1] (zero for g >=
+        // 2 m_row; order 1: e_0 e_0^T) and the column window's C_col[g][2t],
+        // C_col[g][2t + 1] (Window::ch rows are taps)
+        unsigned ah[4], al[4], ch0, cl0, ch1, cl1;
+        {
+            float r0 = 0.f, r1 = 0.f;
+            if (ORD2) {
+                if (g < 2 * MR) {
+                    r0 = __ldg(chr + g * NCOEF + 2 * t);
+                    r1 = __ldg(chr + g * NCOEF + 2 * t + 1);
+                }
+            } else {
+                r0 = g == 0 && t == 0 ? 1.f : 0.f;
+            }
+            split_tf32_x2(pk2(r0, r1), ah[0], al[0], ah[2], al[2]);
+            ah[1] = ah[3] = al[1] = al[3] = 0u;
+            split_tf32_x2(pk2(__ldg(chc + g * NCOEF + 2 * t), __ldg(chc + g * NCOEF + 2 * t + 1)), ch0, cl0, ch1,
+                          cl1);
+        }
         // Q_x[j][i] = sum_l C_row[j][l] Mo_x[i][l]: A = C_row (rows 8..15 zero),
         // B[k][i] = Mo_x[i][l(k)] with l(t) = 2t, l(t + 4) = 2t + 1
         unsigned mh[4], ml[4];
         split_tf32_x2(pk2(d[0], d[1]), mh[0], ml[0], mh[1], ml[1]);
         split_tf32_x2(pk2(d[2], d[3]), mh[2], ml[2], mh[3], ml[3]);
-        const unsigned ah[4] = {C.rh0, 0u, C.rh1, 0u}, al[4] = {C.rl0, 0u, C.rl1, 0u};
         float qr[4] = {0.f, 0.f, 0.f, 0.f}, qi[4] = {0.f, 0.f, 0.f, 0.f};
         mma_tf32(qr, al, mh[0], mh[1]);
         mma_tf32(qr, ah, ml[0], ml[1]);
@@ -623,9 +631,9 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         split_tf32_x2(pk2(qr[0], qi[0]), qh[0], ql[0], qh[1], ql[1]);
         split_tf32_x2(pk2(qr[1], qi[1]), qh[2], ql[2], qh[3], ql[3]);
         float G[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_tf32(G, ql, C.ch0, C.ch1);
-        mma_tf32(G, qh, C.cl0, C.cl1);
-        mma_tf32(G, qh, C.ch0, C.ch1);
+        mma_tf32(G, ql, ch0, ch1);
+        mma_tf32(G, qh, cl0, cl1);
+        mma_tf32(G, qh, ch0, ch1);
         // G = (re, row tap g, column tap 2t), (re, g, 2t + 1), (im, g, 2t), (im, g, 2t + 1)
         if (ORD2 ? g < 2 * MR : g == 0) {
             float *c = (float *)(S + cur + g * stride + 2 * t);
@@ -648,48 +656,38 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
         mma_tf32(e, ah, bh0, bh1);
     };
     // basis row 0 is X_0 = 1 for every node
-#pragma unroll
-    for (int u = lane; u < MMA_STEP; u += 32) xs[u] = make_float2(1.f, 1.f);
+    xs[lane] = make_float2(1.f, 1.f);
+    float2 y_mid = make_float2(0.f, 0.f), y_cur = y_mid;   // values of steps i + 1, i (DY = 2 in flight)
+    static_assert(MmaRing<MMA_STEP>::DY == 2, "two values in flight");
     // A fresh tensor-core sum per step (at most eight groups), added to d in
     // FP32 with rounding to nearest: the tensor core's own accumulation is
     // not rounded to nearest, and its bias would grow with the cell's node
     // count.
     for (int i = -MMA_DR; i < ns; ++i) {
-        // iteration i commits two cp.async groups: A(i), the records of step
-        // i + MMA_DR, and B(i), the values of step i + MMA_DY; steps i < 0 fill
-        // the rings
+        // iteration i commits one cp.async group, the records of step i + DR,
+        // and loads the values of step i + DY; steps i < 0 fill the pipeline
         const int qr = i + MMA_DR, qy = i + MMA_DY, qp = i + R::PF;
         // the records of step qp into L2 (whole records of the run only)
         if (lane == 0 && qp < ns && qp >= MMA_DR)
             prefetch_l2_bulk(rec + MMA_STEP * qp, 16u * (unsigned)min(MMA_STEP, n - MMA_STEP * qp));
-        if (qr < ns)
-#pragma unroll
-            for (int u = lane; u < MMA_STEP; u += 32)
-                cp_async16(&rring[((unsigned)qr % MMA_RING) * MMA_STEP + u], rec + min(MMA_STEP * qr + u, n - 1));
+        if (qr < ns) cp_async16(&rring[((unsigned)qr % MMA_RING) * MMA_STEP + lane], rec + min(MMA_STEP * qr + lane, n - 1));
         cp_async_commit();
-        if (qy >= 0 && qy < ns) {
-            // the records of step qy are A(i - 1); B(i - 1) and A(i) may stay in flight
-            cp_async_wait_n<2>();
-#pragma unroll
-            for (int u = lane; u < MMA_STEP; u += 32) {
-                const int j = __float_as_int(rring[((unsigned)qy % MMA_RING) * MMA_STEP + u].w);
-                cp_async16(&yring[((unsigned)qy % MMA_YRING) * MMA_STEP + u],
-                           (const void *)((size_t)(y + j) & ~(size_t)15));
-            }
-        }
-        cp_async_commit();
+        // this lane's records of steps <= i + DR - 1 (the groups before this one) have landed
+        cp_async_wait_n<1>();
+        // the value of this lane's node of step qy, into registers
+        float2 y_next = make_float2(0.f, 0.f);
+        if (qy >= 0 && qy < ns) y_next = __ldcg(y + __float_as_int(rring[((unsigned)qy % MMA_RING) * MMA_STEP + lane].w));
+        const float2 y_now = y_cur;   // the value of this lane's node of step i
+        y_cur = y_mid;
+        y_mid = y_next;
         if (i < 0) continue;
-        // the values of step i are B(i - MMA_DY) (its records are older)
-        cp_async_wait_n<2 * MMA_DY>();
-        const int sl0 = ((unsigned)i % MMA_RING) * MMA_STEP, yl0 = ((unsigned)i % MMA_YRING) * MMA_STEP;
-        // value and basis values X_1..X_7 of the step's nodes, (row, column)
-        // coordinate pairs, from the lane that loaded the node's record:
-        // X_{k+1} = X_{k-1} + (-1)^k 2 v X_k
-#pragma unroll
-        for (int u = lane; u < MMA_STEP; u += 32) {
+        const int sl0 = ((unsigned)i % MMA_RING) * MMA_STEP;
+        // value and basis values X_1..X_7 of node `lane` of the step, (row,
+        // column) coordinate pairs: X_{k+1} = X_{k-1} + (-1)^k 2 v X_k
+        {
+            const int u = lane;
             const float4 r = rring[sl0 + u];
-            const float4 yb = yring[yl0 + u];
-            yc[u] = ((size_t)(y + __float_as_int(r.w)) & 8) ? make_float2(yb.z, yb.w) : make_float2(yb.x, yb.y);
+            yc[u] = y_now;
             const f32x2 v = pk2(r.x, r.y);
             const f32x2 up = mul2(v, pk2(2.f, 2.f)), um = mul2(v, pk2(-2.f, -2.f));
             f32x2 xm = pk2(1.f, 1.f), x = v;
@@ -789,22 +787,7 @@ __device__ __forceinline__ void spread_mma_run(const float4 *__restrict__ rec, c
 template <int MR>
 __device__ __forceinline__ void spread_mma_item(const DevPlan &P, const Term &T, const float2 *__restrict__ y,
                                                 long long j0, long long j1, float2 *S, unsigned char *stg_raw) {
-    const int warp = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
-    MomentCoef C;
-    {
-        float r0, r1;
-        if (T.order == 2) {
-            const float *rs = P.windows[T.wr].ch[min(g, 2 * MR - 1)];
-            r0 = g < 2 * MR ? __ldg(rs + 2 * t) : 0.f;
-            r1 = g < 2 * MR ? __ldg(rs + 2 * t + 1) : 0.f;
-        } else {
-            r0 = g == 0 && t == 0 ? 1.f : 0.f;
-            r1 = 0.f;
-        }
-        split_tf32_x2(pk2(r0, r1), C.rh0, C.rl0, C.rh1, C.rl1);
-        const float *cs = P.windows[T.wc].ch[g];
-        split_tf32_x2(pk2(__ldg(cs + 2 * t), __ldg(cs + 2 * t + 1)), C.ch0, C.cl0, C.ch1, C.cl1);
-    }
+    const int warp = threadIdx.x >> 5;
     constexpr int NW = SPREAD_MMA_THREADS / 32;
     const long long len = j1 - j0, per = (len + 8 * NW - 1) / (8 * NW) * 8;
     const long long a = j0 + warp * per, b = min(j1, a + per);
@@ -813,13 +796,13 @@ __device__ __forceinline__ void spread_mma_item(const DevPlan &P, const Term &T,
     using R = MmaRing<MMA_STEP>;
     unsigned char *ring = stg_raw + warp * R::BYTES;
     float4 *rring = (float4 *)ring;
-    float4 *yring = (float4 *)(ring + R::REC_BYTES);
     float2 *xs = (float2 *)(ring + R::X_OFF);
     float2 *yc = (float2 *)(ring + R::YC_OFF);
+    const float *chc = &P.windows[T.wc].ch[0][0];
     if (T.order == 2)
-        spread_mma_run<MR, true>(rec, y, (int)(b - a), S, T.stride, C, rring, yring, xs, yc);
+        spread_mma_run<MR, true>(rec, y, (int)(b - a), S, T.stride, &P.windows[T.wr].ch[0][0], chc, rring, xs, yc);
     else
-        spread_mma_run<MR, false>(rec, y, (int)(b - a), S, T.stride, C, rring, yring, xs, yc);
+        spread_mma_run<MR, false>(rec, y, (int)(b - a), S, T.stride, nullptr, chc, rring, xs, yc);
 }
 
 // ---- Third-order cell sums on the tensor cores ----
