@@ -93,8 +93,13 @@ int spread_ctas_per_sm(long long max_grid_bytes, bool tc) {
     return ctas_for(max_grid_bytes, spread_block_nodes(max_grid_bytes));
 }
 
-int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc) {
-    const long long resident = (long long)spread_ctas_per_sm(max_grid_bytes, tc) * sm_count;
+int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc,
+                      bool order3) {
+    // third-order items cost several times an order-1/2 item per node: with
+    // them, finer chunks (three per CTA of 3 per SM, the forward gather's
+    // count) keep the last wave of both kernels short
+    const int per_sm = spread_ctas_per_sm(max_grid_bytes, tc);
+    const long long resident = (long long)(order3 ? std::max(3, per_sm) : per_sm) * sm_count;
     long long K = (3 * resident + std::max(1, n_act_total) - 1) / std::max(1, n_act_total);
     K = std::min<long long>(K, (M + 2047) / 2048);
     K = std::min<long long>(K, kmax);

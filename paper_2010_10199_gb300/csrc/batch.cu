@@ -300,9 +300,15 @@ int anova_batch_create(anova_batch_t *out, int n_problems, const int *d, const i
     // K_p sized for all problems sharing the GPU
     std::vector<int4> items;
     std::vector<int> Ks(n_problems);
+    bool order3 = false;
+    for (int p = 0; p < n_problems; ++p) {
+        const Plan &pl = b->plans[p]->p;
+        for (int i = 0; i < pl.n_act; ++i) order3 = order3 || pl.h_terms[pl.h_act[i]].order == 3;
+    }
     for (int p = 0; p < n_problems; ++p) {
         Plan &pl = b->plans[p]->p;
-        Ks[p] = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count, b->cell_tc);
+        Ks[p] = spread_chunks_for(pl.M, total_act, pl.spread_kmax, b->max_grid_bytes, b->sm_count, b->cell_tc,
+                                  order3);
         b->views[p].spread_chunks = Ks[p];
     }
     // third-order items of every problem first, then the others

@@ -305,8 +305,8 @@ gather_sorted_f32(DevPlan single, BatchArgs B, const int4 *__restrict__ items, i
 // computes them (the recurrence, 8 packed FP32 operations) and leaves them in
 // shared memory.  A tile of 16 cell-sorted nodes takes P = X_col H^T (16 x 8,
 // real and imaginary parts one mma.m16n8k8 each, three TF32 products) and
-// f_j = sum_l X_l(v_row,j) P[j][l]: two FMAs per lane and a butterfly over
-// the 4 lanes that hold node j's columns.  The contraction index of every
+// f_j = sum_l X_l(v_row,j) P[j][l]: two FMAs per lane and a reduce-scatter
+// over the 4 lanes that hold node j's columns.  The contraction index of every
 // product is permuted (2t, 2t + 1 -> t, t + 4), so that lane (g, t) needs
 // X_2t and X_2t+1 of both coordinates of nodes g, g + 8, one 16-byte read per
 // node, and so that each accumulator fragment is the next product's operand

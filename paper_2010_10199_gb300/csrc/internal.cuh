@@ -290,9 +290,11 @@ int launch_adjoint_f64(Plan &p, const double2 *y, double2 *fhat);
 // CTAs per SM of the order-1/2 spread kernel (tc: the tensor-core one)
 int spread_ctas_per_sm(long long max_grid_bytes, bool tc);
 // Node chunks per term for a spread over n_act_total active terms (all
-// problems of a launch) on sm_count SMs: about three items per resident CTA,
+// problems of a launch) on sm_count SMs: about three items per resident
+// spread CTA (with third-order terms, order3, per CTA of 3 per SM at least),
 // at most kmax, at least 2048 nodes per chunk.
-int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc);
+int spread_chunks_for(long long M, int n_act_total, int kmax, long long max_grid_bytes, int sm_count, bool tc,
+                      bool order3);
 // Appends the spread work items of one problem, K chunks per active term:
 // those of the third-order terms (sel = 3) or of the others, order 2 before
 // order 1 (sel = 0).  Returns the count.

@@ -168,7 +168,9 @@ int set_active_terms(Plan &p, const unsigned char *user_mask) {
     p.n_items = 0;
     p.n_items3 = 0;
     if (n == 0) return ANOVA_OK;
-    p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count, p.cell_tc);
+    bool order3 = false;
+    for (int i = 0; i < n; ++i) order3 = order3 || p.h_terms[p.h_act[i]].order == 3;
+    p.spread_K = spread_chunks_for(p.M, n, p.spread_kmax, p.max_grid_bytes, p.sm_count, p.cell_tc, order3);
     if (p.h_items) {
         p.n_items3 = append_spread_items(p, 0, p.spread_K, p.h_items, 3);
         p.n_items = p.n_items3 + append_spread_items(p, 0, p.spread_K, p.h_items + p.n_items3, 0);
