@@ -137,6 +137,21 @@ def test_sparse_cells_and_wide_window(gft, path):
     _pair_check(gft, x, terms, bw, eps=1e-6, tol=5e-6, **SPREAD_PATHS[path])
 
 
+@pytest.mark.parametrize("path", ["tensor", "cuda"])
+@pytest.mark.parametrize("opts", [dict(window_m_row=3), dict(sigma=1.75), dict(sigma=2.5, window_m_row=3)])
+def test_window_and_oversampling_options(gft, path, opts):
+    """6 row taps (the window for eps >= 5e-5: its own kernel instantiation,
+    the tensor-core tiles' rows 6 and 7 zero) and oversampling factors other
+    than 2 (grid sizes that are not powers of two).  Bar with 6 row taps: 3e-5,
+    the window's own error (single blocks of F^H y reach 2.7e-5 there, which is
+    why 8 row taps are the default below eps 5e-5)."""
+    x = inputs.uniform_points(23, 5, 5003)
+    terms = anova.term_set(5, 2)
+    bw = [0] + [32] * 5 + [16] * 10
+    tol = 3e-5 if opts.get("window_m_row") == 3 else TOL
+    _pair_check(gft, x, terms, bw, tol=tol, **opts, **SPREAD_PATHS[path])
+
+
 def test_c2_subsample_all_terms(gft):
     w = inputs.c2_scale(M=10000)
     _pair_check(gft, w["x"], w["terms"], w["bandwidths"], fhat=w["fhat"], y=w["y"])
