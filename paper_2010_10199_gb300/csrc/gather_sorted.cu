@@ -411,6 +411,10 @@ __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, i
         }
     };
     const int sw = (g >> 1) & 3;   // chunk swizzle of nodes g, g + 8 (of every tile)
+    const float4 *xq0 = xs + g * 4 + (t ^ sw);   // chunk t of node g of tile 0 (+ 8 nodes: + 32)
+    float4 *xw = xs + lane * 4;                  // this lane's node's chunks
+    const int msw = (lane >> 1) & 3;
+    unsigned long long *acc_t = acc + (t & 1);   // this lane's part (real or imaginary)
     for (int i = -GmRing::DR; i < ns; ++i) {
         {
             const int qr = i + GmRing::DR, qp = i + GmRing::PF;
@@ -418,13 +422,14 @@ __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, i
             if (lane == 0 && qp < ns && qp >= GmRing::DR)
                 prefetch_l2_bulk(rec + GM_STEP * qp, 16u * (unsigned)min(GM_STEP, n - GM_STEP * qp));
             // record u of step qr; past the end the last record again (not written back)
-            if (qr < ns) cp_async16(&rring[(qr % GmRing::RING) * GM_STEP + lane], rec + min(GM_STEP * qr + lane, n - 1));
+            if (qr < ns)
+                cp_async16(&rring[((unsigned)qr % GmRing::RING) * GM_STEP + lane], rec + min(GM_STEP * qr + lane, n - 1));
             cp_async_commit();
         }
         if (i < 0) continue;
         cp_async_wait_n<GmRing::DR>();   // the records of step i (this lane's own copy) have landed
         // the basis of node `lane`, (row, column) pairs: X_{k+1} = X_{k-1} + (-1)^k 2 v X_k
-        const float4 r = rring[(i % GmRing::RING) * GM_STEP + lane];
+        const float4 r = rring[((unsigned)i % GmRing::RING) * GM_STEP + lane];
         const int my_cell = __float_as_int(r.z), my_j = __float_as_int(r.w);
         {
             const f32x2 v = pk2(r.x, r.y);
@@ -434,13 +439,12 @@ __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, i
             x[1] = v;
 #pragma unroll
             for (int k = 2; k < NCOEF; ++k) x[k] = fma2((k & 1) ? up : um, x[k - 1], x[k - 2]);
-            const int msw = (lane >> 1) & 3;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 float a0, b0, a1, b1;   // (row, column) of X_2c and X_2c+1
                 upk2(x[2 * c], a0, b0);
                 upk2(x[2 * c + 1], a1, b1);
-                xs[lane * 4 + (c ^ msw)] = make_float4(a0, a1, b0, b1);
+                xw[c ^ msw] = make_float4(a0, a1, b0, b1);
             }
         }
         __syncwarp();   // the step's basis chunks visible to the warp
@@ -448,7 +452,7 @@ __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, i
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int n0 = GM_TILE * h + g, n1 = n0 + 8;   // nodes of this lane's A rows
-            const float4 q0 = xs[n0 * 4 + (t ^ sw)], q1 = xs[n1 * 4 + (t ^ sw)];
+            const float4 q0 = xq0[GM_TILE * 4 * h], q1 = xq0[GM_TILE * 4 * h + 32];
             // A: a0 = X_2t(v_col) of node g, a1 = of node g + 8, a2 = X_2t+1(v_col) of g, a3 = of g + 8
             unsigned ah[4], al[4];
             split_tf32_x2(pk2(q0.z, q0.w), ah[0], al[0], ah[2], al[2]);
@@ -473,7 +477,7 @@ __device__ __forceinline__ void gather_mma_run(const float4 *__restrict__ rec, i
             const float v = (hi1 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, hi1 ? k0 : k1, 1);
             const int nl = t < 2 ? n0 : n1;
             const int j = __shfl_sync(0xffffffffu, my_j, nl);
-            if (GM_STEP * i + nl < n) red_add_u64(acc + 2 * (long long)j + (t & 1), __float2ll_rn(v * sc));
+            if (GM_STEP * i + nl < n) red_add_u64(acc_t + 2 * (long long)j, __float2ll_rn(v * sc));
         }
         __syncwarp();   // ring slot i and the basis chunks are read before later steps refill them
     }
