@@ -108,12 +108,20 @@ struct ScreenWork {
 };
 
 // q = F^H (F f - y) over all terms
-static int full_gradient(Plan &p, SolverWork *W, const float2 *y, const float2 *f, float2 *q) {
-    int rc = set_active_terms(p, nullptr);
+// q = F^H (F f - y) over all groups.  f is zero outside the groups of fmask
+// (user terms; NULL: any group), so the forward runs over those only; the
+// adjoint, which the KKT scores need for every group, over all of them.
+static int full_gradient(Plan &p, SolverWork *W, const float2 *y, const float2 *f, float2 *q,
+                         const uint8_t *fmask) {
+    int rc = set_active_terms(p, fmask);
     if (rc) return rc;
     float2 *tM = (float2 *)W->tM;
     rc = launch_trafo_f32(p, f, tM);
     if (rc) return rc;
+    if (fmask) {
+        rc = set_active_terms(p, nullptr);
+        if (rc) return rc;
+    }
     k_residual<<<RED_BLOCKS, RED_THREADS, 0, p.stream>>>(W->st, tM, y, p.M, nullptr);
     return launch_adjoint_f32(p, tM, q);
 }
@@ -154,7 +162,7 @@ int anova_screen_features(anova_plan_t plan, const void *y_dev, const double *w_
     if (e == cudaSuccess) e = cudaMalloc(&S.order, sizeof(int) * G);
     if (e != cudaSuccess) return cuda_status(e);
     cudaMemcpyAsync(S.order, p.h_user_order, sizeof(int) * G, cudaMemcpyHostToDevice, p.stream);
-    rc = full_gradient(p, W, (const float2 *)y_dev, (const float2 *)fhat_dev, S.q);
+    rc = full_gradient(p, W, (const float2 *)y_dev, (const float2 *)fhat_dev, S.q, nullptr);
     if (rc) return rc;
     std::vector<double> pairs;
     rc = features_host(p, W, S, (const float2 *)fhat_dev, pairs);
@@ -202,7 +210,9 @@ int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, c
         SolverState z;
         std::memset(&z, 0, sizeof(z));
         cudaMemcpyAsync(W->st, &z, sizeof(z), cudaMemcpyHostToDevice, p.stream);
-        rc = full_gradient(p, W, y, S.fprev, S.q);
+        // f = 0: the forward is the empty set's coefficient alone
+        std::vector<uint8_t> none(p.n_user_terms, 0);
+        rc = full_gradient(p, W, y, S.fprev, S.q, none.data());
         if (rc) return rc;
         e = cudaStreamSynchronize(p.stream);
         if (e != cudaSuccess) return cuda_status(e);
@@ -272,7 +282,7 @@ int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, c
             full_term_iters += (long long)I.iterations * p.n_terms;
             {
                 StreamScope scope(p, W);
-                rc = full_gradient(p, W, y, path + (long long)idx * n, S.q);
+                rc = full_gradient(p, W, y, path + (long long)idx * n, S.q, mask.data());
                 if (rc) return rc;
                 rc = features_host(p, W, S, path + (long long)idx * n, pairs);
                 if (rc) return rc;
