@@ -577,7 +577,7 @@ def lambda_path_result(args, local_rank, M: int, K: int) -> dict:
                                             "note": "every listed value is below every group's score at f = 0"
                                                     if min(scores) > max(v / M for v in lams) else
                                                     "some group score at f = 0 is below a listed value"}},
-            "fista": f"constant step L = 1.05 x Lanczos estimate of ||F||^2, tol {args.tol}, max_it {args.max_it}, "
+            "fista": f"constant step L = 1.08 x Lanczos estimate of ||F||^2, tol {args.tol}, max_it {args.max_it}, "
                      f"warm-started path; screen: 7-128-128-1 MLP, threshold 0.5, KKT re-admission",
             "results": res}
 
@@ -883,7 +883,7 @@ def run_bspline(args, local_rank):
                        "draws": draws, "lambdas": "e^0 .. e^10",
                        "lsqr": "atol = btol = 1e-6, at most 200 iterations; U* with eps = 1e-3 per order; "
                                "re-solve on I_N(U*) with the same bandwidths and lambda",
-                       "fista": "warm-started path from e^10, constant step 1.05 x Lanczos estimate, tol 1e-6"},
+                       "fista": "warm-started path from e^10, constant step 1.08 x Lanczos estimate, tol 1e-6"},
             "results": {"lsqr_resolved_on_active_set": {"mean_error_per_lambda": ml.tolist(),
                                                         "min_over_lambda": float(ml.min()),
                                                         "paper_min (100 draws)": 9.1e-2,

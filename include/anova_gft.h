@@ -223,8 +223,9 @@ int lsqr_solve(anova_plan_t plan, const void *y_dev, const double *w_dev, double
  *                  and a smaller tol then runs to max_it
  *   step_mode    : 0 constant step L (Remark after the Algorithm), 1 backtracking
  *   L0, eta      : step constant (constant mode: L; backtracking: L_0) and eta > 1;
- *                  L0 <= 0 asks for 1.05 times a Lanczos (Golub-Kahan) estimate of ||F||^2
- *                  over the allowed groups (at most 60 transform pairs)
+ *                  L0 <= 0 asks for 1.08 times a Lanczos (Golub-Kahan) estimate of ||F||^2
+ *                  over the allowed groups (stopped when a step changes it by less than
+ *                  1e-3 relative, after 8 to 60 transform pairs)
  *   group_mask   : host [n_terms] uint8, 1 = group may be nonzero; NULL = all groups
  *   fhat_path_dev: [n_lambda][num_coeffs] complex, solution per lambda in the
  *                  order lambdas are given

@@ -336,8 +336,13 @@ static double tridiag_max_eig(const std::vector<double> &d, const std::vector<do
 // ||F||^2 on the active terms (group-masked if asked) from the Golub--Kahan
 // bidiagonalisation F V_k = U_k B_k started at the all-ones vector: the largest
 // Ritz value of B_k^T B_k is a lower bound that converges much faster than the
-// power iteration (Lanczos on F^H F); stop when it changes by < 1e-5 relative
-// or after max_steps steps.  Scalars in FP64.
+// power iteration (Lanczos on F^H F).  It stops when a step changes it by less
+// than 1e-3 relative (after at least 8 steps), or after max_steps steps.  On
+// clustered spectra (the d = 30, M = 2e6 workload) the Ritz values creep
+// upwards for dozens of steps: at that point they lie within about 1.5 % of
+// the 60-step value, so the step bound takes LANCZOS_MARGIN = 1.08 times the
+// estimate (1.05 times the 60-step value before).  Scalars in FP64.
+constexpr double LANCZOS_MARGIN = 1.08;
 template <typename C>
 static int lanczos_estimate(Plan &p, SolverWork *W, int max_steps, bool masked, double *out) {
     const Vecs<C> V(W);
@@ -399,7 +404,7 @@ static int lanczos_estimate(Plan &p, SolverWork *W, int max_steps, bool masked, 
         for (int i = 0; i < k; ++i) d[i] = alpha[i] * alpha[i] + (i > 0 ? beta[i - 1] * beta[i - 1] : 0.0);
         for (int i = 0; i + 1 < k; ++i) off[i] = alpha[i] * beta[i];
         est = tridiag_max_eig(d, off);
-        if (prev > 0 && std::fabs(est - prev) <= 1e-5 * est) break;
+        if (k >= 8 && prev > 0 && std::fabs(est - prev) <= 1e-3 * est) break;
         prev = est;
         if (!(h.beta > 0)) break;
     }
@@ -432,7 +437,7 @@ int fista_impl_t(Plan &p, const C *y, const double *w, const double *lambdas, in
         double est = 0.0;
         rc = lanczos_estimate<C>(p, W, 60, mask != nullptr, &est);
         if (rc) return rc;
-        L = 1.05 * est;
+        L = LANCZOS_MARGIN * est;
         if (!(L > 0)) L = 1.0;
     }
     std::vector<int> ord(n_lambda);
@@ -569,7 +574,7 @@ int fista_impl_t(Plan &p, const C *y, const double *w, const double *lambdas, in
     return set_active_terms(p, nullptr);
 }
 
-// 1.05 x the Lanczos estimate of ||F||^2 over all terms (FP32 plans):
+// LANCZOS_MARGIN x the Lanczos estimate of ||F||^2 over all terms (FP32 plans):
 // a valid FISTA step bound for the full problem and for every group-masked one
 int lipschitz_estimate(Plan &p, double *L) {
     int rc;
@@ -583,7 +588,7 @@ int lipschitz_estimate(Plan &p, double *L) {
         rc = lanczos_estimate<float2>(p, W, 60, false, &est);
     }
     if (rc) return rc;
-    *L = est > 0 ? 1.05 * est : 1.0;
+    *L = est > 0 ? LANCZOS_MARGIN * est : 1.0;
     return cuda_status(cudaStreamSynchronize(p.stream));
 }
 

@@ -158,7 +158,8 @@ def test_f64_kkt_and_power_step(gft):
     P = _plan64(gft, x, terms, bw)
     viol, nv = P.kkt(_c128(y), _c128(f), lam, rtol=1e-3)
     assert nv == 0
-    path, infos, rc = P.fista(_c128(y), [lam], max_it=20000, tol=1e-10)   # L from power iteration
+    path, infos, rc = P.fista(_c128(y), [lam], max_it=20000, tol=1e-10)   # L from the Lanczos estimate
     assert rc == 0
-    assert 1.0 <= infos[0]["L"] / np.linalg.norm(Fm, 2) ** 2 <= 1.06
+    # 1.08 x the estimate of ||F||^2, which is exact here (the Krylov space runs out)
+    assert 1.0 <= infos[0]["L"] / np.linalg.norm(Fm, 2) ** 2 <= 1.09
     assert rel_l2(host(path[0]), f) <= 1e-4

@@ -162,8 +162,9 @@ def test_fista_power_iteration_step(gft):
     Fm, F, FH = _dense_ops(x, terms, bw)
     P = _plan(gft, x, terms, bw)
     path, infos, rc = P.fista(cplx_dev(y), [1.0], max_it=20000, tol=1e-9)   # L from power iteration
-    # L = 1.05 x the power-iteration estimate of ||F||^2 (a safe upper bound)
-    assert 1.0 <= infos[0]["L"] / np.linalg.norm(Fm, 2) ** 2 <= 1.06
+    # L = 1.08 x the Lanczos estimate of ||F||^2 (a safe upper bound; the
+    # estimate is exact here, where the Krylov space runs out)
+    assert 1.0 <= infos[0]["L"] / np.linalg.norm(Fm, 2) ** 2 <= 1.09
     ref = solvers.block_coordinate_group_lasso(Fm, y, 1.0, offs, lens)
     assert rel_l2(host(path[0]), ref) <= TOL
 
