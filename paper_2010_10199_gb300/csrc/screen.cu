@@ -111,18 +111,20 @@ struct ScreenWork {
 // q = F^H (F f - y) over all groups.  f is zero outside the groups of fmask
 // (user terms; NULL: any group), so the forward runs over those only; the
 // adjoint, which the KKT scores need for every group, over all of them.
+// residual_ready: W->tM already holds F f - y (a one-lambda fista_impl call
+// with info leaves its solution's residual there), so only the adjoint runs.
 static int full_gradient(Plan &p, SolverWork *W, const float2 *y, const float2 *f, float2 *q,
-                         const uint8_t *fmask) {
-    int rc = set_active_terms(p, fmask);
-    if (rc) return rc;
+                         const uint8_t *fmask, bool residual_ready = false) {
     float2 *tM = (float2 *)W->tM;
-    rc = launch_trafo_f32(p, f, tM);
-    if (rc) return rc;
-    if (fmask) {
-        rc = set_active_terms(p, nullptr);
+    if (!residual_ready) {
+        int rc = set_active_terms(p, fmask);
         if (rc) return rc;
+        rc = launch_trafo_f32(p, f, tM);
+        if (rc) return rc;
+        k_residual<<<RED_BLOCKS, RED_THREADS, 0, p.stream>>>(W->st, tM, y, p.M, nullptr);
     }
-    k_residual<<<RED_BLOCKS, RED_THREADS, 0, p.stream>>>(W->st, tM, y, p.M, nullptr);
+    int rc = set_active_terms(p, nullptr);
+    if (rc) return rc;
     return launch_adjoint_f32(p, tM, q);
 }
 
@@ -282,7 +284,7 @@ int fista_screened_path(anova_plan_t plan, anova_mlp_t mlp, const void *y_dev, c
             full_term_iters += (long long)I.iterations * p.n_terms;
             {
                 StreamScope scope(p, W);
-                rc = full_gradient(p, W, y, path + (long long)idx * n, S.q, mask.data());
+                rc = full_gradient(p, W, y, path + (long long)idx * n, S.q, mask.data(), true);
                 if (rc) return rc;
                 rc = features_host(p, W, S, path + (long long)idx * n, pairs);
                 if (rc) return rc;

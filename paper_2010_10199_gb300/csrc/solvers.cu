@@ -534,6 +534,8 @@ int fista_impl_t(Plan &p, const C *y, const double *w, const double *lambdas, in
             SolverState z;
             std::memset(&z, 0, sizeof(z));
             cudaMemcpyAsync(W->st, &z, sizeof(z), cudaMemcpyHostToDevice, s);
+            // leaves the residual F f - y in tM (the screened path's KKT check
+            // of a one-lambda call reuses it)
             rc = trafo_c(p, (const C *)V.f, V.tM);
             if (rc) return rc;
             k_residual<<<RED_BLOCKS, RED_THREADS, 0, s>>>(W->st, V.tM, y, M, W->part);
