@@ -157,7 +157,10 @@ int anova_term_grid(anova_plan_t plan, int u, int *n, int *m_col, int *m_row);
  * The two buffers must not overlap.  Accuracy: relative l2 error against the
  * exact sum near the plan's eps (FP32 plans: about 3e-6 at the default eps
  * 1e-5).  FP32 plans with sorted nodes sum every node's terms in 64-bit fixed
- * point, so the result is bitwise reproducible for a plan.
+ * point, so the result is bitwise reproducible for a plan.  FP32 plans need
+ * the oversampled grid values (about sum_k |fhat_k| at most) below 2^114
+ * (2e34) in magnitude: the tensor-core kernels split each operand x into two
+ * TF32 parts through 8193 x, which must stay finite.
  */
 int grouped_trafo(anova_plan_t plan, const void *fhat_dev, void *f_dev);
 
@@ -169,7 +172,8 @@ int grouped_trafo(anova_plan_t plan, const void *fhat_dev, void *f_dev);
  * Accuracy as for grouped_trafo (FP32 plans: about 5e-6 at the default eps),
  * whichever cell_kernel the plan uses.  The order of the shared-memory float
  * additions inside a CTA is not fixed, so repeated calls may differ at the
- * rounding level.
+ * rounding level.  FP32 plans need |y_j| below 2^114 (2e34), as for
+ * grouped_trafo.
  */
 int grouped_adjoint(anova_plan_t plan, const void *y_dev, void *fhat_dev);
 
