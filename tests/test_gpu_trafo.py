@@ -152,6 +152,19 @@ def test_window_and_oversampling_options(gft, path, opts):
     _pair_check(gft, x, terms, bw, tol=tol, **opts, **SPREAD_PATHS[path])
 
 
+@pytest.mark.parametrize("scale", [1e-25, 1e25])
+def test_extreme_scales(gft, scale):
+    """Coefficients and data scaled far from 1 (within the FP32 operand range
+    the header states): the operand splits of the tensor-core kernels and the
+    forward's fixed-point exponent keep the relative bar."""
+    x = inputs.uniform_points(29, 4, 3001)
+    terms = anova.term_set(4, 2)
+    bw = [0] + [32] * 4 + [16] * 6
+    fhat = scale * inputs.decaying_coefficients(3, terms, bw)
+    y = scale * inputs.complex_normal(3, 4, x.shape[1])
+    _pair_check(gft, x, terms, bw, fhat=fhat, y=y)
+
+
 def test_c2_subsample_all_terms(gft):
     w = inputs.c2_scale(M=10000)
     _pair_check(gft, w["x"], w["terms"], w["bandwidths"], fhat=w["fhat"], y=w["y"])
